@@ -1,0 +1,80 @@
+"""Independent NumPy brute force of the backprojection sum, for tiny grids.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Written separately from
+``oracle.c`` so that each checks the other: the attitude matrix is built as a
+product of textbook single-axis rotations instead of the entries printed in
+Eq. 2, the Bessel function comes from ``scipy.special.i0`` instead of a series,
+and the sum is a broadcast over (pixel, ping, channel, tap).
+
+Paper: arXiv 2101.05888.  Sec. II-A (per-pixel inversion of Eq. 1), Eq. 2.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import i0 as scipy_i0
+
+
+def rot_x(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+
+
+def rot_y(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[c, 0.0, s], [0.0, 1.0, 0.0], [-s, 0.0, c]])
+
+
+def rot_z(a):
+    c, s = np.cos(a), np.sin(a)
+    return np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+
+
+def attitude_matrix(roll, pitch, yaw):
+    """Rz(yaw) Ry(pitch) Rx(roll): body -> NED."""
+    return rot_z(yaw) @ rot_y(pitch) @ rot_x(roll)
+
+
+def sensor_positions(pos, att, tx_lever, rx_lever, offsets=None):
+    pos = np.asarray(pos, dtype=np.float64)
+    P = pos.shape[0]
+    base = pos + (0.0 if offsets is None else np.asarray(offsets, dtype=np.float64))
+    Rs = np.stack([attitude_matrix(*att[i]) for i in range(P)])           # [P,3,3]
+    tx = base + np.einsum("pab,b->pa", Rs, np.asarray(tx_lever, dtype=np.float64))
+    rx = base[:, None, :] + np.einsum("pab,cb->pca", Rs, np.asarray(rx_lever, dtype=np.float64))
+    return tx, rx
+
+
+def kaiser_sinc(d, taps, beta):
+    """Un-normalised Kaiser-windowed sinc v(d) (support |d| < taps/2)."""
+    h = taps / 2.0
+    arg = np.clip(1.0 - (d / h) ** 2, 0.0, None)
+    win = scipy_i0(beta * np.sqrt(arg)) / scipy_i0(beta)
+    return np.where(np.abs(d) < h, np.sinc(d) * win, 0.0)
+
+
+def weights(f, taps, beta):
+    """Normalised weights for fractions f [...]; returns [..., taps]."""
+    k = np.arange(taps) - taps // 2 + 1
+    v = kaiser_sinc(np.asarray(f)[..., None] - k, taps, beta)
+    return v / v.sum(axis=-1, keepdims=True)
+
+
+def backproject(tx, rx, fc, fs, c, t0, echo, taps, beta, pix):
+    """Direct broadcast evaluation; pix [n,3], echo [P,C,Ns]; returns [n]."""
+    pix = np.asarray(pix, dtype=np.float64)
+    P, C, Ns = echo.shape
+    rt = np.linalg.norm(pix[:, None, :] - tx[None, :, :], axis=-1)                 # [n,P]
+    rr = np.linalg.norm(pix[:, None, None, :] - rx[None, :, :, :], axis=-1)        # [n,P,C]
+    tau = (rt[:, :, None] + rr) / c
+    u = (tau - t0) * fs
+    j0 = np.floor(u)
+    f = u - j0
+    k = np.arange(taps) - taps // 2 + 1
+    j = j0[..., None].astype(np.int64) + k                                          # [n,P,C,T]
+    valid = (j >= 0) & (j < Ns)
+    jc = np.clip(j, 0, Ns - 1)
+    ii = np.arange(P)[None, :, None, None]
+    cc = np.arange(C)[None, None, :, None]
+    samples = np.where(valid, echo[ii, cc, jc], 0.0)
+    s = (weights(f, taps, beta) * samples).sum(-1)
+    return (s * np.exp(2j * np.pi * fc * tau)).sum(axis=(1, 2))
