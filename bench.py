@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of GB300 time-domain backprojection.
+
+One step = one full 2D backprojection of the full-size stripmap workload
+(2048 pings x 32 receivers x 16384 complex samples onto 4096 x 4096 pixels at
+1.5 cm, 8-tap Kaiser-windowed sinc), i.e. 1.10e12 pixel.ping.channel updates.
+Inputs are seeded synthetic data with the shape of the paper's stripmap survey
+(the survey data itself is not available).
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) are replicas: each
+rank images the whole workload on its own GPU; value = all ranks' updates over
+the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload stripmap_2d|volume_3d|autofocus_2d|small_2d] [--echo c64|f16|bf16]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2101_05888_gb300 import synth  # noqa: E402
+
+METRIC = "G pixel·ping·channel updates/s; learned/BF16 vs plain FP32 at rel-L2 ≤3e-3"
+UNIT = "G updates/s"
+BETA = 4.0
+# issue-rate roof per update (a3-a6 of the hot path): ~32 FP32 instructions on
+# 128 FP32 lanes/clk/SM and 4 SFU ops (rsqrt, rcp, sin, cos) on 16 SFU
+# lanes/clk/SM -> 4 updates per clock per SM from either pipe.
+UPDATES_PER_CLK_PER_SM = 4.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stripmap_2d", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--echo", default="c64", choices=["c64", "f16", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        time.sleep(0.05)
+        sm = []
+        smax = 0.0
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax = max(smax, float(r[1]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if r[4 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_inputs(w, seed_echo=None):
+    nav = synth.nav(w)
+    echo = synth.random_echo(w.n_pings, w.n_rx, w.n_samples, seed=w.seed if seed_echo is None else seed_echo)
+    return nav, echo
+
+
+def cpu_baseline(w, nav, echo, seconds: float, rank_seed=0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample of
+    random pixels of the same workload (all pings and channels per pixel)."""
+    import oracle
+    sig = oracle.Signal(synth.FC, synth.FS, synth.C_SOUND, w.t0, w.n_samples)
+    tx, rx = oracle.sensor_positions(nav["pos"], nav["att"], nav["tx_lever"], nav["rx_lever"])
+    cores = oracle.max_threads()
+    pairs = w.n_pings * w.n_rx
+    idx = synth.random_pixel_indices(w.grid, 4096, seed=99 + rank_seed)
+    g = w.grid
+    pts = oracle.grid_index_points(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, idx)
+    # calibrate with a few pixels, then size the sample to the time budget
+    n0 = max(cores, 4)
+    t = time.perf_counter()
+    oracle.backproject(tx, rx, sig, echo, 8, BETA, pts[:n0])
+    dt0 = time.perf_counter() - t
+    n = int(min(len(pts), max(n0, n0 * seconds / max(dt0, 1e-3))))
+    n = max(cores, (n // cores) * cores)
+    t = time.perf_counter()
+    oracle.backproject(tx, rx, sig, echo, 8, BETA, pts[:n])
+    dt = time.perf_counter() - t
+    ups = n * pairs / dt
+    return {"value": ups / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d random pixels x %d pings x %d channels (%.3g updates) of %s, FP64, %.1f s"
+                      % (n, w.n_pings, w.n_rx, n * pairs, w.name, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    nav, echo = build_inputs(w)
+    steps = []
+    cb = None
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(w, nav, echo, per_step if k >= args.warmup else 1.0, rank_seed=k)
+        if k >= args.warmup:
+            steps.append(r["value"])
+            cb = r
+    value = statistics.median(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, args), "ms_per_step": None,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, args):
+    g = w.grid
+    return {"workload": w.name, "pings": w.n_pings, "rx": w.n_rx, "samples": w.n_samples,
+            "pixels": "%dx%dx%d" % (g.nx, g.ny, g.nz), "pixel_m": g.dx, "taps": 8,
+            "interp": "kaiser_sinc beta=%g (Farrow degree 7)" % BETA, "echo": args.echo,
+            "updates_per_step": w.updates, "l2": "inputs larger than L2 (echo %.2f GB, L2 0.13 GB)"
+            % (w.n_pings * w.n_rx * w.n_samples * (8 if args.echo == "c64" else 4) / 1e9),
+            "parallelism": "replicas"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2101_05888_gb300 as sas
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload(args.workload)
+    store = {"c64": sas.SAS_ECHO_C64, "f16": sas.SAS_ECHO_C32_F16, "bf16": sas.SAS_ECHO_C32_BF16}[args.echo]
+    nav, echo = build_inputs(w)
+    sig = sas.make_signal(synth.FC, synth.FS, synth.C_SOUND, w.t0, w.n_samples)
+    stream = torch.cuda.current_stream(dev)
+    geom = sas.Geometry.from_nav(nav, sig)
+    geom.upload_echo(echo, store)
+    grid = sas.grid_from(w.grid)
+    interp = sas.kaiser(BETA)
+    image = torch.empty((w.grid.nz, w.grid.ny, w.grid.nx), dtype=torch.complex64, device=dev)
+    dim3 = w.grid.nz > 1
+    fn = sas.sas_backproject_3d if dim3 else sas.sas_backproject_2d
+
+    def step():
+        fn(geom.h, grid, interp, image, 0)
+
+    for _ in range(args.warmup):
+        step()
+    geom.sync_status()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_all0.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    geom.sync_status()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * w.updates * args.steps / (total_ms / 1e3) / 1e9
+
+    # roofline of the (only) kernel of the step
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    peak = props.multi_processor_count * sm_max * 1e6 * UPDATES_PER_CLK_PER_SM / 1e9
+    achieved = w.updates / (statistics.mean(launch_ms) / 1e3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
+            "traffic": None,
+            "peak_basis": "%d SMs x %.0f MHz x %.0f updates/clk/SM (FP32 128 lanes / 32 ops, SFU 16 lanes / 4 ops)"
+                          % (props.multi_processor_count, sm_max, UPDATES_PER_CLK_PER_SM)}
+    if clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (props.multi_processor_count * clk["sm_mhz"] * 1e6 *
+                                                     UPDATES_PER_CLK_PER_SM / 1e9)
+
+    # end to end through the C ABI with host buffers: H2D of the echo from
+    # pinned memory, backprojection, D2H of the image, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        h_echo = torch.from_numpy(echo).pin_memory()
+        h_img = torch.empty(image.shape, dtype=torch.complex64).pin_memory()
+        for k in range(1 + args.e2e_steps):
+            if k == 1:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            sas.sas_echo_upload(geom.h, h_echo, 0, store)
+            step()
+            h_img.copy_(image, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        geom.sync_status()
+        e2e = {"value": world * w.updates / e2e_s / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_echo.numel() * h_echo.element_size()),
+               "d2h_bytes_per_step": int(h_img.numel() * h_img.element_size()),
+               "ms_per_step": e2e_s * 1e3}
+        del h_echo, h_img
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, nav, echo, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.echo == "c64" else "f32 (echo %s)" % args.echo,
+                "data": "synthetic (seeded band-limited Gaussian echo rows, stripmap nav with sway/heave/yaw)",
+                "config": config_of(w, args), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+                "clocks": clk, "gpu_launches": args.steps,
+                "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms), "max": max(launch_ms)}}
+        print(json.dumps(line), flush=True)
+    geom.close()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

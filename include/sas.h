@@ -1,0 +1,250 @@
+/*
+ * sas.h -- C ABI of the GB300 time-domain backprojection library (libsas).
+ *
+ * The library forms synthetic-aperture-sonar images by time-domain
+ * backprojection (TDBP): for every pixel or voxel x, every ping i and every
+ * receiver channel c it evaluates the two-way delay
+ *     tau_ic(x) = (|x - x_TX,i| + |x - x_RX,i,c|) / c_sound,
+ * interpolates the range-compressed complex baseband echo at that delay and
+ * accumulates it rotated by exp(+j 2 pi f_c tau) into the image:
+ *     I(x) = sum_i sum_c s_ic(u_ic(x)) exp(+j 2 pi f_c tau_ic(x)),
+ *     u = (tau - t0) f_s,   s(u) = sum_{k=-3..4} w_k(frac u) e[i][c][floor u + k].
+ * This is the per-pixel inversion of the forward model, Eq. 1 of arXiv
+ * 2101.05888 (ASASIN), Sec. II-A; samples outside [0, Ns) read as zero.
+ * Transmitter/receiver positions follow Eq. 2 (attitude) and the lever arms of
+ * Sec. II-C, in the north-east-down frame of Sec. II-B.
+ *
+ * Conventions for every call:
+ *  - Return value: SAS_OK (0) or a negative sas_status; no exception crosses
+ *    the ABI.  sas_last_error() gives a message for the calling thread.
+ *  - Calls are asynchronous and stream-ordered on the CUDA stream passed in
+ *    (NULL = legacy default stream).  Device faults detected inside kernels
+ *    (a bounded wait that ran out) are recorded in a per-handle status word and
+ *    reported by sas_sync_status().
+ *  - "Host" pointers are read during the call (the caller may free them when
+ *    the call returns).  "Device" pointers are caller-owned GPU memory that
+ *    must stay valid until the stream work completes.
+ *  - A handle may be used from one stream at a time.
+ *  - Complex arrays are interleaved (re, im) float32 pairs (complex64).
+ *  - Arrays are C-contiguous in the order written, last index fastest.
+ */
+#ifndef SAS_H
+#define SAS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAS_VERSION 10000 /* 1.0.0 */
+
+typedef enum {
+    SAS_OK = 0,
+    SAS_ERR_ARG = -1,         /* invalid argument (null pointer, bad size, ...) */
+    SAS_ERR_CUDA = -2,        /* a CUDA runtime/driver call failed */
+    SAS_ERR_OOM = -3,         /* device allocation failed */
+    SAS_ERR_TIMEOUT = -4,     /* a kernel's bounded wait ran out (results invalid) */
+    SAS_ERR_UNSUPPORTED = -5, /* valid but unsupported configuration */
+    SAS_ERR_STATE = -6        /* call out of order (e.g. no echo uploaded) */
+} sas_status;
+
+/* Storage type of the echo inside the handle. */
+typedef enum {
+    SAS_ECHO_C64 = 0,      /* complex64: float32 (re, im) */
+    SAS_ECHO_C32_F16 = 1,  /* complex as two float16, with a float32 scale per (ping, channel) */
+    SAS_ECHO_C32_BF16 = 2  /* complex as two bfloat16, with a float32 scale per (ping, channel) */
+} sas_echo_dtype;
+
+/* Signal description (Eq. 1): carrier fc [Hz], complex baseband sample rate
+ * fs [Hz], sound speed c [m/s], t0 = delay of echo sample 0 after transmit
+ * [s], n_samples = samples per (ping, channel) row.  n_samples must be a
+ * multiple of 4 (16-byte rows for the bulk-copy engine). */
+typedef struct {
+    double fc, fs, c, t0;
+    int32_t n_samples;
+} sas_signal;
+
+/* Navigation (Sec. II-B/C).  All arrays host, FP64, NED metres / radians.
+ *   ping_pos [P][3]  vehicle reference point per ping
+ *   ping_att [P][3]  (roll, pitch, yaw) per ping, rotation of Eq. 2
+ *   tx_lever [3]     transmitter lever arm, body frame
+ *   rx_lever [C][3]  receiver lever arms, body frame
+ * Stop-and-hop: transmitter and receivers sit at their ping-time positions. */
+typedef struct {
+    int32_t n_pings, n_rx;
+    const double* ping_pos;
+    const double* ping_att;
+    const double* tx_lever;
+    const double* rx_lever;
+} sas_nav;
+
+/* Pixel grid: pixel (ix, iy, iz) sits at (x0 + ix dx, y0 + iy dy, z0 + iz dz);
+ * images are [nz][ny][nx] complex64 with ix fastest.  2D images use nz = 1
+ * (dz ignored). */
+typedef struct {
+    double x0, y0, z0, dx, dy, dz;
+    int32_t nx, ny, nz;
+} sas_grid;
+
+typedef enum {
+    SAS_INTERP_KAISER_SINC = 0, /* normalised Kaiser-windowed sinc, `taps` taps, shape kaiser_beta */
+    SAS_INTERP_TABLE = 1        /* user taps tabulated on a uniform fraction grid (see below) */
+} sas_interp_kind;
+
+/* Fractional-delay interpolator.  The paper does not name its interpolator;
+ * the library's default is the Kaiser-windowed sinc normalised to unit sum:
+ *   w_k(f) = v(f - k) / sum_k' v(f - k'),
+ *   v(d)   = sinc(d) I0(beta sqrt(1 - (2d/taps)^2)) / I0(beta), |d| < taps/2,
+ * taps k = -taps/2+1 .. taps/2 around floor(u), f = u - floor(u).
+ * SAS_INTERP_TABLE: d_table is a device FP32 array [table_n + 1][taps] of tap
+ * values at f = j / table_n (j = 0 .. table_n), e.g. a tabulated learned
+ * interpolator; values between rows are linear in f.
+ * Only taps = 8 is supported by the backprojection kernels. */
+typedef struct {
+    int32_t kind;
+    int32_t taps;
+    double kaiser_beta;
+    int32_t table_n;
+    const float* d_table;
+} sas_interp;
+
+typedef struct sas_geometry_s* sas_geometry_t;
+
+/* Library version (SAS_VERSION) and the message of the last failed call on
+ * this thread ("" if none).  The string stays valid until the next call. */
+int sas_version(void);
+const char* sas_last_error(void);
+
+/* Creates a handle on the current CUDA device: copies the navigation and
+ * signal description, allocates the handle's device slab and computes the
+ * transmitter and receiver positions per ping (Eq. 2 rotation of the lever
+ * arms plus the vehicle position; per-ping offsets start at zero) with an FP64
+ * kernel on `cuda_stream`.  *out receives the handle.
+ * Errors: SAS_ERR_ARG (null pointers, P or C < 1, n_samples < 8 or not a
+ * multiple of 4, non-positive fs or c), SAS_ERR_OOM, SAS_ERR_CUDA. */
+int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, void* cuda_stream,
+                        sas_geometry_t* out);
+
+/* Sets per-ping position offsets dp [P][3] (FP64, metres, added to the vehicle
+ * position, hence to the transmitter and every receiver of that ping) and
+ * recomputes the sensor positions.  offsets == NULL resets them to zero.
+ * on_device: 0 = host array, 1 = device array.  This is the variable that
+ * sas_backproject_adjoint differentiates against (autofocus). */
+int sas_geometry_set_offsets(sas_geometry_t h, const double* offsets, int on_device,
+                             void* cuda_stream);
+
+/* Copies the current sensor positions to device arrays d_tx [P][3] and
+ * d_rx [P][C][3] (FP64).  Either may be NULL. */
+int sas_geometry_positions(sas_geometry_t h, double* d_tx, double* d_rx, void* cuda_stream);
+
+/* Releases the handle and all device memory it owns (synchronises the device). */
+int sas_geometry_destroy(sas_geometry_t h);
+
+/* Stores the echo in the handle.  echo: complex64 [P][C][Ns], host
+ * (on_device = 0) or device (on_device = 1).  store_dtype selects the storage:
+ * SAS_ECHO_C64 copies as is; the 16-bit types divide each (ping, channel) row
+ * by its largest |component| (kept as a float32 scale and re-applied inside
+ * the kernels) and round to float16 / bfloat16 on the device.  Replaces any
+ * previous echo.  Errors: SAS_ERR_ARG, SAS_ERR_OOM, SAS_ERR_CUDA. */
+int sas_echo_upload(sas_geometry_t h, const void* echo, int on_device, int store_dtype,
+                    void* cuda_stream);
+
+/* Copies the stored echo, converted back to complex64 (scale applied), into
+ * d_out [P][C][Ns] (device).  For inspecting the quantised echo. */
+int sas_echo_download(sas_geometry_t h, void* d_out, void* cuda_stream);
+
+/* 2D backprojection onto the grid plane z = z0 (grid->nz must be 1).
+ * d_image: complex64 [ny][nx], device.  accumulate = 0 overwrites the image,
+ * 1 adds to it (e.g. to stream pings through several echo uploads).
+ * Errors: SAS_ERR_ARG, SAS_ERR_STATE (no echo), SAS_ERR_UNSUPPORTED (taps != 8,
+ * a tile's delay span too long for the staging buffers), SAS_ERR_CUDA. */
+int sas_backproject_2d(sas_geometry_t h, const sas_grid* grid, const sas_interp* interp,
+                       void* d_image, int accumulate, void* cuda_stream);
+
+/* 3D backprojection, voxel grid [nz][ny][nx] (Sec. III-B layered volume).
+ * Same contract as sas_backproject_2d. */
+int sas_backproject_3d(sas_geometry_t h, const sas_grid* grid, const sas_interp* interp,
+                       void* d_image, int accumulate, void* cuda_stream);
+
+/* Adjoints of the backprojection B (echo -> image) on `grid` (2D or 3D):
+ *  - d_echo_adj != NULL: linear adjoint  e_adj = B^H d_grad_image, complex64
+ *    [P][C][Ns] device, overwritten:
+ *        e_adj[i][c][floor u + k] += w_k(frac u) exp(-j 2 pi fc tau) I(x);
+ *  - d_grad_offsets != NULL: gradient of a real loss L with respect to the
+ *    per-ping offsets, [P][3] FP64 device, overwritten, given
+ *    d_grad_image = dL/dI* (complex64 image):
+ *        dL/d(dp_i) = 2 Re sum_x sum_c conj(g(x)) dI_ic(x)/d(dp_i).
+ *    Image tiles are recomputed (not stored); per-tile partial sums are
+ *    reduced in a fixed order (deterministic).
+ * At least one output must be non-NULL. */
+int sas_backproject_adjoint(sas_geometry_t h, const sas_grid* grid, const sas_interp* interp,
+                            const void* d_grad_image, void* d_echo_adj, double* d_grad_offsets,
+                            void* cuda_stream);
+
+/* Image sharpness S = sum|I|^4 / (sum|I|^2)^2 over n complex64 values
+ * (d_image, device).  d_out3 (device, FP64 [3]) receives {S, N = sum|I|^4,
+ * D = sum|I|^2}; if d_grad != NULL it receives g = dS/dI* =
+ * 2 I (|I|^2/D^2 - N/D^3) (complex64 [n], device).  Sums are FP64 and
+ * deterministic.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_sharpness(const void* d_image, int64_t n, double* d_out3, void* d_grad, void* cuda_stream);
+
+/* Evaluates the interpolator's taps at n fractions f (device FP32 [n]) into
+ * d_taps (device FP32 [n][taps]) exactly as the backprojection kernels apply
+ * them, and writes to *d_max_err (device FP64, may be NULL) the largest
+ * deviation of that form from the interpolator's definition over a fine
+ * fraction grid. */
+int sas_interp_eval(const sas_interp* interp, const float* d_f, int64_t n, float* d_taps,
+                    double* d_max_err, void* cuda_stream);
+
+/* ---- Learned interpolator (MLP 1 -> 64 -> 64 -> 8, GELU, FP16 weights) ----
+ * Parameters are a flat FP32 master vector theta [SAS_MLP_NPARAMS] in the
+ * order W1 [64][1], b1 [64], W2 [64][64] ([out][in]), b2 [64], W3 [8][64],
+ * b3 [8]; the network input is x = 2 f - 1.  Kernels round the weights to
+ * FP16 and compute in FP32:  a1 = gelu(W1 x + b1), a2 = gelu(W2 a1 + b2),
+ * taps = W3 a2 + b3,  gelu(z) = z/2 (1 + erf(z/sqrt 2)). */
+#define SAS_MLP_NPARAMS 4808
+
+/* Training windows from an echo (device complex64 [rows][Ns]): for n draws
+ * (d_frac [n] FP32 fractions, d_row [n] int32 rows, d_pos [n] int32 sample
+ * indices) writes the 8-sample window e[row][pos-3 .. pos+4] to d_windows
+ * (complex64 [n][8]) and the 32-tap Kaiser-sinc (beta = target_beta)
+ * interpolation at pos + frac to d_targets (complex64 [n]).  Samples outside
+ * the row read as zero. */
+int sas_mlp_make_windows(const void* d_echo, int32_t rows, int32_t n_samples, const float* d_frac,
+                         const int32_t* d_row, const int32_t* d_pos, int64_t n, double target_beta,
+                         void* d_windows, void* d_targets, void* cuda_stream);
+
+/* Loss L = mean_b |sum_m t_m(f_b) s_b,m - y_b|^2 and its gradient w.r.t. theta
+ * (device FP32 [SAS_MLP_NPARAMS], overwritten) on a batch of n windows.
+ * d_loss: device FP32 [1].  d_work: device scratch of sas_mlp_workspace_bytes(n). */
+int64_t sas_mlp_workspace_bytes(int64_t n);
+int sas_mlp_loss_grad(const float* d_theta, const float* d_frac, const void* d_windows,
+                      const void* d_targets, int64_t n, float* d_loss, float* d_grad, void* d_work,
+                      void* cuda_stream);
+
+/* One Adam update (Kingma & Ba) of theta with moments m, v (all device FP32
+ * [SAS_MLP_NPARAMS]); step counts from 1. */
+int sas_mlp_adam(float* d_theta, const float* d_grad, float* d_m, float* d_v, int32_t step,
+                 float lr, float beta1, float beta2, float eps, void* cuda_stream);
+
+/* Tabulates the network's taps at f = j / table_n, j = 0 .. table_n, into
+ * d_table_out (device FP32 [table_n + 1][8]) for use as SAS_INTERP_TABLE. */
+int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, float* d_table_out,
+                            void* cuda_stream);
+
+/* Waits for the stream, then reports and clears the handle's device status:
+ * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check. */
+int sas_sync_status(sas_geometry_t h, void* cuda_stream);
+
+/* Test hook for failure detection: when skip != 0 the next backprojection
+ * launches do not issue their bulk copies and use a wait limit of
+ * wait_limit_ms, so their waits run out and the kernels return early with the
+ * timeout status set (no fault, no trap).  skip = 0 restores normal operation. */
+int sas_debug_starve_copies(sas_geometry_t h, int skip, int32_t wait_limit_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAS_H */

@@ -59,7 +59,7 @@ def lib():
             L.oracle_bessel_i1_over_x.argtypes = [D]
             L.oracle_bessel_i1_over_x.restype = D
             L.oracle_kaiser_sinc_weights.argtypes = [D, I, D, P, P]
-            L.oracle_backproject.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, I]
+            L.oracle_backproject.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, I]
             L.oracle_backproject_adjoint.argtypes = [I, I, P, P, D, D, D, D, I, I, D, Lg, P, P, P, I]
             L.oracle_vjp_offsets.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, P, I]
             L.oracle_sharpness.argtypes = [Lg, P, P, P]
@@ -165,14 +165,18 @@ def _echo_c128(echo) -> np.ndarray:
 
 
 def backproject(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, nthreads: int = 0):
-    """I(x) at the given pixels [n,3]; returns complex128 [n]."""
+    """I(x) at the given pixels [n,3]; returns complex128 [n].  A complex64
+    echo is read in place (widened exactly to FP64), others as complex128."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
-    e = _echo_c128(echo)
+    if isinstance(echo, np.ndarray) and echo.dtype == np.complex64 and echo.flags.c_contiguous:
+        e, f32 = echo, 1
+    else:
+        e, f32 = _echo_c128(echo), 0
     P, C = tx.shape[0], rx.shape[1]
     assert e.shape == (P, C, sig.n_samples)
     out = np.zeros((pix.shape[0], 2))
     lib().oracle_backproject(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
-                             _p(e), int(taps), float(beta), pix.shape[0], _p(pix), _p(out),
+                             _p(e), f32, int(taps), float(beta), pix.shape[0], _p(pix), _p(out),
                              int(nthreads))
     return out[:, 0] + 1j * out[:, 1]
 

@@ -210,13 +210,14 @@ static void delay_eval(const double* x, const double* t, const double* r, double
 
 /* Backprojection (Sec. II-A, Eq. 1 inverted per pixel; pixels independent):
  *   I(x) = sum_i sum_c sum_m w_m(f) e[i][c][j0 + k_m] exp(+j 2 pi fc tau_ic(x))
- * echo: [P][C][Ns] complex interleaved (re, im); pix: [npix][3]; out: [npix][2].
+ * echo: [P][C][Ns] complex interleaved (re, im), FP64 or (echo_f32 = 1) FP32;
+ * pix: [npix][3]; out: [npix][2].
  * Pinned by: NumPy brute force (brute.py) to 1e-12; linearity in the echo;
  * translation invariance; closed-form point-scatterer response (peak at the
  * scatterer, |I| = A P C within the interpolator error, phase = arg A).    */
 void oracle_backproject(int P, int C, const double* tx, const double* rx, double fc, double fs,
-                        double c, double t0, int Ns, const double* echo, int taps, double beta,
-                        long npix, const double* pix, double* out, int nthreads) {
+                        double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
+                        double beta, long npix, const double* pix, double* out, int nthreads) {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
     for (long p = 0; p < npix; ++p) {
@@ -228,13 +229,18 @@ void oracle_backproject(int P, int C, const double* tx, const double* rx, double
                 oracle_delay d;
                 delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
                 oracle_kaiser_sinc_weights(d.f, taps, beta, w, NULL);
-                const double* row = echo + 2 * ((size_t)i * C + ch) * (size_t)Ns;
+                const size_t row = 2 * ((size_t)i * C + ch) * (size_t)Ns;
                 double sr = 0.0, si = 0.0;
                 for (int m = 0; m < taps; ++m) {
                     const long j = d.j0 + (m - taps / 2 + 1);
                     if (j < 0 || j >= Ns) continue;
-                    sr += w[m] * row[2 * j];
-                    si += w[m] * row[2 * j + 1];
+                    /* complex64 input is widened exactly to FP64 */
+                    const double er = echo_f32 ? (double)((const float*)echo)[row + 2 * j]
+                                               : ((const double*)echo)[row + 2 * j];
+                    const double ei = echo_f32 ? (double)((const float*)echo)[row + 2 * j + 1]
+                                               : ((const double*)echo)[row + 2 * j + 1];
+                    sr += w[m] * er;
+                    si += w[m] * ei;
                 }
                 double ph = fc * d.tau;
                 ph -= floor(ph);

@@ -1,0 +1,192 @@
+// Internal definitions shared by the libsas translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/sas.h"
+
+namespace sas {
+
+// ---------------------------------------------------------------------------
+// Error reporting (host)
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SAS_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Device status bits (handle status word).
+enum : uint32_t { DEV_TIMEOUT = 1u };
+
+// ---------------------------------------------------------------------------
+// Interpolator in Farrow form: tap m (offset k_m = m - 3) has weight
+//   w_m(f) = sum_{p<NP} coef[m][p] g^p,  g = f - 1/2,
+// so the interpolated value is a polynomial in g whose coefficients are FIR
+// outputs of the echo:  s = sum_p g^p E_p[i0],  E_p[i] = sum_m coef[m][p] e[i + k_m].
+constexpr int TAPS = 8;
+constexpr int NP = 8;            // polynomial degree 7
+struct FarrowCoef {
+    float c[TAPS][NP];
+};
+
+// Fits the interpolator to Farrow form on the device (FP64 Chebyshev
+// interpolation at NP nodes, converted to monomials in g).  d_coef: device
+// FarrowCoef; d_err: optional device double, max |fit - definition|.
+int fit_interp(const sas_interp* interp, FarrowCoef* d_coef, double* d_err, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// PTX helpers (device)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the barrier phase with the given parity to complete; gives up
+// after limit_ns of wall time (returns false).  Never spins unboundedly.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 15u && globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 2D tiled bulk tensor copy global -> shared, completion on an mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Packed FP32 pair FMA (sm_100+): d = a * b + c on both halves.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t ra = *reinterpret_cast<uint64_t*>(&a), rb = *reinterpret_cast<uint64_t*>(&b),
+             rc = *reinterpret_cast<uint64_t*>(&c), rd;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    return *reinterpret_cast<float2*>(&rd);
+}
+
+// floor() of a float of magnitude < 2^22 on the FP32 pipe: returns the integer
+// and the floored value.  t = u + 1.5*2^23 rounded toward -inf holds floor(u)
+// in its low mantissa bits.
+constexpr float FLOOR_MAGIC = 12582912.0f;  // 1.5 * 2^23
+__device__ __forceinline__ int floor_magic(float u, float& fl) {
+    const float t = __fadd_rd(u, FLOOR_MAGIC);
+    fl = t - FLOOR_MAGIC;
+    return __float_as_int(t) - __float_as_int(FLOOR_MAGIC);
+}
+
+}  // namespace sas
+
+// ---------------------------------------------------------------------------
+// Handle
+
+struct sas_geometry_s {
+    int device;
+    int P, C, Ns;
+    sas_signal sig;
+    // one slab: positions, attitude, levers, offsets, sensor positions, status
+    void* slab;
+    double* d_pos;     // [P][3]
+    double* d_att;     // [P][3]
+    double* d_lever;   // [1 + C][3]  (TX first)
+    double* d_off;     // [P][3]
+    double* d_tx;      // [P][3]
+    double* d_rx;      // [P][C][3]
+    uint32_t* d_status;
+    sas::FarrowCoef* d_coef;
+    double* d_fit_err;
+    int fit_valid;       // d_coef holds the Kaiser fit for (fit_taps, fit_beta)
+    int fit_taps;
+    double fit_beta;
+    // echo storage
+    void* d_echo;
+    float* d_scale;    // [P][C] (16-bit storage)
+    int echo_dtype;    // -1 = none
+    size_t echo_bytes;
+    // adjoint / VJP scratch (grown on demand)
+    void* d_scratch;
+    size_t scratch_bytes;
+    // failure-detection test hook
+    int debug_skip_copies;
+    int32_t debug_wait_ms;
+};
+
+namespace sas {
+
+struct ForwardArgs {
+    sas_geometry_t h;
+    sas_grid grid;
+    float2* image;
+    int dim3;
+    int accumulate;
+    cudaStream_t stream;
+};
+int launch_forward(const ForwardArgs& a);
+
+struct AdjointArgs {
+    sas_geometry_t h;
+    sas_grid grid;
+    const float2* grad_image;
+    float2* echo_adj;
+    double* grad_offsets;
+    cudaStream_t stream;
+};
+int launch_adjoint(const AdjointArgs& a);
+
+// Tensor map encoder obtained from the driver (no link-time libcuda dependency).
+int encode_echo_map(CUtensorMap* map, const void* base, int elem_bytes, int Ns, int rows, int box_len);
+
+int sm_count();
+
+}  // namespace sas

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every entry point the public
+header declares; argument checks run without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2101_05888_gb300 as sas
+from paper_2101_05888_gb300 import build as sas_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sas.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sas_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libsas():
+    sas_build.build()
+    return sas.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("sas_geometry_create", "sas_echo_upload", "sas_backproject_2d", "sas_backproject_3d",
+              "sas_backproject_adjoint"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(libsas):
+    for name in declared_functions():
+        assert hasattr(libsas, name), name
+        assert isinstance(getattr(libsas, name), ctypes._CFuncPtr)
+
+
+def test_python_binding_covers_the_header():
+    assert sorted(sas.ENTRY_POINTS) == declared_functions()
+    for name in declared_functions():
+        assert callable(getattr(sas, name))
+
+
+def test_version_and_error_string(libsas):
+    assert sas.sas_version() == 10000
+    assert isinstance(sas.sas_last_error(), str)
+
+
+def test_argument_errors_without_gpu(libsas):
+    h = ctypes.c_void_p()
+    assert libsas.sas_geometry_create(None, None, None, ctypes.byref(h)) == sas.SAS_ERR_ARG
+    assert "null" in sas.sas_last_error()
+    nav = sas.sas_nav(0, 1, 1, 1, 1, 1)
+    sig = sas.make_signal(1e5, 4e4, 1500.0, 0.0, 1024)
+    assert libsas.sas_geometry_create(ctypes.byref(nav), ctypes.byref(sig), None, ctypes.byref(h)) == sas.SAS_ERR_ARG
+    assert libsas.sas_backproject_2d(None, None, None, None, 0, None) == sas.SAS_ERR_ARG
+    assert libsas.sas_sharpness(None, 0, None, None, None) == sas.SAS_ERR_ARG
+    assert libsas.sas_debug_starve_copies(None, 1, 10) == sas.SAS_ERR_ARG

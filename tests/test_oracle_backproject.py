@@ -179,3 +179,14 @@ def test_offset_gradient_central_difference():
             om[i, a] -= h
             fd[i, a] = (S(op) - S(om)) / (2 * h)
     assert oracle.rel_l2(grad, fd) < 1e-6
+
+
+def test_complex64_echo_read_in_place():
+    """A complex64 echo gives the same image as its exact complex128 widening."""
+    pos, att, txl, rxl = _scene(P=4, C=2, seed=20)
+    tx, rx = oracle.sensor_positions(pos, att, txl, rxl)
+    e = _random_echo(4, 2, SIG.n_samples, 21).astype(np.complex64)
+    pix = _pixels(8, 8)
+    a = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix)
+    b = oracle.backproject(tx, rx, SIG, e.astype(np.complex128), 8, 4.0, pix)
+    assert np.array_equal(a, b)
