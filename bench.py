@@ -52,7 +52,15 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pings", type=int, default=0, help="profiling: fewer pings (same grid and tiles)")
     return ap.parse_args()
+
+
+def workload_of(args):
+    w = synth.workload(args.workload)
+    if args.pings:
+        w = synth.scaled(w, n_pings=args.pings)
+    return w
 
 
 def measured_peaks():
@@ -132,8 +140,10 @@ def cpu_baseline(w, nav, echo, seconds: float, rank_seed=0):
     idx = synth.random_pixel_indices(w.grid, 4096, seed=99 + rank_seed)
     g = w.grid
     pts = oracle.grid_index_points(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, idx)
-    # calibrate with a few pixels, then size the sample to the time budget
+    # warm the thread pool, calibrate with a few pixels, then size the sample
+    # to the time budget
     n0 = max(cores, 4)
+    oracle.backproject(tx, rx, sig, echo, 8, BETA, pts[:cores])
     t = time.perf_counter()
     oracle.backproject(tx, rx, sig, echo, 8, BETA, pts[:n0])
     dt0 = time.perf_counter() - t
@@ -151,7 +161,7 @@ def cpu_baseline(w, nav, echo, seconds: float, rank_seed=0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = synth.workload(args.workload)
+    w = workload_of(args)
     nav, echo = build_inputs(w)
     steps = []
     cb = None
@@ -189,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = synth.workload(args.workload)
+    w = workload_of(args)
     store = {"c64": sas.SAS_ECHO_C64, "f16": sas.SAS_ECHO_C32_F16, "bf16": sas.SAS_ECHO_C32_BF16}[args.echo]
     nav, echo = build_inputs(w)
     sig = sas.make_signal(synth.FC, synth.FS, synth.C_SOUND, w.t0, w.n_samples)
