@@ -189,6 +189,27 @@ int sas_backproject_adjoint(sas_geometry_t h, const sas_grid* grid, const sas_in
  * deterministic.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
 int sas_sharpness(const void* d_image, int64_t n, double* d_out3, void* d_grad, void* cuda_stream);
 
+/* sas_sharpness for callers that may not allocate device memory while they
+ * run (for example a vehicle-borne processor that reserves all of its GPU
+ * memory at start-up, or a host framework whose memory manager forbids
+ * cudaMalloc/cudaFree because they synchronise the device).  The paper has no
+ * counterpart; this is a service entry point of the library.
+ * Same arguments and outputs as sas_sharpness; the sums agree with it to FP64
+ * rounding (a different block split).  It allocates nothing: its per-block
+ * partial sums live in a 64 KiB array compiled into the library, which every
+ * GPU that loads the library holds until the process exits.
+ * Limits and rules:
+ *  - n <= 67,108,864 (16384 elements per block x 4096 blocks); larger n is
+ *    rejected with SAS_ERR_ARG before anything is launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    each call writes every slot it later reads, so nothing needs clearing.
+ *    Calls whose GPU work overlaps (different streams, no ordering) race on
+ *    the array and give wrong results: order them. */
+int sas_sharpness_static(const void* d_image, int64_t n, double* d_out3, void* d_grad, void* cuda_stream);
+
 /* Evaluates the interpolator's taps at n fractions f (device FP32 [n]) into
  * d_taps (device FP32 [n][taps]) exactly as the backprojection kernels apply
  * them, and writes to *d_max_err (device FP64, may be NULL) the largest

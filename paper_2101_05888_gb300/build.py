@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsas.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
-SOURCES = ["sas_api.cu", "tdbp_forward.cu", "tdbp_adjoint.cu", "sharpness.cu", "mlp.cu"]
+SOURCES = ["sas_api.cu", "tdbp_forward.cu", "tdbp_adjoint.cu", "sharpness.cu", "sharpness_static.cu", "mlp.cu"]
 HEADERS = ["sas_common.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
