@@ -218,6 +218,19 @@ int sas_sharpness_static(const void* d_image, int64_t n, double* d_out3, void* d
 int sas_interp_eval(const sas_interp* interp, const float* d_f, int64_t n, float* d_taps,
                     double* d_max_err, void* cuda_stream);
 
+/* Echo simulator (Eq. 1 for point scatterers, spreading loss omitted),
+ * complex baseband after matched filtering, using the handle's current sensor
+ * positions.  Adds to d_echo (device complex64 [P][C][Ns]):
+ *   e[i][c][k] += A q(t_k - tau) exp(-j 2 pi fc tau),  t_k = t0 + k/fs,
+ *   q(t) = (1 - |t|/T) sinc(B t (1 - |t|/T)) for |t| < T, else 0
+ * (matched-filter output of a linear FM pulse of length T = pulse_T and
+ * bandwidth B = bandwidth with a rectangular envelope, unit peak;
+ * pulse_T <= 0 gives sinc(B t)).  d_scat: device FP64 [n][5] =
+ * (x, y, z, Re A, Im A).  half_width > 0 limits each response to samples
+ * |k - (tau - t0) fs| <= half_width (0 = whole row). */
+int sas_simulate_points(sas_geometry_t h, const double* d_scat, int64_t n, double bandwidth, double pulse_T,
+                        int32_t half_width, void* d_echo, void* cuda_stream);
+
 /* ---- Learned interpolator (MLP 1 -> 64 -> 64 -> 8, GELU, FP16 weights) ----
  * Parameters are a flat FP32 master vector theta [SAS_MLP_NPARAMS] in the
  * order W1 [64][1], b1 [64], W2 [64][64] ([out][in]), b2 [64], W3 [8][64],

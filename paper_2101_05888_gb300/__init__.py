@@ -41,7 +41,7 @@ ENTRY_POINTS = [
     "sas_version", "sas_last_error", "sas_geometry_create", "sas_geometry_set_offsets",
     "sas_geometry_positions", "sas_geometry_destroy", "sas_echo_upload", "sas_echo_download",
     "sas_backproject_2d", "sas_backproject_3d", "sas_backproject_adjoint", "sas_sharpness",
-    "sas_sharpness_static",
+    "sas_sharpness_static", "sas_simulate_points",
     "sas_interp_eval", "sas_mlp_make_windows", "sas_mlp_workspace_bytes", "sas_mlp_loss_grad",
     "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_debug_starve_copies",
 ]
@@ -104,6 +104,7 @@ def lib():
                 "sas_backproject_adjoint": ([V, P(sas_grid), P(sas_interp), V, V, V, V], I),
                 "sas_sharpness": ([V, I64, V, V, V], I),
                 "sas_sharpness_static": ([V, I64, V, V, V], I),
+                "sas_simulate_points": ([V, V, I64, D, D, ctypes.c_int32, V, V], I),
                 "sas_interp_eval": ([P(sas_interp), V, I64, V, V, V], I),
                 "sas_mlp_make_windows": ([V, ctypes.c_int32, ctypes.c_int32, V, V, V, I64, D, V, V, V], I),
                 "sas_mlp_workspace_bytes": ([I64], I64),
@@ -209,6 +210,12 @@ def sas_sharpness_static(d_image, n: int, d_out3, d_grad=None, stream=None):
     """sas_sharpness without device allocation (built-in 64 KiB scratch,
     n <= 67,108,864; see include/sas.h)."""
     _check(lib().sas_sharpness_static(_ptr(d_image), n, _ptr(d_out3), _ptr(d_grad), _stream(stream)))
+
+
+def sas_simulate_points(h, d_scat, n: int, bandwidth: float, pulse_T: float, half_width: int, d_echo,
+                        stream=None):
+    _check(lib().sas_simulate_points(h, _ptr(d_scat), n, bandwidth, pulse_T, half_width, _ptr(d_echo),
+                                     _stream(stream)))
 
 
 def sas_interp_eval(interp: sas_interp, d_f, n: int, d_taps, d_max_err=None, stream=None):

@@ -1,0 +1,78 @@
+// Echo simulator: the forward model of Eq. 1 for point scatterers (spreading
+// loss omitted), complex baseband after matched filtering:
+//   e[i][c][k] += A q(t_k - tau) exp(-j 2 pi fc tau),  t_k = t0 + k / fs,
+//   tau = (|x_s - x_TX,i| + |x_s - x_RX,i,c|) / c,
+//   q(t) = (1 - |t|/T) sinc(B t (1 - |t|/T)),  |t| < T,
+// the autocorrelation of a linear FM pulse of length T and bandwidth B with a
+// rectangular envelope, normalised to a unit peak (T <= 0 selects sinc(B t)).
+// One block per (ping, channel) row; FP64 delay and carrier phase per
+// (row, scatterer); FP32 pulse samples accumulated with global atomics.
+#include "sas_common.cuh"
+
+namespace sas {
+namespace {
+
+__global__ void simulate_points_kernel(const double* __restrict__ tx, const double* __restrict__ rx, int C, int Ns,
+                                       double t0, double fs, double fc, double inv_c, const double* __restrict__ scat,
+                                       long long nscat, float B, float T, int half_width, float2* __restrict__ echo) {
+    const long long row = blockIdx.x;
+    const int i = (int)(row / C);
+    const double* t = tx + 3 * (size_t)i;
+    const double* r = rx + 3 * (size_t)row;
+    float2* e = echo + (size_t)row * Ns;
+    const float inv_fs = (float)(1.0 / fs);
+    for (long long s = 0; s < nscat; ++s) {
+        const double* q = scat + 5 * s;
+        const double ax = q[0] - t[0], ay = q[1] - t[1], az = q[2] - t[2];
+        const double bx = q[0] - r[0], by = q[1] - r[1], bz = q[2] - r[2];
+        const double tau = (sqrt(ax * ax + ay * ay + az * az) + sqrt(bx * bx + by * by + bz * bz)) * inv_c;
+        const double u = (tau - t0) * fs;
+        double ph = fc * tau;
+        ph -= floor(ph);
+        double sn, cs;
+        sincospi(-2.0 * ph, &sn, &cs);
+        const float Ar = (float)(q[3] * cs - q[4] * sn), Ai = (float)(q[3] * sn + q[4] * cs);
+        const long long kc = (long long)floor(u);
+        long long k0 = 0, k1 = Ns - 1;
+        if (half_width > 0) {
+            k0 = max(0LL, kc - half_width);
+            k1 = min((long long)Ns - 1, kc + half_width + 1);
+        }
+        const float frac = (float)(u - (double)kc);
+        for (long long k = k0 + threadIdx.x; k <= k1; k += blockDim.x) {
+            const float dt = ((float)(k - kc) - frac) * inv_fs;   // t_k - tau
+            float a;
+            if (T <= 0.f) {
+                const float x = B * dt;
+                a = (x == 0.f) ? 1.f : sinpif(x) / (3.14159265358979f * x);
+            } else {
+                const float ad = fabsf(dt);
+                if (ad >= T) continue;
+                const float rr = 1.f - ad / T;
+                const float x = B * dt * rr;
+                a = rr * ((x == 0.f) ? 1.f : sinpif(x) / (3.14159265358979f * x));
+            }
+            atomicAdd(e + k, make_float2(a * Ar, a * Ai));
+        }
+    }
+}
+
+}  // namespace
+}  // namespace sas
+
+using namespace sas;
+
+extern "C" int sas_simulate_points(sas_geometry_t h, const double* d_scat, int64_t n, double bandwidth, double pulse_T,
+                                   int32_t half_width, void* d_echo, void* stream) {
+    if (!h || !d_echo || n < 0 || (n > 0 && !d_scat) || !(bandwidth > 0) || half_width < 0) {
+        set_error("sas_simulate_points: bad argument");
+        return SAS_ERR_ARG;
+    }
+    if (n == 0) return SAS_OK;
+    const unsigned rows = (unsigned)((long long)h->P * h->C);
+    simulate_points_kernel<<<rows, 256, 0, (cudaStream_t)stream>>>(
+        h->d_tx, h->d_rx, h->C, h->Ns, h->sig.t0, h->sig.fs, h->sig.fc, 1.0 / h->sig.c, d_scat, n, (float)bandwidth,
+        (float)pulse_T, half_width, (float2*)d_echo);
+    SAS_CUDA(cudaGetLastError());
+    return SAS_OK;
+}

@@ -1,9 +1,208 @@
-// Adjoints of the backprojection (placeholder until the adjoint kernels land).
-#include "sas_common.cuh"
+// Adjoints of the backprojection on a pixel grid:
+//  * the linear adjoint B^H (image -> echo), the exact transpose of the
+//    forward sum:  e_adj[i][c][floor u + k] += w_k(frac u) exp(-j 2 pi fc tau) I(x);
+//  * dispatch of the offset gradient (tdbp_vjp.cu).
+//
+// Linear adjoint, one CTA per tile (warp 0 computes the FP64 reference terms
+// of 32 pairs at a time, warps 1..7 own 8 pixels each).  With the Farrow form
+// w_k(f) = sum_p coef[k][p] g^p the per-pixel work is a scatter of g^p v
+// (v = I(x) exp(-j 2 pi fc tau)) into accumulators A_p[floor u] in shared
+// memory; a transposed FIR e[floor u + k] += sum_p coef[k][p] A_p[floor u]
+// then adds each pair's segment to the echo with global atomics.
+#include "tdbp_core.cuh"
 
 namespace sas {
-int launch_adjoint(const AdjointArgs&) {
-    set_error("sas_backproject_adjoint: not built yet");
-    return SAS_ERR_UNSUPPORTED;
+
+int launch_offset_grad(sas_geometry_t h, const sas_grid& g, const float2* grad_image, double* grad_offsets,
+                       cudaStream_t st);
+
+namespace core {
+
+template <bool DIM3>
+__global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, const float2* __restrict__ img,
+                                                              float2* __restrict__ eadj, int Ns) {
+    using T = Tile<DIM3>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* A = reinterpret_cast<float2*>(smem);                    // [GROUP][npos][NP]
+    float* rec = reinterpret_cast<float*>(A + GROUP * p.npos * NP);  // [NREC][PAIRS]
+    float* coef_s = rec + NREC * PAIRS;                             // [TAPS][NP]
+    int* base_s = reinterpret_cast<int*>(coef_s + TAPS * NP);       // [PAIRS]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = p.tiles_x * p.tiles_y * p.tiles_z;
+    const int tile = blockIdx.x % ntiles;
+    const int split = blockIdx.x / ntiles;
+    const int tx0 = (tile % p.tiles_x) * T::TX;
+    const int ty0 = ((tile / p.tiles_x) % p.tiles_y) * T::TY;
+    const int tz0 = (tile / (p.tiles_x * p.tiles_y)) * T::TZ;
+    const int ping0 = min(p.P, split * p.pings_per_split);
+    const int ping1 = min(p.P, ping0 + p.pings_per_split);
+    const long long q0 = (long long)ping0 * p.C, q1 = (long long)ping1 * p.C;
+    const int nq = (int)(q1 - q0);
+    const double cx = tx0 + 0.5 * (T::TX - 1), cy = ty0 + 0.5 * (T::TY - 1), cz = tz0 + 0.5 * (T::TZ - 1);
+    const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = p.z0 + (DIM3 ? cz * p.dz : 0.0);
+    const int alen = GROUP * p.npos * NP;
+    const int span = p.npos + TAPS - 1;            // output samples per pair segment
+
+    for (int t = tid; t < alen; t += NTHREADS) A[t] = make_float2(0.f, 0.f);
+    if (tid < TAPS * NP) coef_s[tid] = (&p.coef->c[0][0])[tid];
+
+    const bool consumer = warp > 0;
+    const int ct = tid - 32;
+    float dxv = 0.f, dyv_c = 0.f, d2c = 0.f;
+    float dvar[PX], dT[PX];
+    float2 G[PX];
+    if (consumer) {
+        int lx, ly, lz;
+        T::pixel(ct, 0, lx, ly, lz);
+        dxv = (float)((tx0 + lx - cx) * p.dx);
+        dyv_c = (float)((ty0 + ly - cy) * p.dy);
+#pragma unroll
+        for (int s = 0; s < PX; ++s) {
+            T::pixel(ct, s, lx, ly, lz);
+            const float dxs = (float)((tx0 + lx - cx) * p.dx);
+            const float dys = (float)((ty0 + ly - cy) * p.dy);
+            const float dzs = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : 0.f;
+            dvar[s] = DIM3 ? dzs : dys;
+            d2c = DIM3 ? dxs * dxs + dys * dys : dxs * dxs;
+            dT[s] = 0.f;
+            const int ix = tx0 + lx, iy = ty0 + ly, iz = tz0 + lz;
+            G[s] = (ix < p.nx && iy < p.ny && iz < p.nz) ? img[((size_t)iz * p.ny + iy) * p.nx + ix]
+                                                        : make_float2(0.f, 0.f);
+        }
+    }
+    int prev_ping = -1;
+    const int nstages = (nq + PAIRS - 1) / PAIRS;
+    for (int k = 0; k < nstages; ++k) {
+        const long long qs = q0 + (long long)k * PAIRS;
+        __syncthreads();   // previous stage's records no longer in use
+        if (warp == 0 && qs + lane < q1) base_s[lane] = pair_record(p, X0, Y0, Z0, qs + lane, rec + lane);
+        __syncthreads();
+        float r[NHOLD];
+#pragma unroll
+        for (int f = 0; f < NHOLD; ++f) r[f] = rec[f * PAIRS + lane];
+        const int npairs = (int)min((long long)PAIRS, q1 - qs);
+        for (int g0 = 0; g0 < npairs; g0 += GROUP) {
+            if (consumer) {
+                for (int j = 0; j < GROUP && g0 + j < npairs; ++j) {
+                    const int pr = g0 + j;
+                    const int ping = (int)((qs + pr) / p.C);
+                    if (ping != prev_ping) {
+                        prev_ping = ping;
+                        const float tT0 = __shfl_sync(0xffffffffu, r[F_TX], pr);
+                        const float tT1 = __shfl_sync(0xffffffffu, r[F_TY], pr);
+                        const float tT2 = __shfl_sync(0xffffffffu, r[F_TZ], pr);
+                        const float nT2 = __shfl_sync(0xffffffffu, r[F_NT2], pr);
+                        const float nT = __shfl_sync(0xffffffffu, r[F_NT], pr);
+                        const float Ax = DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv;
+#pragma unroll
+                        for (int s = 0; s < PX; ++s) {
+                            const float d2 = fmaf(dvar[s], dvar[s], d2c);
+                            const float a = DIM3 ? fmaf(tT2, dvar[s], d2) + Ax : fmaf(tT1, dvar[s], d2) + Ax;
+                            const float sm = nT2 + a;
+                            dT[s] = a * rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nT));
+                        }
+                    }
+                    const float tRx = __shfl_sync(0xffffffffu, r[F_RX], pr);
+                    const float tRy = __shfl_sync(0xffffffffu, r[F_RY], pr);
+                    const float tRz = __shfl_sync(0xffffffffu, r[F_RZ], pr);
+                    const float nR2 = __shfl_sync(0xffffffffu, r[F_NR2], pr);
+                    const float nR = __shfl_sync(0xffffffffu, r[F_NR], pr);
+                    const float uf = __shfl_sync(0xffffffffu, r[F_UF], pr);
+                    const float phr = __shfl_sync(0xffffffffu, r[F_PH], pr);
+                    const float Ax = DIM3 ? fmaf(tRx, dxv, tRy * dyv_c) : tRx * dxv;
+                    float2* Aj = A + j * p.npos * NP;
+#pragma unroll
+                    for (int s = 0; s < PX; ++s) {
+                        const float d2 = fmaf(dvar[s], dvar[s], d2c);
+                        const float a = DIM3 ? fmaf(tRz, dvar[s], d2) + Ax : fmaf(tRy, dvar[s], d2) + Ax;
+                        const float sm = nR2 + a;
+                        const float D = fmaf(a, rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nR)), dT[s]);
+                        const float u = fmaf(D, p.fs_c, uf);
+                        const float ph = fmaf(D, p.fc_c, phr);
+                        float fl;
+                        const int di = floor_magic(u, fl);
+                        const float g = (u - fl) - 0.5f;
+                        const unsigned pos = min((unsigned)(di + p.U), (unsigned)(p.npos - 1));
+                        const float pt = __fadd_rn(ph, FLOOR_MAGIC) - FLOOR_MAGIC;
+                        float sn, cs;
+                        __sincosf((ph - pt) * 6.28318530717958647f, &sn, &cs);
+                        // v = G exp(-j phase)
+                        float vx = fmaf(G[s].x, cs, G[s].y * sn);
+                        float vy = fmaf(G[s].y, cs, -G[s].x * sn);
+                        float* dst = reinterpret_cast<float*>(Aj + pos * NP);
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            atomicAdd(dst + 2 * q, vx);
+                            atomicAdd(dst + 2 * q + 1, vy);
+                            vx *= g;
+                            vy *= g;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // transposed FIR and flush: out[t] = sum_m sum_p coef[m][p] A_p[t - m]
+            const int items = GROUP * span;
+            for (int it = tid; it < items; it += NTHREADS) {
+                const int j = it / span, t = it - j * span;
+                const int pr = g0 + j;
+                if (pr >= npairs) continue;
+                const float2* Aj = A + j * p.npos * NP;
+                float ox = 0.f, oy = 0.f;
+#pragma unroll
+                for (int m = 0; m < TAPS; ++m) {
+                    const int pos = t - m;
+                    if (pos < 0 || pos >= p.npos) continue;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const float c = coef_s[m * NP + q];
+                        const float2 v = Aj[pos * NP + q];
+                        ox = fmaf(c, v.x, ox);
+                        oy = fmaf(c, v.y, oy);
+                    }
+                }
+                const long long idx = (long long)base_s[pr] + t;
+                if (idx >= 0 && idx < Ns && (ox != 0.f || oy != 0.f))
+                    atomicAdd(eadj + (size_t)(qs + pr) * Ns + idx, make_float2(ox, oy));
+            }
+            __syncthreads();
+            for (int t = tid; t < alen; t += NTHREADS) A[t] = make_float2(0.f, 0.f);
+        }
+    }
 }
+
+}  // namespace core
+
+static int launch_linear_adjoint(sas_geometry_t h, const sas_grid& g, const float2* img, float2* eadj,
+                                 cudaStream_t st) {
+    const int dim3 = g.nz > 1;
+    core::Setup S;
+    int rc = core::prepare(h, g, dim3, 2LL * sm_count(), S, false);
+    if (rc != SAS_OK) return rc;
+    SAS_CUDA(cudaMemsetAsync(eadj, 0, sizeof(float2) * (size_t)h->P * h->C * h->Ns, st));
+    const size_t smem = sizeof(float2) * core::GROUP * S.prm.npos * NP + sizeof(float) * core::NREC * core::PAIRS +
+                        sizeof(float) * TAPS * NP + sizeof(int) * core::PAIRS;
+    if (dim3) {
+        auto k = core::adjoint_kernel<true>;
+        SAS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<S.blocks, core::NTHREADS, smem, st>>>(S.prm, img, eadj, h->Ns);
+    } else {
+        auto k = core::adjoint_kernel<false>;
+        SAS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k<<<S.blocks, core::NTHREADS, smem, st>>>(S.prm, img, eadj, h->Ns);
+    }
+    SAS_CUDA(cudaGetLastError());
+    return SAS_OK;
+}
+
+int launch_adjoint(const AdjointArgs& a) {
+    if (a.grad_offsets) {
+        int rc = launch_offset_grad(a.h, a.grid, a.grad_image, a.grad_offsets, a.stream);
+        if (rc != SAS_OK) return rc;
+    }
+    if (a.echo_adj) return launch_linear_adjoint(a.h, a.grid, a.grad_image, a.echo_adj, a.stream);
+    return SAS_OK;
+}
+
 }  // namespace sas
