@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pings", type=int, default=0, help="profiling: fewer pings (same grid and tiles)")
+    ap.add_argument("--beam-deg", type=float, default=0.0,
+                    help="azimuth beam width [deg] (ray culling on); 0 = omnidirectional")
     return ap.parse_args()
 
 
@@ -163,19 +165,21 @@ def run_reference(args, rank, world):
         return
     w = workload_of(args)
     nav, echo = build_inputs(w)
-    steps = []
+    steps, walls = [], []
     cb = None
     per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
     for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
         r = cpu_baseline(w, nav, echo, per_step if k >= args.warmup else 1.0, rank_seed=k)
         if k >= args.warmup:
             steps.append(r["value"])
+            walls.append(time.perf_counter() - t)
             cb = r
     value = statistics.median(steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(w, args), "ms_per_step": None,
+            "config": config_of(w, args), "ms_per_step": 1e3 * statistics.median(walls),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -188,9 +192,17 @@ def config_of(w, args):
     return {"workload": w.name, "pings": w.n_pings, "rx": w.n_rx, "samples": w.n_samples,
             "pixels": "%dx%dx%d" % (g.nx, g.ny, g.nz), "pixel_m": g.dx, "taps": 8,
             "interp": "kaiser_sinc beta=%g (Farrow degree 7)" % BETA, "echo": args.echo,
-            "updates_per_step": w.updates, "l2": "inputs larger than L2 (echo %.2f GB, L2 0.13 GB)"
-            % (w.n_pings * w.n_rx * w.n_samples * (8 if args.echo == "c64" else 4) / 1e9),
-            "parallelism": "replicas"}
+            "updates_per_step": w.updates, "l2": l2_note(w, args), "parallelism": "replicas",
+            **({"beam_deg": args.beam_deg,
+                "beam_note": "value counts every pixel.ping.channel term of the image, culled ones included; "
+                             "roofline.achieved counts the updates of the computed (not culled) blocks"}
+               if args.beam_deg > 0 else {})}
+
+
+def l2_note(w, args):
+    echo_gb = w.n_pings * w.n_rx * w.n_samples * (8 if args.echo == "c64" else 4) / 1e9
+    rel = "larger" if echo_gb > 0.129 else "smaller"
+    return "inputs %s than L2, no flush between steps (echo %.2f GB, L2 0.129 GB)" % (rel, echo_gb)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -206,6 +218,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     geom = sas.Geometry.from_nav(nav, sig)
     geom.upload_echo(echo, store)
+    if args.beam_deg > 0:
+        geom.set_beam(np.deg2rad(args.beam_deg), 1)
     grid = sas.grid_from(w.grid)
     interp = sas.kaiser(BETA)
     image = torch.empty((w.grid.nz, w.grid.ny, w.grid.nx), dtype=torch.complex64, device=dev)
@@ -218,6 +232,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step()
     geom.sync_status()
+    geom.cull_stats(reset=True)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -239,6 +254,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     geom.sync_status()
+    cand, computed, edge = (v / args.steps for v in geom.cull_stats(reset=True))
+    tx_, ty_, tz_ = (8, 28, 8) if w.grid.nz > 1 else (56, 32, 1)     # pixels per CTA tile
+    computed_updates = computed * tx_ * ty_ * tz_
     total_ms = t_all0.elapsed_time(t_all1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     if world > 1:
@@ -254,7 +272,8 @@ def run_ours(args, rank, world, local_rank):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or 2070.0)
     peak = props.multi_processor_count * sm_max * 1e6 * UPDATES_PER_CLK_PER_SM / 1e9
-    achieved = w.updates / (statistics.mean(launch_ms) / 1e3) / 1e9
+    work = computed_updates if args.beam_deg > 0 else w.updates
+    achieved = work / (statistics.mean(launch_ms) / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
             "traffic": None,
             "peak_basis": "%d SMs x %.0f MHz x %.0f updates/clk/SM (FP32 128 lanes / 32 ops, SFU 16 lanes / 4 ops)"
@@ -296,6 +315,10 @@ def run_ours(args, rank, world, local_rank):
                 "data": "synthetic (seeded band-limited Gaussian echo rows, stripmap nav with sway/heave/yaw)",
                 "config": config_of(w, args), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
                 "clocks": clk, "gpu_launches": args.steps,
+                **({"cull": {"blocks_candidate": cand, "blocks_computed": computed, "blocks_beam_edge": edge,
+                             "computed_fraction": computed / max(cand, 1.0),
+                             "updates_computed": computed_updates, "updates_dense": w.updates}}
+                   if args.beam_deg > 0 else {}),
                 "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms), "max": max(launch_ms)}}
         print(json.dumps(line), flush=True)
     geom.close()

@@ -134,6 +134,20 @@ int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, void* cuda_st
 int sas_geometry_set_offsets(sas_geometry_t h, const double* offsets, int on_device,
                              void* cuda_stream);
 
+/* Beam field of view (Sec. II-C: pixels outside the transmit or receive beam
+ * are not integrated).  Every transducer gets an azimuth beam of full width
+ * beam_width [rad] centred on the vehicle's side axis (side = +1: body +y,
+ * starboard; -1: port); elevation is unrestricted.  Sensor s of ping i sees
+ * pixel x iff b = R_i^T (x - x_s) has side b_y > 0 and
+ * |b_x| <= tan(beam_width/2) side b_y; a (ping, channel) term is integrated
+ * iff the transmitter and that receiver both see x.  Applies to every later
+ * backprojection and adjoint call; beam_width <= 0 switches it off (the
+ * default).  The kernels skip (ping, channel, tile) blocks that a
+ * conservative test of the tile corners proves invisible (ray culling) and
+ * test pixels individually only in tiles on a beam edge, so the result equals
+ * the per-pixel definition.  Errors: SAS_ERR_ARG (beam_width >= pi, bad side). */
+int sas_geometry_set_beam(sas_geometry_t h, double beam_width, int side);
+
 /* Copies the current sensor positions to device arrays d_tx [P][3] and
  * d_rx [P][C][3] (FP64).  Either may be NULL. */
 int sas_geometry_positions(sas_geometry_t h, double* d_tx, double* d_rx, void* cuda_stream);
@@ -270,6 +284,16 @@ int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, float* d_tabl
 /* Waits for the stream, then reports and clears the handle's device status:
  * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check. */
 int sas_sync_status(sas_geometry_t h, void* cuda_stream);
+
+/* Ray-culling counts (Sec. II-C: blocks of pixels outside the beams are
+ * pruned before the per-pixel test) accumulated by the forward and
+ * offset-gradient backprojections of this handle since the last reset:
+ * out[0] = candidate (ping, channel, image tile) blocks, out[1] = blocks
+ * computed (not culled), out[2] = computed blocks on a beam edge, whose pixels
+ * are tested one by one.  With no beam all candidates are computed and none
+ * is on an edge.  Waits for the stream; reset != 0 zeroes the counts after
+ * reading.  out: host array of 3.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_cull_stats(sas_geometry_t h, long long* out, int reset, void* cuda_stream);
 
 /* Test hook for failure detection: when skip != 0 the next backprojection
  * launches do not issue their bulk copies and use a wait limit of

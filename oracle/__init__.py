@@ -59,9 +59,11 @@ def lib():
             L.oracle_bessel_i1_over_x.argtypes = [D]
             L.oracle_bessel_i1_over_x.restype = D
             L.oracle_kaiser_sinc_weights.argtypes = [D, I, D, P, P]
-            L.oracle_backproject.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, I]
-            L.oracle_backproject_adjoint.argtypes = [I, I, P, P, D, D, D, D, I, I, D, Lg, P, P, P, I]
-            L.oracle_vjp_offsets.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, P, I]
+            L.oracle_backproject.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, P, D, I, I]
+            L.oracle_backproject_beam_split.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, D, I, D,
+                                                        P, P, I]
+            L.oracle_backproject_adjoint.argtypes = [I, I, P, P, D, D, D, D, I, I, D, Lg, P, P, P, P, D, I, I]
+            L.oracle_vjp_offsets.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, P, P, D, I, I]
             L.oracle_sharpness.argtypes = [Lg, P, P, P]
             L.oracle_lfm_compressed_pulse.argtypes = [D, D, D]
             L.oracle_lfm_compressed_pulse.restype = D
@@ -164,9 +166,12 @@ def _echo_c128(echo) -> np.ndarray:
     return e
 
 
-def backproject(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, nthreads: int = 0):
+def backproject(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, nthreads: int = 0,
+                att=None, beam_width: float = 0.0, side: int = 1):
     """I(x) at the given pixels [n,3]; returns complex128 [n].  A complex64
-    echo is read in place (widened exactly to FP64), others as complex128."""
+    echo is read in place (widened exactly to FP64), others as complex128.
+    att [P,3] and beam_width (full azimuth width, radians) > 0 apply the
+    beam field of view looking to ``side`` (+1 starboard, -1 port)."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
     if isinstance(echo, np.ndarray) and echo.dtype == np.complex64 and echo.flags.c_contiguous:
         e, f32 = echo, 1
@@ -175,34 +180,71 @@ def backproject(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, nthreads
     P, C = tx.shape[0], rx.shape[1]
     assert e.shape == (P, C, sig.n_samples)
     out = np.zeros((pix.shape[0], 2))
+    a = None if att is None else _f64(att).reshape(P, 3)
+    btan = float(np.tan(0.5 * beam_width)) if (beam_width and beam_width > 0) else 0.0
     lib().oracle_backproject(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
                              _p(e), f32, int(taps), float(beta), pix.shape[0], _p(pix), _p(out),
-                             int(nthreads))
+                             None if a is None else _p(a), btan, int(side), int(nthreads))
     return out[:, 0] + 1j * out[:, 1]
 
 
-def backproject_adjoint(tx, rx, sig: Signal, img, taps: int, beta: float, pix, nthreads: int = 0):
+def backproject_beam_split(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, att, beam_width: float,
+                           side: int = 1, eps: float = 2e-6, nthreads: int = 0):
+    """Beam-limited image split by decision margin: (sure [n] complex128,
+    amb [n] float64).  ``sure`` sums the terms whose transmitter and receiver
+    see the pixel by a relative margin above eps, ``amb`` the magnitudes of
+    the terms within eps of a beam edge; any beam test accurate to eps gives
+    an image I with |I - sure| <= amb pixel by pixel."""
+    tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
+    if isinstance(echo, np.ndarray) and echo.dtype == np.complex64 and echo.flags.c_contiguous:
+        e, f32 = echo, 1
+    else:
+        e, f32 = _echo_c128(echo), 0
+    P, C = tx.shape[0], rx.shape[1]
+    assert e.shape == (P, C, sig.n_samples) and beam_width > 0
+    out = np.zeros((pix.shape[0], 2))
+    amb = np.zeros(pix.shape[0])
+    a = _f64(att).reshape(P, 3)
+    lib().oracle_backproject_beam_split(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
+                                        _p(e), f32, int(taps), float(beta), pix.shape[0], _p(pix), _p(a),
+                                        float(np.tan(0.5 * beam_width)), int(side), float(eps), _p(out), _p(amb),
+                                        int(nthreads))
+    return out[:, 0] + 1j * out[:, 1], amb
+
+
+def _beam_args(att, beam_width, P):
+    a = None if att is None else _f64(att).reshape(P, 3)
+    btan = float(np.tan(0.5 * beam_width)) if (beam_width and beam_width > 0) else 0.0
+    return a, btan
+
+
+def backproject_adjoint(tx, rx, sig: Signal, img, taps: int, beta: float, pix, nthreads: int = 0,
+                        att=None, beam_width: float = 0.0, side: int = 1):
     """Linear adjoint: image values at pixels -> echo [P,C,Ns] complex128."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
     im = np.ascontiguousarray(np.asarray(img, dtype=np.complex128).reshape(-1))
     P, C = tx.shape[0], rx.shape[1]
     out = np.zeros((P, C, sig.n_samples), dtype=np.complex128)
+    a, btan = _beam_args(att, beam_width, P)
     lib().oracle_backproject_adjoint(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0,
                                      sig.n_samples, int(taps), float(beta), pix.shape[0], _p(pix),
-                                     _p(im), _p(out), int(nthreads))
+                                     _p(im), _p(out), None if a is None else _p(a), btan, int(side),
+                                     int(nthreads))
     return out
 
 
-def vjp_offsets(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, g, nthreads: int = 0):
+def vjp_offsets(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, g, nthreads: int = 0,
+                att=None, beam_width: float = 0.0, side: int = 1):
     """dL/d(dp) [P,3] given g = dL/dI* at the pixels."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
     e = _echo_c128(echo)
     gg = np.ascontiguousarray(np.asarray(g, dtype=np.complex128).reshape(-1))
     P, C = tx.shape[0], rx.shape[1]
     out = np.zeros((P, 3))
+    a, btan = _beam_args(att, beam_width, P)
     lib().oracle_vjp_offsets(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
                              _p(e), int(taps), float(beta), pix.shape[0], _p(pix), _p(gg),
-                             _p(out), int(nthreads))
+                             _p(out), None if a is None else _p(a), btan, int(side), int(nthreads))
     return out
 
 

@@ -59,8 +59,21 @@ def weights(f, taps, beta):
     return v / v.sum(axis=-1, keepdims=True)
 
 
-def backproject(tx, rx, fc, fs, c, t0, echo, taps, beta, pix):
-    """Direct broadcast evaluation; pix [n,3], echo [P,C,Ns]; returns [n]."""
+def beam_mask(att, tx, rx, pix, beam_width, side):
+    """[n,P,C] boolean: both the transmitter and the receiver see the pixel,
+    i.e. the azimuth arctan2(b_x, side b_y) of the body-frame vector lies
+    within +-beam_width/2 (and in front of the side axis)."""
+    Rs = np.stack([attitude_matrix(*a) for a in att])                         # [P,3,3]
+    def sees(sensor):                                                           # sensor [P,(C,)3]
+        v = pix[:, None, None, :] - (sensor[None, :, None, :] if sensor.ndim == 2 else sensor[None])
+        b = np.einsum("pji,npcj->npci", Rs, v)                                 # R^T v
+        az = np.arctan2(b[..., 0], side * b[..., 1])
+        return (side * b[..., 1] > 0) & (np.abs(az) <= 0.5 * beam_width)
+    return sees(tx) & sees(rx)
+
+
+def terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix):
+    """Every term of the sum: [n,P,C] complex."""
     pix = np.asarray(pix, dtype=np.float64)
     P, C, Ns = echo.shape
     rt = np.linalg.norm(pix[:, None, :] - tx[None, :, :], axis=-1)                 # [n,P]
@@ -77,4 +90,13 @@ def backproject(tx, rx, fc, fs, c, t0, echo, taps, beta, pix):
     cc = np.arange(C)[None, None, :, None]
     samples = np.where(valid, echo[ii, cc, jc], 0.0)
     s = (weights(f, taps, beta) * samples).sum(-1)
-    return (s * np.exp(2j * np.pi * fc * tau)).sum(axis=(1, 2))
+    return s * np.exp(2j * np.pi * fc * tau)
+
+
+def backproject(tx, rx, fc, fs, c, t0, echo, taps, beta, pix, mask=None):
+    """Direct broadcast evaluation; pix [n,3], echo [P,C,Ns]; optional mask
+    [n,P,C] of the terms that count; returns [n]."""
+    t = terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix)
+    if mask is not None:
+        t = np.where(mask, t, 0.0)
+    return t.sum(axis=(1, 2))

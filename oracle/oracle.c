@@ -208,49 +208,148 @@ static void delay_eval(const double* x, const double* t, const double* r, double
     o->f = o->u - fl;
 }
 
+/* Beam field of view (Sec. II-C: each pixel is tested against the
+ * transmit and receive beams).  This build's reading: every transducer has
+ * an azimuth beam of full width theta centred on the vehicle's side axis
+ * (body +y for side = +1, starboard; -y for side = -1, port), elevation
+ * unrestricted.  Sensor s of ping i sees x iff b = R_i^T (x - x_s) satisfies
+ * side * b_y > 0 and |b_x| <= tan(theta/2) * side * b_y.  A (ping, channel)
+ * term counts iff the transmitter and that receiver both see x.
+ * beam_tan = tan(theta/2) <= 0 switches the test off.
+ * Pinned by: the NumPy restatement (arctan2 of body-frame vectors) in
+ * brute.py, and beam off = unmasked sum.                                  */
+static int sensor_sees(const double* R, const double* x, const double* s, double beam_tan, int side) {
+    const double v0 = x[0] - s[0], v1 = x[1] - s[1], v2 = x[2] - s[2];
+    const double bx = R[0] * v0 + R[3] * v1 + R[6] * v2;   /* R^T v, row 0 = column 0 of R */
+    const double by = (R[1] * v0 + R[4] * v1 + R[7] * v2) * (double)side;
+    return by > 0.0 && fabs(bx) <= beam_tan * by;
+}
+
+/* One term of the backprojection sum: pixel x, ping i, channel ch
+ * (Sec. II-A): s = sum_m w_m(f) e[i][ch][j0 + k_m] (zero outside the row)
+ * rotated by exp(+j 2 pi fc tau).  w: scratch of at least taps doubles.      */
+static void term_eval(const double* x, int i, int ch, int C, const double* tx, const double* rx, double fc,
+                      double fs, double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
+                      double beta, double* w, double* tre, double* tim) {
+    oracle_delay d;
+    delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
+    oracle_kaiser_sinc_weights(d.f, taps, beta, w, NULL);
+    const size_t row = 2 * ((size_t)i * C + ch) * (size_t)Ns;
+    double sr = 0.0, si = 0.0;
+    for (int m = 0; m < taps; ++m) {
+        const long j = d.j0 + (m - taps / 2 + 1);
+        if (j < 0 || j >= Ns) continue;
+        /* complex64 input is widened exactly to FP64 */
+        const double er = echo_f32 ? (double)((const float*)echo)[row + 2 * j] : ((const double*)echo)[row + 2 * j];
+        const double ei = echo_f32 ? (double)((const float*)echo)[row + 2 * j + 1]
+                                   : ((const double*)echo)[row + 2 * j + 1];
+        sr += w[m] * er;
+        si += w[m] * ei;
+    }
+    double ph = fc * d.tau;
+    ph -= floor(ph);
+    const double cs = cos(2.0 * ORACLE_PI * ph), sn = sin(2.0 * ORACLE_PI * ph);
+    *tre = sr * cs - si * sn;
+    *tim = sr * sn + si * cs;
+}
+
 /* Backprojection (Sec. II-A, Eq. 1 inverted per pixel; pixels independent):
  *   I(x) = sum_i sum_c sum_m w_m(f) e[i][c][j0 + k_m] exp(+j 2 pi fc tau_ic(x))
  * echo: [P][C][Ns] complex interleaved (re, im), FP64 or (echo_f32 = 1) FP32;
- * pix: [npix][3]; out: [npix][2].
+ * pix: [npix][3]; out: [npix][2].  att [P][3] (roll, pitch, yaw) with
+ * beam_tan > 0 applies the beam field of view (see sensor_sees).
  * Pinned by: NumPy brute force (brute.py) to 1e-12; linearity in the echo;
  * translation invariance; closed-form point-scatterer response (peak at the
  * scatterer, |I| = A P C within the interpolator error, phase = arg A).    */
 void oracle_backproject(int P, int C, const double* tx, const double* rx, double fc, double fs,
                         double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
-                        double beta, long npix, const double* pix, double* out, int nthreads) {
+                        double beta, long npix, const double* pix, double* out,
+                        const double* att, double beam_tan, int side, int nthreads) {
     set_threads(nthreads);
+    const int beam = att != NULL && beam_tan > 0.0;
 #pragma omp parallel for schedule(dynamic, 8)
     for (long p = 0; p < npix; ++p) {
         const double* x = pix + 3 * p;
         double acc_re = 0.0, acc_im = 0.0;
         double w[64];
         for (int i = 0; i < P; ++i) {
+            double R[9];
+            if (beam) {
+                oracle_attitude_matrix(att[3 * i], att[3 * i + 1], att[3 * i + 2], R);
+                if (!sensor_sees(R, x, tx + 3 * i, beam_tan, side)) continue;
+            }
             for (int ch = 0; ch < C; ++ch) {
-                oracle_delay d;
-                delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
-                oracle_kaiser_sinc_weights(d.f, taps, beta, w, NULL);
-                const size_t row = 2 * ((size_t)i * C + ch) * (size_t)Ns;
-                double sr = 0.0, si = 0.0;
-                for (int m = 0; m < taps; ++m) {
-                    const long j = d.j0 + (m - taps / 2 + 1);
-                    if (j < 0 || j >= Ns) continue;
-                    /* complex64 input is widened exactly to FP64 */
-                    const double er = echo_f32 ? (double)((const float*)echo)[row + 2 * j]
-                                               : ((const double*)echo)[row + 2 * j];
-                    const double ei = echo_f32 ? (double)((const float*)echo)[row + 2 * j + 1]
-                                               : ((const double*)echo)[row + 2 * j + 1];
-                    sr += w[m] * er;
-                    si += w[m] * ei;
-                }
-                double ph = fc * d.tau;
-                ph -= floor(ph);
-                const double cs = cos(2.0 * ORACLE_PI * ph), sn = sin(2.0 * ORACLE_PI * ph);
-                acc_re += sr * cs - si * sn;
-                acc_im += sr * sn + si * cs;
+                if (beam && !sensor_sees(R, x, rx + 3 * ((size_t)i * C + ch), beam_tan, side)) continue;
+                double tre, tim;
+                term_eval(x, i, ch, C, tx, rx, fc, fs, c, t0, Ns, echo, echo_f32, taps, beta, w, &tre, &tim);
+                acc_re += tre;
+                acc_im += tim;
             }
         }
         out[2 * p] = acc_re;
         out[2 * p + 1] = acc_im;
+    }
+}
+
+/* Beam decision of one sensor with a relative margin eps: +1 when the
+ * decision "sees" of sensor_sees holds with both of its inequalities
+ * satisfied by more than eps |b| (distances in the (b_x, b_y) plane), -1 when
+ * one of them fails by more than eps |b|, 0 otherwise (the decision could
+ * flip under a relative perturbation of the geometry of order eps).        */
+static int sensor_class(const double* R, const double* x, const double* s, double beam_tan, int side,
+                        double eps) {
+    const double v0 = x[0] - s[0], v1 = x[1] - s[1], v2 = x[2] - s[2];
+    const double bx = R[0] * v0 + R[3] * v1 + R[6] * v2;
+    const double by = (R[1] * v0 + R[4] * v1 + R[7] * v2) * (double)side;
+    const double nb = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+    const double m1 = by / nb;
+    const double m2 = (beam_tan * by - fabs(bx)) / (sqrt(1.0 + beam_tan * beam_tan) * nb);
+    if (m1 > eps && m2 > eps) return 1;
+    if (m1 < -eps || m2 < -eps) return -1;
+    return 0;
+}
+
+/* Backprojection with the beam field of view split by decision margin:
+ * out_sure [npix][2] sums the terms whose transmitter and receiver both see
+ * the pixel by more than eps (relative), amb [npix] sums |term| over the
+ * terms whose decision is within eps of flipping (neither surely in nor
+ * surely out).  Any evaluation of the beam test whose relative error is
+ * below eps gives sum(out_sure) + a subset of the ambiguous terms, so
+ * |I - out_sure| <= amb pixel by pixel.  Requires att and beam_tan > 0.
+ * Pinned by: NumPy restatement of the margins (brute.py); eps -> 0 gives
+ * oracle_backproject and amb = 0.                                          */
+void oracle_backproject_beam_split(int P, int C, const double* tx, const double* rx, double fc, double fs,
+                                   double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
+                                   double beta, long npix, const double* pix, const double* att,
+                                   double beam_tan, int side, double eps, double* out_sure, double* amb,
+                                   int nthreads) {
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long p = 0; p < npix; ++p) {
+        const double* x = pix + 3 * p;
+        double acc_re = 0.0, acc_im = 0.0, acc_amb = 0.0;
+        double w[64];
+        for (int i = 0; i < P; ++i) {
+            double R[9];
+            oracle_attitude_matrix(att[3 * i], att[3 * i + 1], att[3 * i + 2], R);
+            const int kt = sensor_class(R, x, tx + 3 * i, beam_tan, side, eps);
+            if (kt < 0) continue;
+            for (int ch = 0; ch < C; ++ch) {
+                const int kr = sensor_class(R, x, rx + 3 * ((size_t)i * C + ch), beam_tan, side, eps);
+                if (kr < 0) continue;
+                double tre, tim;
+                term_eval(x, i, ch, C, tx, rx, fc, fs, c, t0, Ns, echo, echo_f32, taps, beta, w, &tre, &tim);
+                if (kt > 0 && kr > 0) {
+                    acc_re += tre;
+                    acc_im += tim;
+                } else {
+                    acc_amb += sqrt(tre * tre + tim * tim);
+                }
+            }
+        }
+        out_sure[2 * p] = acc_re;
+        out_sure[2 * p + 1] = acc_im;
+        amb[p] = acc_amb;
     }
 }
 
@@ -262,16 +361,22 @@ void oracle_backproject(int P, int C, const double* tx, const double* rx, double
 void oracle_backproject_adjoint(int P, int C, const double* tx, const double* rx, double fc,
                                 double fs, double c, double t0, int Ns, int taps, double beta,
                                 long npix, const double* pix, const double* img, double* echo_adj,
-                                int nthreads) {
+                                const double* att, double beam_tan, int side, int nthreads) {
     set_threads(nthreads);
     const long rows = (long)P * C;
+    const int beam = att != NULL && beam_tan > 0.0;
 #pragma omp parallel for schedule(dynamic, 1)
     for (long r = 0; r < rows; ++r) {
         const int i = (int)(r / C), ch = (int)(r % C);
         double* row = echo_adj + 2 * (size_t)r * (size_t)Ns;
         memset(row, 0, sizeof(double) * 2 * (size_t)Ns);
         double w[64];
+        double R[9];
+        if (beam) oracle_attitude_matrix(att[3 * i], att[3 * i + 1], att[3 * i + 2], R);
         for (long p = 0; p < npix; ++p) {
+            if (beam && !(sensor_sees(R, pix + 3 * p, tx + 3 * i, beam_tan, side) &&
+                          sensor_sees(R, pix + 3 * p, rx + 3 * ((size_t)i * C + ch), beam_tan, side)))
+                continue;
             oracle_delay d;
             delay_eval(pix + 3 * p, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
             oracle_kaiser_sinc_weights(d.f, taps, beta, w, NULL);
@@ -304,15 +409,20 @@ void oracle_backproject_adjoint(int P, int C, const double* tx, const double* rx
 void oracle_vjp_offsets(int P, int C, const double* tx, const double* rx, double fc, double fs,
                         double c, double t0, int Ns, const double* echo, int taps, double beta,
                         long npix, const double* pix, const double* g, double* grad,
-                        int nthreads) {
+                        const double* att, double beam_tan, int side, int nthreads) {
     set_threads(nthreads);
+    const int beam = att != NULL && beam_tan > 0.0;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < P; ++i) {
         double gx = 0.0, gy = 0.0, gz = 0.0;
         double w[64], dw[64];
+        double R[9];
+        if (beam) oracle_attitude_matrix(att[3 * i], att[3 * i + 1], att[3 * i + 2], R);
         for (long p = 0; p < npix; ++p) {
             const double* x = pix + 3 * p;
+            if (beam && !sensor_sees(R, x, tx + 3 * i, beam_tan, side)) continue;
             for (int ch = 0; ch < C; ++ch) {
+                if (beam && !sensor_sees(R, x, rx + 3 * ((size_t)i * C + ch), beam_tan, side)) continue;
                 oracle_delay d;
                 delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
                 oracle_kaiser_sinc_weights(d.f, taps, beta, w, dw);

@@ -38,12 +38,13 @@ SAS_INTERP_TABLE = 1
 SAS_MLP_NPARAMS = 4808
 
 ENTRY_POINTS = [
-    "sas_version", "sas_last_error", "sas_geometry_create", "sas_geometry_set_offsets",
+    "sas_version", "sas_last_error", "sas_geometry_create", "sas_geometry_set_offsets", "sas_geometry_set_beam",
     "sas_geometry_positions", "sas_geometry_destroy", "sas_echo_upload", "sas_echo_download",
     "sas_backproject_2d", "sas_backproject_3d", "sas_backproject_adjoint", "sas_sharpness",
     "sas_sharpness_static", "sas_simulate_points",
     "sas_interp_eval", "sas_mlp_make_windows", "sas_mlp_workspace_bytes", "sas_mlp_loss_grad",
-    "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_debug_starve_copies",
+    "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_cull_stats",
+    "sas_debug_starve_copies",
 ]
 
 
@@ -95,6 +96,7 @@ def lib():
                 "sas_last_error": ([], ctypes.c_char_p),
                 "sas_geometry_create": ([P(sas_nav), P(sas_signal), V, P(V)], I),
                 "sas_geometry_set_offsets": ([V, V, I, V], I),
+                "sas_geometry_set_beam": ([V, D, I], I),
                 "sas_geometry_positions": ([V, V, V, V], I),
                 "sas_geometry_destroy": ([V], I),
                 "sas_echo_upload": ([V, V, I, I, V], I),
@@ -112,6 +114,7 @@ def lib():
                 "sas_mlp_adam": ([V, V, V, V, ctypes.c_int32, F, F, F, F, V], I),
                 "sas_interp_tabulate_mlp": ([V, ctypes.c_int32, V, V], I),
                 "sas_sync_status": ([V, V], I),
+                "sas_cull_stats": ([V, ctypes.POINTER(ctypes.c_longlong), I, V], I),
                 "sas_debug_starve_copies": ([V, I, ctypes.c_int32], I),
             }
             for name, (args, res) in sig.items():
@@ -168,6 +171,10 @@ def sas_geometry_create(nav: sas_nav, sig: sas_signal, stream=None) -> int:
 
 def sas_geometry_set_offsets(h, offsets, on_device: int, stream=None):
     _check(lib().sas_geometry_set_offsets(h, _ptr(offsets), on_device, _stream(stream)))
+
+
+def sas_geometry_set_beam(h, beam_width: float, side: int = 1):
+    _check(lib().sas_geometry_set_beam(h, float(beam_width), int(side)))
 
 
 def sas_geometry_positions(h, d_tx, d_rx, stream=None):
@@ -251,6 +258,13 @@ def sas_sync_status(h, stream=None):
     _check(lib().sas_sync_status(h, _stream(stream)))
 
 
+def sas_cull_stats(h, reset: int = 0, stream=None):
+    """(candidate, computed, beam-edge) (ping, channel, tile) block counts."""
+    out = (ctypes.c_longlong * 3)()
+    _check(lib().sas_cull_stats(h, out, reset, _stream(stream)))
+    return tuple(int(v) for v in out)
+
+
 def sas_debug_starve_copies(h, skip: int, wait_limit_ms: int):
     _check(lib().sas_debug_starve_copies(h, skip, wait_limit_ms))
 
@@ -319,6 +333,10 @@ class Geometry:
             a = np.ascontiguousarray(offsets, dtype=np.float64)
             sas_geometry_set_offsets(self.h, a, 0, stream)
 
+    def set_beam(self, beam_width: float, side: int = 1):
+        """Beam field of view of full azimuth width beam_width [rad] (0 = off)."""
+        sas_geometry_set_beam(self.h, beam_width, side)
+
     def positions(self):
         import torch
         tx = torch.empty((self.P, 3), dtype=torch.float64, device="cuda")
@@ -355,3 +373,6 @@ class Geometry:
 
     def sync_status(self, stream=None):
         sas_sync_status(self.h, stream)
+
+    def cull_stats(self, reset: bool = True, stream=None):
+        return sas_cull_stats(self.h, 1 if reset else 0, stream)

@@ -87,7 +87,7 @@ int encode_echo_map(CUtensorMap* map, const void* base, int elem_bytes, int Ns, 
 //   [ -st,     ct sph,                ct cph               ]
 __global__ void geometry_kernel(int P, int C, const double* __restrict__ pos, const double* __restrict__ att,
                                 const double* __restrict__ lever, const double* __restrict__ off,
-                                double* __restrict__ tx, double* __restrict__ rx) {
+                                double* __restrict__ tx, double* __restrict__ rx, float* __restrict__ rotc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     double sph, cph, sth, cth, sps, cps;
@@ -99,6 +99,13 @@ __global__ void geometry_kernel(int P, int C, const double* __restrict__ pos, co
                          -sth,      cth * sph,                   cth * cph};
     const double b0 = pos[3 * i] + off[3 * i], b1 = pos[3 * i + 1] + off[3 * i + 1],
                  b2 = pos[3 * i + 2] + off[3 * i + 2];
+    // columns 0 and 1 of R: body-frame components (R^T v).x, (R^T v).y of a NED vector v
+    rotc[6 * i + 0] = (float)R[0];
+    rotc[6 * i + 1] = (float)R[3];
+    rotc[6 * i + 2] = (float)R[6];
+    rotc[6 * i + 3] = (float)R[1];
+    rotc[6 * i + 4] = (float)R[4];
+    rotc[6 * i + 5] = (float)R[7];
     for (int c = -1; c < C; ++c) {
         const double* l = lever + 3 * (c + 1);
         double* o = (c < 0) ? tx + 3 * (size_t)i : rx + 3 * ((size_t)i * C + c);
@@ -110,7 +117,7 @@ __global__ void geometry_kernel(int P, int C, const double* __restrict__ pos, co
 
 static int run_geometry(sas_geometry_t h, cudaStream_t st) {
     geometry_kernel<<<(h->P + 127) / 128, 128, 0, st>>>(h->P, h->C, h->d_pos, h->d_att, h->d_lever, h->d_off,
-                                                        h->d_tx, h->d_rx);
+                                                        h->d_tx, h->d_rx, h->d_rotc);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }
@@ -367,6 +374,7 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     h->Ns = sig->n_samples;
     h->sig = *sig;
     h->echo_dtype = -1;
+    h->beam_side = 1;
     cudaGetDevice(&h->device);
     const size_t P = h->P, C = h->C;
     size_t o = 0;
@@ -376,7 +384,9 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     const size_t o_off = o; o = align256(o + P * 3 * 8);
     const size_t o_tx = o;  o = align256(o + P * 3 * 8);
     const size_t o_rx = o;  o = align256(o + P * C * 3 * 8);
+    const size_t o_rc = o;  o = align256(o + P * 6 * 4);
     const size_t o_st = o;  o = align256(o + 16);
+    const size_t o_cu = o;  o = align256(o + 4 * 8);
     const size_t o_cf = o;  o = align256(o + sizeof(FarrowCoef));
     const size_t o_fe = o;  o = align256(o + 8);
     cudaError_t e = cudaMalloc(&h->slab, o);
@@ -391,7 +401,9 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     h->d_off = (double*)(b + o_off);
     h->d_tx = (double*)(b + o_tx);
     h->d_rx = (double*)(b + o_rx);
+    h->d_rotc = (float*)(b + o_rc);
     h->d_status = (uint32_t*)(b + o_st);
+    h->d_cull = (unsigned long long*)(b + o_cu);
     h->d_coef = (FarrowCoef*)(b + o_cf);
     h->d_fit_err = (double*)(b + o_fe);
     int rc = SAS_OK;
@@ -404,6 +416,7 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     ck(cudaMemcpyAsync(h->d_lever + 3, nav->rx_lever, C * 3 * 8, cudaMemcpyHostToDevice, st), "copy rx_lever");
     ck(cudaMemsetAsync(h->d_off, 0, P * 3 * 8, st), "zero offsets");
     ck(cudaMemsetAsync(h->d_status, 0, 16, st), "zero status");
+    ck(cudaMemsetAsync(h->d_cull, 0, 4 * 8, st), "zero culling counts");
     if (rc == SAS_OK) rc = run_geometry(h, st);
     if (rc != SAS_OK) {
         cudaFree(h->slab);
@@ -427,6 +440,16 @@ extern "C" int sas_geometry_set_offsets(sas_geometry_t h, const double* offsets,
         SAS_CUDA(cudaMemcpyAsync(h->d_off, offsets, bytes,
                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     return run_geometry(h, st);
+}
+
+extern "C" int sas_geometry_set_beam(sas_geometry_t h, double beam_width, int side) {
+    if (!h || !(beam_width < M_PI) || (side != 1 && side != -1)) {
+        set_error("sas_geometry_set_beam: need a handle, beam_width < pi and side = +1 or -1");
+        return SAS_ERR_ARG;
+    }
+    h->beam_tan = beam_width > 0.0 ? tan(0.5 * beam_width) : 0.0;
+    h->beam_side = side;
+    return SAS_OK;
 }
 
 extern "C" int sas_geometry_positions(sas_geometry_t h, double* d_tx, double* d_rx, void* stream) {
@@ -663,6 +686,20 @@ extern "C" int sas_sync_status(sas_geometry_t h, void* stream) {
         set_error("a kernel's bounded wait ran out (status 0x%x); its results are invalid", v);
         return SAS_ERR_TIMEOUT;
     }
+    return SAS_OK;
+}
+
+extern "C" int sas_cull_stats(sas_geometry_t h, long long* out, int reset, void* stream) {
+    if (!h || !out) {
+        set_error("null argument");
+        return SAS_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long v[4];
+    SAS_CUDA(cudaStreamSynchronize(st));
+    SAS_CUDA(cudaMemcpy(v, h->d_cull, sizeof(v), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) out[k] = (long long)v[k];
+    if (reset) SAS_CUDA(cudaMemset(h->d_cull, 0, sizeof(v)));
     return SAS_OK;
 }
 

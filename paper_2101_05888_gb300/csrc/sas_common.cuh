@@ -72,6 +72,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  : "memory");
 }
 
+// Announces `bytes` more transaction bytes on the barrier's current phase
+// without arriving (one call per bulk copy that will complete on it).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -116,15 +122,10 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return *reinterpret_cast<float2*>(&rd);
 }
 
-// floor() of a float of magnitude < 2^22 on the FP32 pipe: returns the integer
-// and the floored value.  t = u + 1.5*2^23 rounded toward -inf holds floor(u)
-// in its low mantissa bits.
+// Integer rounding on the FP32 pipe: for |v| < 2^22, t = v + 1.5*2^23 (round
+// to nearest) holds the nearest integer n of v in its low mantissa bits
+// (bits(t) = bits(1.5*2^23) + n) and t - 1.5*2^23 = n exactly.
 constexpr float FLOOR_MAGIC = 12582912.0f;  // 1.5 * 2^23
-__device__ __forceinline__ int floor_magic(float u, float& fl) {
-    const float t = __fadd_rd(u, FLOOR_MAGIC);
-    fl = t - FLOOR_MAGIC;
-    return __float_as_int(t) - __float_as_int(FLOOR_MAGIC);
-}
 
 }  // namespace sas
 
@@ -143,7 +144,11 @@ struct sas_geometry_s {
     double* d_off;     // [P][3]
     double* d_tx;      // [P][3]
     double* d_rx;      // [P][C][3]
+    float* d_rotc;     // [P][6]: columns 0 and 1 of the attitude matrix (beam tests)
+    double beam_tan;   // tan(beam width / 2); <= 0: no beam field of view
+    int beam_side;     // +1 starboard, -1 port
     uint32_t* d_status;
+    unsigned long long* d_cull;   // [4] ray-culling counts (candidate, computed, beam edge, -)
     sas::FarrowCoef* d_coef;
     double* d_fit_err;
     int fit_valid;       // d_coef holds the Kaiser fit for (fit_taps, fit_beta)

@@ -22,9 +22,9 @@ template <bool DIM3>
 __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, const float2* __restrict__ img,
                                                               float2* __restrict__ eadj, int Ns) {
     using T = Tile<DIM3>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     float2* A = reinterpret_cast<float2*>(smem);                    // [GROUP][npos][NP]
-    float* rec = reinterpret_cast<float*>(A + GROUP * p.npos * NP);  // [NREC][PAIRS]
+    float* rec = reinterpret_cast<float*>(A + GROUP * p.npos * NP);  // [NREC][PAIRS], field-major
     float* coef_s = rec + NREC * PAIRS;                             // [TAPS][NP]
     int* base_s = reinterpret_cast<int*>(coef_s + TAPS * NP);       // [PAIRS]
 
@@ -57,14 +57,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
         T::pixel(ct, 0, lx, ly, lz);
         dxv = (float)((tx0 + lx - cx) * p.dx);
         dyv_c = (float)((ty0 + ly - cy) * p.dy);
+        // the varying coordinate as the forward kernel forms it (first slot plus
+        // s steps, in FP32), so that both take identical beam decisions
+        const float dv0 = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : dyv_c;
+        const float dvstep = DIM3 ? (float)p.dz : (float)(4.0 * p.dy);
+        d2c = DIM3 ? dxv * dxv + dyv_c * dyv_c : dxv * dxv;
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
             T::pixel(ct, s, lx, ly, lz);
-            const float dxs = (float)((tx0 + lx - cx) * p.dx);
-            const float dys = (float)((ty0 + ly - cy) * p.dy);
-            const float dzs = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : 0.f;
-            dvar[s] = DIM3 ? dzs : dys;
-            d2c = DIM3 ? dxs * dxs + dys * dys : dxs * dxs;
+            dvar[s] = fmaf((float)s, dvstep, dv0);
             dT[s] = 0.f;
             const int ix = tx0 + lx, iy = ty0 + ly, iz = tz0 + lz;
             G[s] = (ix < p.nx && iy < p.ny && iz < p.nz) ? img[((size_t)iz * p.ny + iy) * p.nx + ix]
@@ -76,11 +77,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
     for (int k = 0; k < nstages; ++k) {
         const long long qs = q0 + (long long)k * PAIRS;
         __syncthreads();   // previous stage's records no longer in use
-        if (warp == 0 && qs + lane < q1) base_s[lane] = pair_record(p, X0, Y0, Z0, qs + lane, rec + lane);
+        if (warp == 0 && qs + lane < q1) {
+            const int i = (int)((qs + lane) / p.C);
+            base_s[lane] = pair_record(p, pair_geo(p, X0, Y0, Z0, qs + lane, i), rec + lane, PAIRS);
+        }
         __syncthreads();
-        float r[NHOLD];
+        float r[F_NT + 1];
 #pragma unroll
-        for (int f = 0; f < NHOLD; ++f) r[f] = rec[f * PAIRS + lane];
+        for (int f = 0; f <= F_NT; ++f) r[f] = rec[f * PAIRS + lane];
         const int npairs = (int)min((long long)PAIRS, q1 - qs);
         for (int g0 = 0; g0 < npairs; g0 += GROUP) {
             if (consumer) {
@@ -108,25 +112,42 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                     const float tRz = __shfl_sync(0xffffffffu, r[F_RZ], pr);
                     const float nR2 = __shfl_sync(0xffffffffu, r[F_NR2], pr);
                     const float nR = __shfl_sync(0xffffffffu, r[F_NR], pr);
-                    const float uf = __shfl_sync(0xffffffffu, r[F_UF], pr);
+                    const float ufc = __shfl_sync(0xffffffffu, r[F_UF], pr);
                     const float phr = __shfl_sync(0xffffffffu, r[F_PH], pr);
                     const float Ax = DIM3 ? fmaf(tRx, dxv, tRy * dyv_c) : tRx * dxv;
                     float2* Aj = A + j * p.npos * NP;
+                    float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f;
+                    if (p.beam) {
+#pragma unroll
+                        for (int t = 0; t < 6; ++t) rot[t] = p.rotc[6 * (size_t)ping + t];
+                        tT0 = __shfl_sync(0xffffffffu, r[F_TX], pr);
+                        tT1 = __shfl_sync(0xffffffffu, r[F_TY], pr);
+                        tT2 = __shfl_sync(0xffffffffu, r[F_TZ], pr);
+                    }
 #pragma unroll
                     for (int s = 0; s < PX; ++s) {
+                        if (p.beam) {
+                            // both beams must see the pixel (sensor-to-pixel vectors R + d)
+                            const float dy = DIM3 ? dyv_c : dvar[s], dz = DIM3 ? dvar[s] : 0.f;
+                            if (!beam_sees(p, fmaf(0.5f, tT0, dxv), fmaf(0.5f, tT1, dy), fmaf(0.5f, tT2, dz), rot) ||
+                                !beam_sees(p, fmaf(0.5f, tRx, dxv), fmaf(0.5f, tRy, dy), fmaf(0.5f, tRz, dz), rot))
+                                continue;
+                        }
                         const float d2 = fmaf(dvar[s], dvar[s], d2c);
                         const float a = DIM3 ? fmaf(tRz, dvar[s], d2) + Ax : fmaf(tRy, dvar[s], d2) + Ax;
                         const float sm = nR2 + a;
                         const float D = fmaf(a, rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nR)), dT[s]);
-                        const float u = fmaf(D, p.fs_c, uf);
-                        const float ph = fmaf(D, p.fc_c, phr);
-                        float fl;
-                        const int di = floor_magic(u, fl);
-                        const float g = (u - fl) - 0.5f;
-                        const unsigned pos = min((unsigned)(di + p.U), (unsigned)(p.npos - 1));
+                        const float v = fmaf(D, p.fs_c, ufc);              // u - 1/2
+                        const float ph = fmaf(D, p.fc_c, phr);             // carrier phase [cycles]
+                        // nearest integer of u - 1/2 = floor(u); g = frac(u) - 1/2
+                        const float t = __fadd_rn(v, FLOOR_MAGIC);
+                        const float g = v - (t - FLOOR_MAGIC);
+                        const unsigned pos = min((unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - p.U)),
+                                                 (unsigned)(p.npos - 1));
                         const float pt = __fadd_rn(ph, FLOOR_MAGIC) - FLOOR_MAGIC;
                         float sn, cs;
-                        __sincosf((ph - pt) * 6.28318530717958647f, &sn, &cs);
+                        sincos_2pi(ph - pt, sn, cs);
                         // v = G exp(-j phase)
                         float vx = fmaf(G[s].x, cs, G[s].y * sn);
                         float vy = fmaf(G[s].y, cs, -G[s].x * sn);

@@ -41,6 +41,8 @@
 
 #include "sas_common.cuh"
 
+#include <type_traits>
+
 namespace sas {
 namespace core {
 
@@ -53,13 +55,23 @@ constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
 constexpr int EROW = 48;                // bytes per Farrow row: E0..E3 float2, E4..E7 bfloat162
+constexpr int RUN = 10;                 // Farrow positions per expansion run
+constexpr int NRUNSLOT = NCONS / 8;     // expansion runs in flight (one power p per thread)
 constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
 enum { MODE_FORWARD = 0, MODE_OFFSET_GRAD = 1 };
 
-// producer record fields (structure of arrays in shared memory, one column per pair)
-enum { F_TX, F_TY, F_TZ, F_NT2, F_NT, F_RX, F_RY, F_RZ, F_NR2, F_NR, F_UF, F_PH, F_SCALE, F_OFF, NREC };
-constexpr int NHOLD = 13;               // fields the per-pixel work needs (F_TX .. F_SCALE)
+// record fields of one (ping, channel) pair, in the order of the six float4
+// a consumer loads: {2R_R, |R_R|^2}, {|R_R|, frac u_ref - 1/2, phase, scale},
+// {2R_T, |R_T|^2}, {|R_T|, ping, flags, segment offset}, {c0, c1.x},
+// {c1.y, c1.z, -, -} (c0, c1: columns 0 and 1 of the attitude matrix)
+enum {
+    F_RX, F_RY, F_RZ, F_NR2, F_NR, F_UF, F_PH, F_SCALE, F_TX, F_TY, F_TZ, F_NT2, F_NT, F_PING, F_FLAGS, F_OFF,
+    F_C0X, F_C0Y, F_C0Z, F_C1X, F_C1Y, F_C1Z, NREC = 24
+};
+constexpr int HROW = NREC;              // floats per record row (6 x float4)
+// pair flags: the whole tile lies inside the transmitter / receiver beam
+enum { FL_TX_FULL = 1, FL_RX_FULL = 2 };
 
 struct KParams {
     const double* tx;       // [P][3]
@@ -78,7 +90,14 @@ struct KParams {
     float fs_c, fc_c;       // fs/c, fc/c
     float fs_f, wfc;        // fs, 2 pi fc
     float grad_scale;       // -2/c (factor 2 of dL/dp = 2 Re(...), -1/c of dtau/dp)
-    int U, npos, seglen, seg_align, slot_bytes;
+    // beam field of view (Sec. II-C): sensor sees x iff b = R^T (x - sensor) has
+    // side b_y > 0 and |b_x| <= beam_tan side b_y; rotc [P][6] = columns 0, 1 of R
+    const float* rotc;
+    int beam;
+    float beam_tan, beam_side;
+    unsigned long long* cull;   // [3] candidate, computed, beam-edge (ping, channel, tile) blocks
+    float hx, hy, hz;       // half extents of a tile's pixel-centre box [m]
+    int U, npos, npos_pad, seglen, seg_align, slot_bytes;
     int accumulate, atomic_out, skip_copies;
     unsigned long long wait_ns;
 };
@@ -134,12 +153,16 @@ __device__ __forceinline__ float rcp_sfu(float x) {
     return y;
 }
 
-// sin and cos of 2 pi x for |x| <= 1/2 on the SFU
+// sin and cos of 2 pi x on the SFU; callers reduce x to [-1/2, 1/2] first
+// (the SFU approximations are accurate on [-pi, pi])
 __device__ __forceinline__ void sincos_2pi(float x, float& sn, float& cs) {
     const float a = x * 6.28318530717958647f;
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(a));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(a));
 }
+
+__device__ __forceinline__ uint32_t bits_of(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+__device__ __forceinline__ uint32_t bits_of(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
 
 __device__ __forceinline__ __half2 h2_of_bits(uint32_t b) {
     return *reinterpret_cast<__half2*>(&b);
@@ -149,37 +172,79 @@ __device__ __forceinline__ __nv_bfloat162 b2_of_bits(uint32_t b) {
     return *reinterpret_cast<__nv_bfloat162*>(&b);
 }
 
-// FP64 reference terms of pair q (ping q / C, channel q % C) at the tile
-// centre (X0, Y0, Z0), written to the record column rc (stride PAIRS):
-// 2R and |R|^2, |R| for transmitter and receiver (R = x0 - sensor), the
-// fraction of u_ref = (tau_ref - t0) fs and the carrier phase fc tau_ref mod 1.
-// Returns the raw sample index of Farrow position 0, tap 0: floor(u_ref) - U - 3.
-__device__ __forceinline__ int pair_record(const KParams& p, double X0, double Y0, double Z0, long long q, float* rc) {
-    const int i = (int)(q / p.C);
+// FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
+// R_T = x0 - x_TX (ping i = q / C), R_R = x0 - x_RX (pair q).
+struct PairGeo {
+    double Tx, Ty, Tz, Rx, Ry, Rz;
+};
+__device__ __forceinline__ PairGeo pair_geo(const KParams& p, double X0, double Y0, double Z0, long long q, int i) {
     const double* t = p.tx + 3 * (size_t)i;
     const double* r = p.rx + 3 * (size_t)q;
-    const double Tx = X0 - t[0], Ty = Y0 - t[1], Tz = Z0 - t[2];
-    const double Rx = X0 - r[0], Ry = Y0 - r[1], Rz = Z0 - r[2];
-    const double nT2 = Tx * Tx + Ty * Ty + Tz * Tz, nR2 = Rx * Rx + Ry * Ry + Rz * Rz;
+    return PairGeo{X0 - t[0], Y0 - t[1], Z0 - t[2], X0 - r[0], Y0 - r[1], Z0 - r[2]};
+}
+
+// FP64 reference terms of a pair written to the record rc (field f at
+// rc[f * stride]): 2R and |R|^2, |R| for transmitter and receiver, the fraction of
+// u_ref = (tau_ref - t0) fs minus 1/2 (so that rounding u - 1/2 to the
+// nearest integer gives floor(u)) and the carrier phase fc tau_ref mod 1
+// (cycles).
+// Returns the raw sample index of Farrow position 0, tap 0: floor(u_ref) - U - 3.
+__device__ __forceinline__ int pair_record(const KParams& p, const PairGeo& G, float* rc, int stride) {
+    const double nT2 = G.Tx * G.Tx + G.Ty * G.Ty + G.Tz * G.Tz, nR2 = G.Rx * G.Rx + G.Ry * G.Ry + G.Rz * G.Rz;
     const double nT = sqrt(nT2), nR = sqrt(nR2);
     const double tau = (nT + nR) * p.inv_c;
     double u = (tau - p.t0) * p.fs;
     u = fmin(fmax(u, -268435456.0), 268435456.0);  // keep sample coordinates in int range
     const double iref = floor(u);
     const double ph = p.fc * tau;
-    rc[F_TX * PAIRS] = (float)(2.0 * Tx);
-    rc[F_TY * PAIRS] = (float)(2.0 * Ty);
-    rc[F_TZ * PAIRS] = (float)(2.0 * Tz);
-    rc[F_NT2 * PAIRS] = (float)nT2;
-    rc[F_NT * PAIRS] = (float)nT;
-    rc[F_RX * PAIRS] = (float)(2.0 * Rx);
-    rc[F_RY * PAIRS] = (float)(2.0 * Ry);
-    rc[F_RZ * PAIRS] = (float)(2.0 * Rz);
-    rc[F_NR2 * PAIRS] = (float)nR2;
-    rc[F_NR * PAIRS] = (float)nR;
-    rc[F_UF * PAIRS] = (float)(u - iref);
-    rc[F_PH * PAIRS] = (float)(ph - floor(ph));
+    rc[F_TX * stride] = (float)(2.0 * G.Tx);
+    rc[F_TY * stride] = (float)(2.0 * G.Ty);
+    rc[F_TZ * stride] = (float)(2.0 * G.Tz);
+    rc[F_NT2 * stride] = (float)nT2;
+    rc[F_NT * stride] = (float)nT;
+    rc[F_RX * stride] = (float)(2.0 * G.Rx);
+    rc[F_RY * stride] = (float)(2.0 * G.Ry);
+    rc[F_RZ * stride] = (float)(2.0 * G.Rz);
+    rc[F_NR2 * stride] = (float)nR2;
+    rc[F_NR * stride] = (float)nR;
+    rc[F_UF * stride] = (float)(u - iref - 0.5);
+    rc[F_PH * stride] = (float)(ph - floor(ph));
     return (int)iref - p.U - 3;
+}
+
+// Beam class of one sensor for the whole tile (FP32, conservative):
+// 0 = no pixel of the tile can be seen, 2 = every pixel is seen, 1 = test per
+// pixel.  The tile's pixel-centre box, seen through the linear map
+// (b_x, side b_y) = (c0 . w, side c1 . w), is a convex polygon spanned by the
+// corners: it misses the beam wedge |b_x| <= k b_y if all corners lie beyond
+// one edge or behind the sensor, and lies inside if all corners do.  Margins
+// of 1e-5 relative keep both decisions on the safe side of FP32 rounding.
+template <bool DIM3>
+__device__ __forceinline__ int beam_class(const KParams& p, float vx, float vy, float vz, const float* c) {
+    bool all_right = true, all_left = true, all_behind = true, all_in = true;
+    const float k = p.beam_tan;
+#pragma unroll
+    for (int n = 0; n < (DIM3 ? 8 : 4); ++n) {
+        const float wx = vx + ((n & 1) ? p.hx : -p.hx);
+        const float wy = vy + ((n & 2) ? p.hy : -p.hy);
+        const float wz = vz + (DIM3 ? ((n & 4) ? p.hz : -p.hz) : 0.f);
+        const float bx = fmaf(c[0], wx, fmaf(c[1], wy, c[2] * wz));
+        const float by = p.beam_side * fmaf(c[3], wx, fmaf(c[4], wy, c[5] * wz));
+        const float mu = 1e-5f * (fabsf(bx) + fabsf(by)) + 1e-6f;
+        all_right = all_right && (bx - k * by > mu);
+        all_left = all_left && (-bx - k * by > mu);
+        all_behind = all_behind && (by < -mu);
+        all_in = all_in && (fabsf(bx) - k * by < -mu) && (by > mu);
+    }
+    if (all_right || all_left || all_behind) return 0;
+    return all_in ? 2 : 1;
+}
+
+// Per-pixel beam test (FP32), w = sensor-to-pixel vector.
+__device__ __forceinline__ bool beam_sees(const KParams& p, float wx, float wy, float wz, const float* c) {
+    const float bx = fmaf(c[0], wx, fmaf(c[1], wy, c[2] * wz));
+    const float by = p.beam_side * fmaf(c[3], wx, fmaf(c[4], wy, c[5] * wz));
+    return by > 0.f && fabsf(bx) <= p.beam_tan * by;
 }
 
 // Shared-memory size and launch geometry, host side.
@@ -188,18 +253,21 @@ struct Layout {
     size_t smem;
 };
 
-inline size_t smem_bytes(int slot_bytes, int npos) {
+inline size_t smem_bytes(int slot_bytes, int npos_pad) {
     return (size_t)NSTAGE * PAIRS * slot_bytes          // echo segments
-           + (size_t)2 * GROUP * npos * EROW            // Farrow rows, double buffered
-           + (size_t)NSTAGE * NREC * PAIRS * 4          // producer records
+           + (size_t)2 * GROUP * npos_pad * EROW        // Farrow rows, double buffered
+           + (size_t)NSTAGE * PAIRS * NREC * 4          // producer records
            + (size_t)TAPS * NP * 4                      // coefficients
-           + (size_t)2 * NHOLD * PAIRS * 4              // consumer copy of the records
+           + (size_t)2 * PAIRS * HROW * 4               // consumer copy of the records
            + (size_t)NCW * 4 * 8                        // cross-warp reduction (gradient)
-           + (size_t)(2 * NSTAGE + 4) * 8 + 16;         // mbarriers (copy ring, Farrow buffers), abort flag
+           + (size_t)(2 * NSTAGE + 4) * 8 + 16          // mbarriers (copy ring, Farrow buffers), abort flag
+           + (size_t)2 * NSTAGE * 4;                    // pairs per stage, last-stage flags
 }
 
 // ----------------------------------------------------------------------------
-template <typename ET, bool DIM3, int MODE>
+// BEAM: the beam field of view is on (culling in the producer, per-pixel tests
+// in tiles on a beam edge); without it every candidate pair is computed.
+template <typename ET, bool DIM3, int MODE, bool BEAM>
 __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant__ CUtensorMap tmap, const KParams p) {
     using T = Tile<DIM3>;
     // FP16 Farrow rows for 16-bit echoes in the forward pass
@@ -210,14 +278,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
 
     unsigned char* seg = smem;
     unsigned char* ebuf = seg + (size_t)NSTAGE * PAIRS * p.slot_bytes;
-    const int ebuf_pair = p.npos * EROW;
+    const int ebuf_pair = p.npos_pad * EROW;          // positions padded to whole expansion runs
     float* rec = reinterpret_cast<float*>(ebuf + 2 * GROUP * ebuf_pair);
-    float* coef_s = rec + NSTAGE * NREC * PAIRS;
+    float* coef_s = rec + NSTAGE * PAIRS * NREC;
     float* hold = coef_s + TAPS * NP;
-    double* wred = reinterpret_cast<double*>(hold + 2 * NHOLD * PAIRS);
+    double* wred = reinterpret_cast<double*>(hold + 2 * PAIRS * HROW);
     uint64_t* bars = reinterpret_cast<uint64_t*>(wred + NCW * 4);      // full[NSTAGE], empty[NSTAGE]
     uint64_t* ebar = bars + 2 * NSTAGE;                                   // Farrow buffers: efull[2], eempty[2]
     volatile int* abort_flag = reinterpret_cast<volatile int*>(ebar + 4);
+    volatile int* st_count = abort_flag + 4;                              // pairs in ring stage s
+    volatile int* st_last = st_count + NSTAGE;                            // stage s is the final one
 
     const int ntiles = p.tiles_x * p.tiles_y * p.tiles_z;
     const int tile = blockIdx.x % ntiles;
@@ -225,14 +295,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     const int tx0 = (tile % p.tiles_x) * T::TX;
     const int ty0 = ((tile / p.tiles_x) % p.tiles_y) * T::TY;
     const int tz0 = (tile / (p.tiles_x * p.tiles_y)) * T::TZ;
-    // pairs of this CTA: whole pings [ping0, ping1)
+    // candidate pairs of this CTA: whole pings [ping0, ping1)
     const int ping0 = min(p.P, split * p.pings_per_split);
     const int ping1 = min(p.P, ping0 + p.pings_per_split);
     const long long q0 = (long long)ping0 * p.C;
     const long long q1 = (long long)ping1 * p.C;
-    const int nq = (int)(q1 - q0);
-    const int nstages = (nq + PAIRS - 1) / PAIRS;
-    const int ngroups = (nq + GROUP - 1) / GROUP;
     const double cx = tx0 + 0.5 * (T::TX - 1), cy = ty0 + 0.5 * (T::TY - 1), cz = tz0 + 0.5 * (T::TZ - 1);
 
     if (tid == 0) {
@@ -249,51 +316,123 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
 
     if (warp == 0) {
         // ================= producer =================
+        // Scans the candidate pairs 32 at a time, drops those whose beams
+        // cannot see the tile, and packs the rest into full stages of PAIRS
+        // pairs (the last stage may be partial or empty and carries the
+        // last-stage flag).  Each pair's copy is announced on the stage's full
+        // barrier (expect_tx) before it is issued; lane 0 arrives once the
+        // stage's records are written.
         const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = p.z0 + (DIM3 ? cz * p.dz : 0.0);
         const uint32_t seg_bytes = (uint32_t)p.seglen * (uint32_t)sizeof(ET);
-        int k = 0;
-        for (; k < nstages; ++k) {
-            const int s = k % NSTAGE;
-            if (k >= NSTAGE) {
-                const bool ok =
-                    mbar_wait_bounded(smem_u32(&bars[NSTAGE + s]), ((k / NSTAGE) - 1) & 1, p.wait_ns);
-                if (!ok && lane == 0) {
-                    *abort_flag = 1;
-                    atomicOr(p.status, DEV_TIMEOUT);
-                }
+        int k = 0;            // stages opened
+        int fill = 0;         // pairs in the open stage
+        bool open = false;
+        unsigned n_cand = 0, n_act = 0, n_edge = 0;   // this lane's culling counts
+        auto fail = [&]() {
+            if (lane == 0) {
+                *abort_flag = 1;
+                atomicOr(p.status, DEV_TIMEOUT);
             }
             __syncwarp();
-            if (*abort_flag) break;
-            const long long q = q0 + (long long)k * PAIRS + lane;
-            const bool valid = q < q1;
-            int seg_start = 0;
-            if (valid) {
-                const int base = pair_record(p, X0, Y0, Z0, q, rec + s * NREC * PAIRS + lane);
-                seg_start = base - (((base % p.seg_align) + p.seg_align) % p.seg_align);
-                float* rc = rec + s * NREC * PAIRS;
-                rc[F_OFF * PAIRS + lane] = __int_as_float(base - seg_start);
-                rc[F_SCALE * PAIRS + lane] = p.scale ? p.scale[q] : 1.0f;
-            }
+        };
+        auto open_stage = [&]() -> bool {
+            const int s = k % NSTAGE;
+            if (k >= NSTAGE && !mbar_wait_bounded(smem_u32(&bars[NSTAGE + s]), ((k / NSTAGE) - 1) & 1, p.wait_ns))
+                fail();
+            __syncwarp();
+            if (*abort_flag) return false;
+            ++k;
+            fill = 0;
+            open = true;
+            return true;
+        };
+        auto close_stage = [&](bool last) {
+            const int s = (k - 1) % NSTAGE;
             __syncwarp();
             if (lane == 0) {
-                const int nvalid = (int)min((long long)PAIRS, q1 - (q0 + (long long)k * PAIRS));
-                mbar_arrive_expect_tx(smem_u32(&bars[s]), (uint32_t)nvalid * seg_bytes);
+                st_count[s] = fill;
+                st_last[s] = last ? 1 : 0;
+                mbar_arrive(smem_u32(&bars[s]));
             }
             __syncwarp();
-            if (valid && !p.skip_copies)
-                tma_load_2d(smem_u32(seg + ((size_t)s * PAIRS + lane) * p.slot_bytes), &tmap, seg_start, (int32_t)q,
-                            smem_u32(&bars[s]));
+            open = false;
+        };
+        for (long long qb = q0; qb < q1; qb += PAIRS) {
+            const long long q = qb + lane;
+            const bool valid = q < q1;
+            const int i = valid ? (int)(q / p.C) : 0;
+            PairGeo G{};
+            int flags = FL_TX_FULL | FL_RX_FULL;
+            bool active = valid;
+            float rc6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (valid) {
+                G = pair_geo(p, X0, Y0, Z0, q, i);
+                if (BEAM) {
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) rc6[t] = p.rotc[6 * (size_t)i + t];
+                    const int ct_ = beam_class<DIM3>(p, (float)G.Tx, (float)G.Ty, (float)G.Tz, rc6);
+                    const int cr_ = beam_class<DIM3>(p, (float)G.Rx, (float)G.Ry, (float)G.Rz, rc6);
+                    active = ct_ != 0 && cr_ != 0;
+                    flags = (ct_ == 2 ? FL_TX_FULL : 0) | (cr_ == 2 ? FL_RX_FULL : 0);
+                }
+            }
+            n_cand += valid ? 1u : 0u;
+            n_act += active ? 1u : 0u;
+            n_edge += (active && flags != (FL_TX_FULL | FL_RX_FULL)) ? 1u : 0u;
+            const unsigned amask = __ballot_sync(0xffffffffu, active);
+            const int n = __popc(amask);
+            const int rank = __popc(amask & ((1u << lane) - 1u));
+            int done = 0;
+            while (done < n) {
+                if (!open && !open_stage()) break;
+                const int take = min(PAIRS - fill, n - done);
+                if (active && rank >= done && rank < done + take) {
+                    const int s = (k - 1) % NSTAGE;
+                    const int slot = fill + rank - done;
+                    float* rc = rec + (s * PAIRS + slot) * NREC;
+                    const int base = pair_record(p, G, rc, 1);
+                    const int seg_start = base - (((base % p.seg_align) + p.seg_align) % p.seg_align);
+                    rc[F_OFF] = __int_as_float(base - seg_start);
+                    rc[F_SCALE] = p.scale ? p.scale[q] : 1.0f;
+                    rc[F_PING] = __int_as_float(i);
+                    rc[F_FLAGS] = __int_as_float(flags);
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) rc[F_C0X + t] = rc6[t];
+                    const uint32_t bar = smem_u32(&bars[s]);
+                    mbar_expect_tx(bar, seg_bytes);
+                    if (!p.skip_copies)
+                        tma_load_2d(smem_u32(seg + ((size_t)s * PAIRS + slot) * p.slot_bytes), &tmap, seg_start,
+                                    (int32_t)q, bar);
+                }
+                fill += take;
+                done += take;
+                if (fill == PAIRS) close_stage(false);
+            }
+            if (*abort_flag) break;
         }
+        if (!*abort_flag && (open || open_stage())) close_stage(true);
         // every issued stage must have landed before the CTA may exit
         for (int kk = max(0, k - NSTAGE); kk < k; ++kk)
             mbar_wait_bounded(smem_u32(&bars[kk % NSTAGE]), (kk / NSTAGE) & 1, p.wait_ns);
+        if (p.cull) {
+            n_cand = __reduce_add_sync(0xffffffffu, n_cand);
+            n_act = __reduce_add_sync(0xffffffffu, n_act);
+            n_edge = __reduce_add_sync(0xffffffffu, n_edge);
+            if (lane == 0) {
+                atomicAdd(&p.cull[0], (unsigned long long)n_cand);
+                atomicAdd(&p.cull[1], (unsigned long long)n_act);
+                atomicAdd(&p.cull[2], (unsigned long long)n_edge);
+            }
+        }
         return;
     }
 
     // ================= consumers =================
     const int ct = tid - 32;
-    float dxv, dyv_c, d2c = 0.f;
-    float dvar[PX], dT[PX];
+    // pixel offsets from the tile centre: x (and y in 3D) fixed per thread; the
+    // slot s moves along y (2D, 4 rows a slot) or z (3D): d_var(s) = dv0 + s dvstep
+    float dxv, dyv_c, dv0, dvstep;
+    float d2[PX], dT[PX];                 // |d|^2 per pixel; transmitter differential range of the ping
     float2 acc[PX];                       // forward: image accumulators; gradient: G(x)
     float rsum[MODE == MODE_OFFSET_GRAD ? PX : 1];
     {
@@ -301,14 +440,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         T::pixel(ct, 0, lx, ly, lz);
         dxv = (float)((tx0 + lx - cx) * p.dx);
         dyv_c = (float)((ty0 + ly - cy) * p.dy);
+        dv0 = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : dyv_c;
+        dvstep = DIM3 ? (float)p.dz : (float)(4.0 * p.dy);
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
             T::pixel(ct, s, lx, ly, lz);
-            const float dxs = (float)((tx0 + lx - cx) * p.dx);
-            const float dys = (float)((ty0 + ly - cy) * p.dy);
-            const float dzs = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : 0.f;
-            dvar[s] = DIM3 ? dzs : dys;
-            d2c = DIM3 ? dxs * dxs + dys * dys : dxs * dxs;
+            const double ddx = (tx0 + lx - cx) * p.dx, ddy = (ty0 + ly - cy) * p.dy;
+            const double ddz = DIM3 ? (tz0 + lz - cz) * p.dz : 0.0;
+            d2[s] = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
             dT[s] = 0.f;
             if (MODE == MODE_FORWARD) {
                 acc[s] = make_float2(0.f, 0.f);
@@ -321,77 +460,67 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
     }
     float gacc0 = 0.f, gacc1 = 0.f, gacc2 = 0.f;   // gradient: receiver-side sum for the current ping
+    uint32_t tmask = 0xffu;                         // pixels the current ping's transmitter sees
 
-    float r_cur[NHOLD];
-#pragma unroll
-    for (int f = 0; f < NHOLD; ++f) r_cur[f] = 0.f;
+    // Farrow expansion work split: thread (run slot r, power p) computes E_p at
+    // RUN consecutive positions of one pair of the group from a sliding window
+    // of RUN + 7 samples.  Runs never need a bounds test: the Farrow buffer and
+    // the echo slot are padded to whole runs (padding values are never read).
     const int Ep = ct & 7;
     const int Erun = ct >> 3;                       // 0 .. NRUNSLOT - 1
-    constexpr int NRUNSLOT = NCONS / 8;
-    constexpr int RMAX = 12;                        // longest run of positions per thread
-    // runs of R positions, as few as needed for every run slot to get at most one
-    const int runs_per_pair_min = max(1, NRUNSLOT / GROUP);
-    const int R = min(RMAX, (p.npos + runs_per_pair_min - 1) / runs_per_pair_min);
-    const int runs_per_pair = (p.npos + R - 1) / R;
-
-    // Farrow expansion of group gg into ebuf[gg & 1]
-    auto expand = [&](int gg) {
-        const int stage = gg / GPS;
-        const int s = stage % NSTAGE;
-        const float* rc = rec + s * NREC * PAIRS;
-        unsigned char* eb = ebuf + (gg & 1) * GROUP * ebuf_pair;
-        float cc[TAPS];
+    const int runs_per_pair = (p.npos + RUN - 1) / RUN;
+    float2 cc2[TAPS];                               // this thread's coefficients, packed (c, c)
 #pragma unroll
-        for (int m = 0; m < TAPS; ++m) cc[m] = coef_s[m * NP + Ep];
-        const int total = GROUP * runs_per_pair;
+    for (int m = 0; m < TAPS; ++m) cc2[m] = make_float2(coef_s[m * NP + Ep], coef_s[m * NP + Ep]);
+    // byte offset of E_p in a row and its format (FP32 pair, or a packed 16-bit pair)
+    const bool e_wide = !E16 && Ep < 4;
+    const int e_off = E16 ? Ep * 4 : (Ep < 4 ? Ep * 8 : 32 + (Ep - 4) * 4);
+
+    // Farrow rows of group gi of stage kst (npairs pairs in the stage) into buffer b
+    auto expand = [&](int kst, int gi, int npairs, int b) {
+        const int s = kst % NSTAGE;
+        const float* rc = rec + s * PAIRS * NREC;
+        unsigned char* eb = ebuf + b * GROUP * ebuf_pair;
+        const int ng = min(GROUP, npairs - gi * GROUP);
+        const int total = ng * runs_per_pair;
         for (int run = Erun; run < total; run += NRUNSLOT) {
             const int j = run / runs_per_pair;
-            const int pos0 = (run - j * runs_per_pair) * R;
-            const int pr = (gg % GPS) * GROUP + j;
-            if (stage * PAIRS + pr >= nq) continue;
+            const int pos0 = (run - j * runs_per_pair) * RUN;
+            const int pr = gi * GROUP + j;
             const unsigned char* slot = seg + ((size_t)s * PAIRS + pr) * p.slot_bytes;
-            const int off = __float_as_int(rc[F_OFF * PAIRS + pr]);
-            const float sc = E16 ? 1.0f : rc[F_SCALE * PAIRS + pr];
-            const int nout = min(R, p.npos - pos0);
-            float2 w[RMAX + TAPS - 1];
+            const int off = __float_as_int(rc[pr * NREC + F_OFF]) + pos0;
+            const float sc = E16 ? 1.0f : rc[pr * NREC + F_SCALE];
+            float2 w[RUN + TAPS - 1];
 #pragma unroll
-            for (int t = 0; t < RMAX + TAPS - 1; ++t)
-                w[t] = (t < nout + TAPS - 1) ? load_sample<ET>(slot, off + pos0 + t, sc) : make_float2(0.f, 0.f);
-            unsigned char* dst = eb + j * ebuf_pair + pos0 * EROW;
+            for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
+            unsigned char* dst = eb + j * ebuf_pair + pos0 * EROW + e_off;
 #pragma unroll
-            for (int kq = 0; kq < RMAX; ++kq) {
-                if (kq < nout) {
-                    float2 e = make_float2(0.f, 0.f);
+            for (int kq = 0; kq < RUN; ++kq) {
+                float2 e = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int m = 0; m < TAPS; ++m) e = ffma2(make_float2(cc[m], cc[m]), w[kq + m], e);
-                    if (E16)
-                        *reinterpret_cast<__half2*>(dst + kq * EROW + Ep * 4) = __floats2half2_rn(e.x, e.y);
-                    else if (Ep < 4)
-                        *reinterpret_cast<float2*>(dst + kq * EROW + Ep * 8) = e;
-                    else
-                        *reinterpret_cast<__nv_bfloat162*>(dst + kq * EROW + 32 + (Ep - 4) * 4) =
-                            __floats2bfloat162_rn(e.x, e.y);
-                }
+                for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
+                const uint32_t narrow = E16 ? bits_of(__floats2half2_rn(e.x, e.y)) : bits_of(__floats2bfloat162_rn(e.x, e.y));
+                if (e_wide) *reinterpret_cast<float2*>(dst + kq * EROW) = e;
+                if (!e_wide) *reinterpret_cast<uint32_t*>(dst + kq * EROW) = narrow;
             }
         }
     };
 
-    auto hold_records = [&](int stage) {
-        const float* rc = rec + (stage % NSTAGE) * NREC * PAIRS;
-        float* hd = hold + (stage & 1) * NHOLD * PAIRS;
-        for (int t = ct; t < NHOLD * PAIRS; t += NCONS) hd[t] = rc[t];
+    // consumer copy of a stage's records (read by uniform 16-byte loads; the
+    // producer's ring slot is recycled as soon as the stage's expansions are done)
+    auto hold_records = [&](int kst) {
+        const float4* rc = reinterpret_cast<const float4*>(rec + (kst % NSTAGE) * PAIRS * NREC);
+        float4* hd = reinterpret_cast<float4*>(hold + (kst & 1) * PAIRS * HROW);
+        for (int t = ct; t < PAIRS * HROW / 4; t += NCONS) hd[t] = rc[t];
     };
 
-    auto maybe_release = [&](int gg) {
-        const int stage = gg / GPS;
-        if (((gg % GPS) == GPS - 1) || (gg == ngroups - 1)) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bars[NSTAGE + stage % NSTAGE]));
-        }
+    auto release = [&](int kst) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars[NSTAGE + kst % NSTAGE]));
     };
 
-    auto wait_stage = [&](int stage) -> bool {
-        const bool ok = mbar_wait_bounded(smem_u32(&bars[stage % NSTAGE]), (stage / NSTAGE) & 1, p.wait_ns);
+    auto wait_stage = [&](int kst) -> bool {
+        const bool ok = mbar_wait_bounded(smem_u32(&bars[kst % NSTAGE]), (kst / NSTAGE) & 1, p.wait_ns);
         if (!ok) {
             *abort_flag = 1;
             atomicOr(p.status, DEV_TIMEOUT);
@@ -404,22 +533,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f, tNT2 = 0.f, tNT = 0.f;   // transmitter terms of the current ping
     auto flush_ping = [&](int ping) {
         if (MODE != MODE_OFFSET_GRAD) return;
-        const float Ax = DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv;
+        const float tTv = DIM3 ? tT2 : tT1;
+        const float P0 = fmaf(tTv, dv0, DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv);
+        const float P1 = tTv * dvstep;
         float hx = 0.5f * tT0 + dxv;
         float hy = DIM3 ? 0.5f * tT1 + dyv_c : 0.f;
         float hz = DIM3 ? 0.f : 0.5f * tT2;
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
-            const float d2 = fmaf(dvar[s], dvar[s], d2c);
-            const float a = DIM3 ? fmaf(tT2, dvar[s], d2) + Ax : fmaf(tT1, dvar[s], d2) + Ax;
+            const float dvs = fmaf((float)s, dvstep, dv0);
+            const float a = fmaf((float)s, P1, P0) + d2[s];
             const float sm = tNT2 + a;
-            const float k = rsum[MODE == MODE_OFFSET_GRAD ? s : 0] * rsqrt_sfu(sm);   // r / |R_T + d|
-            // R_T + d: (R.x + dx, R.y + dy or R.y + dy_s, R.z + dz_s)
-            const float vy = DIM3 ? hy : 0.5f * tT1 + dvar[s];
-            const float vz = DIM3 ? 0.5f * tT2 + dvar[s] : hz;
-            gacc0 = fmaf(k, hx, gacc0);
-            gacc1 = fmaf(k, vy, gacc1);
-            gacc2 = fmaf(k, vz, gacc2);
+            const float kk = rsum[MODE == MODE_OFFSET_GRAD ? s : 0] * rsqrt_sfu(sm);   // r / |R_T + d|
+            const float vy = DIM3 ? hy : 0.5f * tT1 + dvs;
+            const float vz = DIM3 ? 0.5f * tT2 + dvs : hz;
+            gacc0 = fmaf(kk, hx, gacc0);
+            gacc1 = fmaf(kk, vy, gacc1);
+            gacc2 = fmaf(kk, vz, gacc2);
             rsum[MODE == MODE_OFFSET_GRAD ? s : 0] = 0.f;
         }
         (void)hy;
@@ -461,174 +591,225 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
     };
 
-    bool aborted = false;
-    if (ngroups > 0) {
-        const bool ok = wait_stage(0);
-        if (ok) {
-            hold_records(0);
-            expand(0);
-            maybe_release(0);
+    // per-pixel work of one pair; MASKED: apply the beam test per pixel
+    auto pixels = [&](auto masked, const float4 q0, const float4 q1, const float* rot, uint32_t rmask_needed,
+                      const unsigned char* erow) {
+        constexpr bool MASKED = decltype(masked)::value;
+        const float tRx = q0.x, tRy = q0.y, tRz = q0.z, nR2 = q0.w;
+        const float nR = q1.x, ufc = q1.y, phr = q1.z;
+        const float scl = E16 ? q1.w : 1.0f;
+        const float tRv = DIM3 ? tRz : tRy;
+        const float P0 = fmaf(tRv, dv0, DIM3 ? fmaf(tRx, dxv, tRy * dyv_c) : tRx * dxv);
+        const float P1 = tRv * dvstep;
+#pragma unroll
+        for (int s = 0; s < PX; ++s) {
+            bool seen = true;
+            if (MASKED) {
+                const float dvs = fmaf((float)s, dvstep, dv0);
+                const float wx = fmaf(0.5f, tRx, dxv);
+                const float wy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvs);
+                const float wz = DIM3 ? fmaf(0.5f, tRz, dvs) : 0.5f * tRz;
+                seen = ((tmask >> s) & 1u) && (!rmask_needed || beam_sees(p, wx, wy, wz, rot));
+            }
+            const float a = fmaf((float)s, P1, P0) + d2[s];       // 2 R.d + |d|^2
+            const float sm = nR2 + a;
+            const float rs = rsqrt_sfu(sm);                     // 1 / |R_R + d|
+            const float den = fmaf(sm, rs, nR);
+            const float D = fmaf(a, rcp_sfu(den), dT[s]);       // two-way differential path [m]
+            const float v = fmaf(D, p.fs_c, ufc);                // u - 1/2, rel. to floor(u_ref)
+            const float ph = fmaf(D, p.fc_c, phr);               // carrier phase [cycles]
+            // the nearest integer of u - 1/2 is floor(u): it sits in the mantissa of
+            // t = v + 1.5*2^23 (round to nearest), and g = v - that = frac(u) - 1/2
+            const float t = __fadd_rn(v, FLOOR_MAGIC);
+            const float g = v - (t - FLOOR_MAGIC);
+            const unsigned pos = min((unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - p.U)),
+                                     (unsigned)(p.npos - 1));
+            const float4* e = reinterpret_cast<const float4*>(erow + pos * EROW);
+            const float pt = __fadd_rn(ph, FLOOR_MAGIC) - FLOOR_MAGIC;   // nearest integer
+            float sn, cs;
+            sincos_2pi(ph - pt, sn, cs);                                // argument in [-pi, pi]
+            if (MASKED && !seen) {
+                sn = 0.f;
+                cs = 0.f;
+            }
+            if (E16) {
+                // packed FP16 Horner over E_7 .. E_0, scale and accumulate in FP32
+                const uint4 lo = *reinterpret_cast<const uint4*>(e), hi = *reinterpret_cast<const uint4*>(e + 1);
+                const __half2 g16 = __float2half2_rn(g);
+                __half2 h = __hfma2(h2_of_bits(hi.w), g16, h2_of_bits(hi.z));
+                h = __hfma2(h, g16, h2_of_bits(hi.y));
+                h = __hfma2(h, g16, h2_of_bits(hi.x));
+                h = __hfma2(h, g16, h2_of_bits(lo.w));
+                h = __hfma2(h, g16, h2_of_bits(lo.z));
+                h = __hfma2(h, g16, h2_of_bits(lo.y));
+                h = __hfma2(h, g16, h2_of_bits(lo.x));
+                const float2 hv = __half22float2(h);
+                const float vx = hv.x * scl, vy = hv.y * scl;
+                acc[s].x = fmaf(vx, cs, fmaf(-vy, sn, acc[s].x));
+                acc[s].y = fmaf(vx, sn, fmaf(vy, cs, acc[s].y));
+                continue;
+            }
+            const float4 e01 = e[0], e23 = e[1];
+            const uint4 eh = *reinterpret_cast<const uint4*>(e + 2);
+            const float2 gg2 = make_float2(g, g);
+            if (MODE == MODE_FORWARD) {
+                // high-order part in packed BF16: h = ((E7 g + E6) g + E5) g + E4
+                const __nv_bfloat162 g16 = __float2bfloat162_rn(g);
+                __nv_bfloat162 h = __hfma2(b2_of_bits(eh.w), g16, b2_of_bits(eh.z));
+                h = __hfma2(h, g16, b2_of_bits(eh.y));
+                h = __hfma2(h, g16, b2_of_bits(eh.x));
+                float2 v = __bfloat1622float2(h);
+                v = ffma2(v, gg2, make_float2(e23.z, e23.w));
+                v = ffma2(v, gg2, make_float2(e23.x, e23.y));
+                v = ffma2(v, gg2, make_float2(e01.z, e01.w));
+                v = ffma2(v, gg2, make_float2(e01.x, e01.y));
+                acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
+                acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
+            } else {
+                // value and derivative in g (FP32): b = s(g), d = s'(g)
+                float2 b = __bfloat1622float2(b2_of_bits(eh.w));
+                float2 d = make_float2(0.f, 0.f);
+                const float2 c6 = __bfloat1622float2(b2_of_bits(eh.z)), c5 = __bfloat1622float2(b2_of_bits(eh.y)),
+                             c4 = __bfloat1622float2(b2_of_bits(eh.x));
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, c6);
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, c5);
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, c4);
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.z, e23.w));
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.x, e23.y));
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.z, e01.w));
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.x, e01.y));
+                // a = fs s' + j 2 pi fc s ;  r = Re{ conj(G) a exp(j phase) }  (0 outside the beam)
+                const float ax = fmaf(p.fs_f, d.x, -p.wfc * b.y);
+                const float ay = fmaf(p.fs_f, d.y, p.wfc * b.x);
+                const float Hx = fmaf(acc[s].x, cs, acc[s].y * sn);       // conj(G) exp(j phase)
+                const float Hy = fmaf(acc[s].x, sn, -acc[s].y * cs);
+                const float r = fmaf(Hx, ax, -Hy * ay);
+                rsum[MODE == MODE_OFFSET_GRAD ? s : 0] += r;
+                // receiver unit vector (R_R + d) / |R_R + d| times r
+                const float kr = r * rs;
+                const float dvs = fmaf((float)s, dvstep, dv0);
+                const float vx = fmaf(0.5f, tRx, dxv);
+                const float vy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvs);
+                const float vz = DIM3 ? fmaf(0.5f, tRz, dvs) : 0.5f * tRz;
+                gacc0 = fmaf(kr, vx, gacc0);
+                gacc1 = fmaf(kr, vy, gacc1);
+                gacc2 = fmaf(kr, vz, gacc2);
+            }
         }
-        warp_arrive(&ebar[0]);
-        aborted = *abort_flag != 0;
-    }
+    };
 
-    int prev_ping = -1;
-    int cur_ping = ping0, cur_ch = 0;     // (ping, channel) of the next pair, no divisions
-    for (int gg = 0; gg < ngroups && !aborted; ++gg) {
-        const int nxt = gg + 1;
-        if (nxt < ngroups) {
-            bool ok = true;
-            if (nxt >= 2) wait_bar(&ebar[2 + (nxt & 1)], ((nxt - 2) >> 1) & 1);   // readers of group nxt-2 done
-            if (nxt % GPS == 0) {
-                ok = wait_stage(nxt / GPS);
-                if (ok) hold_records(nxt / GPS);
-            }
-            if (ok && !*abort_flag) {
-                expand(nxt);
-                maybe_release(nxt);
-            }
-            warp_arrive(&ebar[nxt & 1]);
+    // ---- walk the stages group by group, expanding one group ahead
+    bool aborted = false;
+    int kc = 0, gi = 0, nkc = 0, lastkc = 1;
+    if (wait_stage(0)) {
+        nkc = st_count[0];
+        lastkc = st_last[0];
+        if (nkc > 0) {
+            hold_records(0);
+            expand(0, 0, nkc, 0);
+            if ((nkc + GROUP - 1) / GROUP == 1) release(0);
         }
-        wait_bar(&ebar[gg & 1], (gg >> 1) & 1);                  // rows of group gg complete
+    }
+    warp_arrive(&ebar[0]);
+    aborted = *abort_flag != 0;
+    int prev_ping = -1;
+    for (int G = 0; !aborted && nkc > 0; ++G) {
+        // the group after (kc, gi)
+        int kn = kc, gn = gi + 1, nkn = nkc, lastkn = lastkc;
+        bool have_next = true;
+        if (gn * GROUP >= nkc) {
+            if (lastkc) {
+                have_next = false;
+            } else {
+                kn = kc + 1;
+                gn = 0;
+                if (!wait_stage(kn)) {
+                    have_next = false;
+                } else {
+                    nkn = st_count[kn % NSTAGE];
+                    lastkn = st_last[kn % NSTAGE];
+                    have_next = nkn > 0;
+                }
+            }
+        }
+        if (have_next) {
+            if (G >= 1) wait_bar(&ebar[2 + ((G + 1) & 1)], ((G - 1) >> 1) & 1);   // readers of group G-1 done
+            if (!*abort_flag) {
+                // a new stage's records go to the hold buffer of stage kn - 2,
+                // whose last reader finished with group G - 1 at the latest
+                if (gn == 0) hold_records(kn);
+                expand(kn, gn, nkn, (G + 1) & 1);
+                if ((gn + 1) * GROUP >= nkn) release(kn);
+            }
+            warp_arrive(&ebar[(G + 1) & 1]);
+        }
+        wait_bar(&ebar[G & 1], (G >> 1) & 1);                  // rows of group G complete
         if (*abort_flag) {
             aborted = true;
             break;
         }
-        if (gg % GPS == 0) {
-            const float* hd = hold + ((gg / GPS) & 1) * NHOLD * PAIRS;
-#pragma unroll
-            for (int f = 0; f < NHOLD; ++f) r_cur[f] = hd[f * PAIRS + lane];
-        }
-        const int stage = gg / GPS;
-        const unsigned char* eb = ebuf + (gg & 1) * GROUP * ebuf_pair;
+        const float4* hq = reinterpret_cast<const float4*>(hold + (kc & 1) * PAIRS * HROW);
+        const unsigned char* eb = ebuf + (G & 1) * GROUP * ebuf_pair;
+        const int ng = min(GROUP, nkc - gi * GROUP);
 #pragma unroll 1
-        for (int j = 0; j < GROUP; ++j) {
-            const int pr = (gg % GPS) * GROUP + j;
-            if (stage * PAIRS + pr >= nq) break;
-            if (cur_ch == 0) {
-                const int ping = cur_ping;
+        for (int j = 0; j < ng; ++j) {
+            const int pr = gi * GROUP + j;
+            const float4* hr = hq + pr * (HROW / 4);
+            const float4 q3 = hr[3];
+            const int ping = __float_as_int(q3.y);
+            const int flags = BEAM ? __float_as_int(q3.z) : (FL_TX_FULL | FL_RX_FULL);
+            float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (BEAM) {
+                const float4 q4 = hr[4], q5 = hr[5];
+                rot[0] = q4.x; rot[1] = q4.y; rot[2] = q4.z; rot[3] = q4.w; rot[4] = q5.x; rot[5] = q5.y;
+            }
+            if (ping != prev_ping) {
                 if (prev_ping >= 0) flush_ping(prev_ping);
                 prev_ping = ping;
-                tT0 = __shfl_sync(0xffffffffu, r_cur[F_TX], pr);
-                tT1 = __shfl_sync(0xffffffffu, r_cur[F_TY], pr);
-                tT2 = __shfl_sync(0xffffffffu, r_cur[F_TZ], pr);
-                tNT2 = __shfl_sync(0xffffffffu, r_cur[F_NT2], pr);
-                tNT = __shfl_sync(0xffffffffu, r_cur[F_NT], pr);
-                const float Ax = DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv;
+                const float4 q2 = hr[2];
+                tT0 = q2.x;
+                tT1 = q2.y;
+                tT2 = q2.z;
+                tNT2 = q2.w;
+                tNT = q3.x;
+                const float tTv = DIM3 ? tT2 : tT1;
+                const float P0 = fmaf(tTv, dv0, DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv);
+                const float P1 = tTv * dvstep;
+                tmask = 0xffu;
 #pragma unroll
                 for (int s = 0; s < PX; ++s) {
-                    const float d2 = fmaf(dvar[s], dvar[s], d2c);
-                    const float a = DIM3 ? fmaf(tT2, dvar[s], d2) + Ax : fmaf(tT1, dvar[s], d2) + Ax;
+                    const float a = fmaf((float)s, P1, P0) + d2[s];
                     const float sm = tNT2 + a;
                     const float den = fmaf(sm, rsqrt_sfu(sm), tNT);
                     dT[s] = a * rcp_sfu(den);
+                    if (BEAM && !(flags & FL_TX_FULL)) {
+                        const float dvs = fmaf((float)s, dvstep, dv0);
+                        const float wx = fmaf(0.5f, tT0, dxv);
+                        const float wy = DIM3 ? fmaf(0.5f, tT1, dyv_c) : fmaf(0.5f, tT1, dvs);
+                        const float wz = DIM3 ? fmaf(0.5f, tT2, dvs) : 0.5f * tT2;
+                        if (!beam_sees(p, wx, wy, wz, rot)) tmask &= ~(1u << s);
+                    }
                 }
             }
-            const float tRx = __shfl_sync(0xffffffffu, r_cur[F_RX], pr);
-            const float tRy = __shfl_sync(0xffffffffu, r_cur[F_RY], pr);
-            const float tRz = __shfl_sync(0xffffffffu, r_cur[F_RZ], pr);
-            const float nR2 = __shfl_sync(0xffffffffu, r_cur[F_NR2], pr);
-            const float nR = __shfl_sync(0xffffffffu, r_cur[F_NR], pr);
-            const float uf = __shfl_sync(0xffffffffu, r_cur[F_UF], pr);
-            const float phr = __shfl_sync(0xffffffffu, r_cur[F_PH], pr);
-            const float scl = E16 ? __shfl_sync(0xffffffffu, r_cur[F_SCALE], pr) : 1.0f;
-            const float Ax = DIM3 ? fmaf(tRx, dxv, tRy * dyv_c) : tRx * dxv;
+            const float4 q0 = hr[0], q1 = hr[1];
             const unsigned char* erow = eb + j * ebuf_pair;
-#pragma unroll
-            for (int s = 0; s < PX; ++s) {
-                const float d2 = fmaf(dvar[s], dvar[s], d2c);
-                const float a = DIM3 ? fmaf(tRz, dvar[s], d2) + Ax : fmaf(tRy, dvar[s], d2) + Ax;
-                const float sm = nR2 + a;
-                const float rs = rsqrt_sfu(sm);                     // 1 / |R_R + d|
-                const float den = fmaf(sm, rs, nR);
-                const float D = fmaf(a, rcp_sfu(den), dT[s]);       // two-way differential path [m]
-                const float u = fmaf(D, p.fs_c, uf);                 // sample position rel. to floor(u_ref)
-                const float ph = fmaf(D, p.fc_c, phr);               // carrier phase [cycles]
-                float fl;
-                const int di = floor_magic(u, fl);
-                const float g = (u - fl) - 0.5f;
-                const unsigned pos = min((unsigned)(di + p.U), (unsigned)(p.npos - 1));
-                const float4* e = reinterpret_cast<const float4*>(erow + pos * EROW);
-                const float pt = __fadd_rn(ph, FLOOR_MAGIC) - FLOOR_MAGIC;   // rint(ph)
-                float sn, cs;
-                sincos_2pi(ph - pt, sn, cs);
-                if (E16) {
-                    // packed FP16 Horner over E_7 .. E_0, scale and accumulate in FP32
-                    const uint4 lo = *reinterpret_cast<const uint4*>(e), hi = *reinterpret_cast<const uint4*>(e + 1);
-                    const __half2 g16 = __float2half2_rn(g);
-                    __half2 h = __hfma2(h2_of_bits(hi.w), g16, h2_of_bits(hi.z));
-                    h = __hfma2(h, g16, h2_of_bits(hi.y));
-                    h = __hfma2(h, g16, h2_of_bits(hi.x));
-                    h = __hfma2(h, g16, h2_of_bits(lo.w));
-                    h = __hfma2(h, g16, h2_of_bits(lo.z));
-                    h = __hfma2(h, g16, h2_of_bits(lo.y));
-                    h = __hfma2(h, g16, h2_of_bits(lo.x));
-                    const float2 hv = __half22float2(h);
-                    const float vx = hv.x * scl, vy = hv.y * scl;
-                    acc[s].x = fmaf(vx, cs, fmaf(-vy, sn, acc[s].x));
-                    acc[s].y = fmaf(vx, sn, fmaf(vy, cs, acc[s].y));
-                    continue;
-                }
-                const float4 e01 = e[0], e23 = e[1];
-                const uint4 eh = *reinterpret_cast<const uint4*>(e + 2);
-                const float2 gg2 = make_float2(g, g);
-                if (MODE == MODE_FORWARD) {
-                    // high-order part in packed BF16: h = ((E7 g + E6) g + E5) g + E4
-                    const __nv_bfloat162 g16 = __float2bfloat162_rn(g);
-                    __nv_bfloat162 h = __hfma2(b2_of_bits(eh.w), g16, b2_of_bits(eh.z));
-                    h = __hfma2(h, g16, b2_of_bits(eh.y));
-                    h = __hfma2(h, g16, b2_of_bits(eh.x));
-                    float2 v = __bfloat1622float2(h);
-                    v = ffma2(v, gg2, make_float2(e23.z, e23.w));
-                    v = ffma2(v, gg2, make_float2(e23.x, e23.y));
-                    v = ffma2(v, gg2, make_float2(e01.z, e01.w));
-                    v = ffma2(v, gg2, make_float2(e01.x, e01.y));
-                    acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
-                    acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
-                } else {
-                    // value and derivative in g (FP32): b = s(g), d = s'(g)
-                    float2 b = __bfloat1622float2(b2_of_bits(eh.w));
-                    float2 d = make_float2(0.f, 0.f);
-                    const float2 c6 = __bfloat1622float2(b2_of_bits(eh.z)), c5 = __bfloat1622float2(b2_of_bits(eh.y)),
-                                 c4 = __bfloat1622float2(b2_of_bits(eh.x));
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, c6);
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, c5);
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, c4);
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.z, e23.w));
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.x, e23.y));
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.z, e01.w));
-                    d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.x, e01.y));
-                    // a = fs s' + j 2 pi fc s ;  r = Re{ conj(G) a exp(j phase) }
-                    const float ax = fmaf(p.fs_f, d.x, -p.wfc * b.y);
-                    const float ay = fmaf(p.fs_f, d.y, p.wfc * b.x);
-                    const float Hx = fmaf(acc[s].x, cs, acc[s].y * sn);       // conj(G) exp(j phase)
-                    const float Hy = fmaf(acc[s].x, sn, -acc[s].y * cs);
-                    const float r = fmaf(Hx, ax, -Hy * ay);
-                    rsum[MODE == MODE_OFFSET_GRAD ? s : 0] += r;
-                    // receiver unit vector (R_R + d) / |R_R + d| times r
-                    const float kr = r * rs;
-                    const float vx = fmaf(0.5f, tRx, dxv);
-                    const float vy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvar[s]);
-                    const float vz = DIM3 ? fmaf(0.5f, tRz, dvar[s]) : 0.5f * tRz;
-                    gacc0 = fmaf(kr, vx, gacc0);
-                    gacc1 = fmaf(kr, vy, gacc1);
-                    gacc2 = fmaf(kr, vz, gacc2);
-                }
-            }
-            if (++cur_ch == p.C) {
-                cur_ch = 0;
-                ++cur_ping;
-            }
+            if (!BEAM || (flags & (FL_TX_FULL | FL_RX_FULL)) == (FL_TX_FULL | FL_RX_FULL))
+                pixels(std::integral_constant<bool, false>{}, q0, q1, rot, 0u, erow);
+            else
+                pixels(std::integral_constant<bool, BEAM>{}, q0, q1, rot, (flags & FL_RX_FULL) ? 0u : 1u, erow);
         }
-        warp_arrive(&ebar[2 + (gg & 1)]);
+        warp_arrive(&ebar[2 + (G & 1)]);
+        if (!have_next) break;
+        kc = kn;
+        gi = gn;
+        nkc = nkn;
+        lastkc = lastkn;
     }
     if (aborted) return;
-    if (MODE == MODE_OFFSET_GRAD) {
+    if constexpr (MODE == MODE_OFFSET_GRAD) {
         if (prev_ping >= 0) flush_ping(prev_ping);
         return;
-    }
-
+    } else {
 #pragma unroll
     for (int s = 0; s < PX; ++s) {
         int lx, ly, lz;
@@ -644,6 +825,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         } else {
             *dst = acc[s];
         }
+    }
     }
 }
 

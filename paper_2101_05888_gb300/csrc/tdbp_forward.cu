@@ -27,8 +27,10 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
         set_error("pixel spacing too coarse: a tile's delay span needs %d samples (max 256)", seglen);
         return SAS_ERR_UNSUPPORTED;
     }
-    const int slot_bytes = ((seglen + 8) * elem + 127) / 128 * 128;
-    const size_t smem = smem_bytes(slot_bytes, npos);
+    const int npos_pad = (npos + RUN - 1) / RUN * RUN;
+    // expansion runs read up to RUN + 7 samples past a run start: pad the slot
+    const int slot_bytes = ((seglen + RUN + 8) * elem + 127) / 128 * 128;
+    const size_t smem = smem_bytes(slot_bytes, npos_pad);
     if (smem > 227 * 1024) {
         set_error("shared memory need %zu exceeds the per-block limit", smem);
         return SAS_ERR_UNSUPPORTED;
@@ -53,7 +55,15 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     prm.fs_f = (float)h->sig.fs;
     prm.wfc = (float)(2.0 * M_PI * h->sig.fc);
     prm.grad_scale = (float)(-2.0 / h->sig.c);
-    prm.U = U; prm.npos = npos; prm.seglen = seglen; prm.seg_align = align; prm.slot_bytes = slot_bytes;
+    prm.U = U; prm.npos = npos; prm.npos_pad = npos_pad; prm.seglen = seglen; prm.seg_align = align; prm.slot_bytes = slot_bytes;
+    prm.rotc = h->d_rotc;
+    prm.beam = h->beam_tan > 0.0;
+    prm.beam_tan = (float)h->beam_tan;
+    prm.beam_side = (float)h->beam_side;
+    prm.cull = h->d_cull;
+    prm.hx = (float)hx;
+    prm.hy = (float)hy;
+    prm.hz = (float)hz;
     prm.skip_copies = h->debug_skip_copies;
     prm.wait_ns = (unsigned long long)(h->debug_wait_ms > 0 ? h->debug_wait_ms : 4000) * 1000000ull;
     const long long ntiles = (long long)prm.tiles_x * prm.tiles_y * prm.tiles_z;
@@ -81,7 +91,7 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
 
 template <typename ET, bool DIM3, int MODE>
 static int launch_one(const Setup& S, cudaStream_t st) {
-    auto kern = tdbp_kernel<ET, DIM3, MODE>;
+    auto kern = S.prm.beam ? tdbp_kernel<ET, DIM3, MODE, true> : tdbp_kernel<ET, DIM3, MODE, false>;
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());

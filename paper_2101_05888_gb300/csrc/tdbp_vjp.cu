@@ -8,7 +8,7 @@ namespace core {
 
 template <typename ET, bool DIM3, int MODE>
 static int launch_one_grad(const Setup& S, cudaStream_t st) {
-    auto kern = tdbp_kernel<ET, DIM3, MODE>;
+    auto kern = S.prm.beam ? tdbp_kernel<ET, DIM3, MODE, true> : tdbp_kernel<ET, DIM3, MODE, false>;
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());
@@ -62,6 +62,8 @@ int launch_offset_grad(sas_geometry_t h, const sas_grid& g, const float2* grad_i
         SAS_CUDA(cudaMalloc(&h->d_scratch, need));
         h->scratch_bytes = need;
     }
+    // (tile, ping) partials with no pair inside the beams are never written
+    SAS_CUDA(cudaMemsetAsync(h->d_scratch, 0, need, st));
     S.prm.gimage = grad_image;
     S.prm.partials = (double*)h->d_scratch;
     rc = core::launch_mode<core::MODE_OFFSET_GRAD>(S, h->echo_dtype, dim3, st);

@@ -190,3 +190,105 @@ def test_complex64_echo_read_in_place():
     a = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix)
     b = oracle.backproject(tx, rx, SIG, e.astype(np.complex128), 8, 4.0, pix)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("side", [1, -1])
+def test_beam_mask_matches_brute_force(side):
+    """Beam field of view: the C tangent-form test against the NumPy arctan2
+    restatement, with attitude, on pixels both inside and outside the beam."""
+    P, C = 10, 2
+    pos, att, txl, rxl = _scene(P=P, C=C, seed=30)
+    att[:, 2] += 0.05                         # some yaw so the beam edge moves with the ping
+    tx, rx = oracle.sensor_positions(pos, att, txl, rxl)
+    e = _random_echo(P, C, SIG.n_samples, 31)
+    y0 = 16.0 * side
+    pix = oracle.grid_points(-6.0, y0, 0.0, 0.5, 0.05, 0.0, 28, 12, 1)   # spans far forward / aft of the track
+    width = np.deg2rad(40.0)
+    a = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, att=att, beam_width=width, side=side)
+    m = brute.beam_mask(att, tx, rx, pix, width, side)
+    assert 0.1 < m.mean() < 0.9
+    b = brute.backproject(tx, rx, SIG.fc, SIG.fs, SIG.c, SIG.t0, e, 8, 4.0, pix, mask=m)
+    assert oracle.rel_l2(a, b) < 1e-10
+
+
+def test_beam_off_is_unmasked_and_wrong_side_is_empty():
+    pos, att, txl, rxl = _scene(P=6, C=2, seed=32)
+    tx, rx = oracle.sensor_positions(pos, att, txl, rxl)
+    e = _random_echo(6, 2, SIG.n_samples, 33)
+    pix = _pixels()
+    full = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix)
+    assert np.array_equal(full, oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, att=att, beam_width=0.0))
+    wide = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, att=att, beam_width=np.deg2rad(179.0), side=1)
+    assert oracle.rel_l2(wide, full) < 1e-12          # the scene is broadside to starboard
+    assert np.abs(oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, att=att, beam_width=np.deg2rad(179.0),
+                                     side=-1)).max() == 0.0
+
+
+def test_beam_adjoint_dot_product_and_gradient():
+    """With the beam on, the masked adjoint stays the exact adjoint of the
+    masked sum, and the masked offset gradient matches central differences."""
+    P, C = 6, 2
+    pos, att, txl, rxl = _scene(P=P, C=C, seed=34)
+    width = np.deg2rad(30.0)
+    tx, rx = oracle.sensor_positions(pos, att, txl, rxl)
+    e = _random_echo(P, C, SIG.n_samples, 35)
+    pix = oracle.grid_points(-7.0, 16.0, 0.0, 1.0, 0.05, 0.0, 14, 8, 1)   # beam edges at about x = -4, +4.8
+    rng = np.random.default_rng(36)
+    img = rng.normal(size=pix.shape[0]) + 1j * rng.normal(size=pix.shape[0])
+    kw = dict(att=att, beam_width=width, side=1)
+    Be = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, **kw)
+    BhI = oracle.backproject_adjoint(tx, rx, SIG, img, 8, 4.0, pix, **kw)
+    m = brute.beam_mask(att, tx, rx, pix, width, 1)
+    assert 0.1 < m.mean() < 0.9                       # the beam edge crosses the pixels
+    lhs, rhs = np.vdot(Be, img), np.vdot(e, BhI)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    # gradient of S through the masked sum (the mask moves with the offsets,
+    # but central differences of size h rarely cross its edge)
+    off = rng.normal(0, 0.002, size=(P, 3))
+
+    def S(o):
+        t, r = oracle.sensor_positions(pos, att, txl, rxl, o)
+        return oracle.sharpness(oracle.backproject(t, r, SIG, e, 8, 4.0, pix, **kw))[0]
+
+    t, r = oracle.sensor_positions(pos, att, txl, rxl, off)
+    _, g = oracle.sharpness(oracle.backproject(t, r, SIG, e, 8, 4.0, pix, **kw), want_grad=True)
+    grad = oracle.vjp_offsets(t, r, SIG, e, 8, 4.0, pix, g, **kw)
+    h = 1e-7
+    fd = np.zeros((P, 3))
+    for i in range(P):
+        for a in range(3):
+            op, om = off.copy(), off.copy()
+            op[i, a] += h
+            om[i, a] -= h
+            fd[i, a] = (S(op) - S(om)) / (2 * h)
+    assert oracle.rel_l2(grad, fd) < 1e-5
+
+
+def test_beam_split_bounds_every_nearby_decision():
+    """Margin split of the beam-limited sum: eps -> 0 gives the plain sum with
+    no ambiguous terms; beam widths perturbed by a relative +-eps (each moves
+    the decision margins by well under eps) change the image only through
+    ambiguous terms, so |I_perturbed - sure| <= amb pixel by pixel, and they do
+    change it; the ambiguous sum grows with eps."""
+    P, C = 10, 2
+    pos, att, txl, rxl = _scene(P=P, C=C, seed=37)
+    att[:, 2] += 0.05
+    tx, rx = oracle.sensor_positions(pos, att, txl, rxl)
+    e = _random_echo(P, C, SIG.n_samples, 38)
+    pix = oracle.grid_points(-6.0, 16.0, 0.0, 0.5, 0.05, 0.0, 28, 12, 1)
+    width = np.deg2rad(40.0)
+    kw = dict(att=att, side=1)
+    plain = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, beam_width=width, **kw)
+    sure0, amb0 = oracle.backproject_beam_split(tx, rx, SIG, e, 8, 4.0, pix, att, width, 1, eps=1e-15)
+    assert amb0.max() == 0.0 and oracle.rel_l2(sure0, plain) < 1e-14
+    eps = 1e-2
+    sure, amb = oracle.backproject_beam_split(tx, rx, SIG, e, 8, 4.0, pix, att, width, 1, eps=eps)
+    assert np.count_nonzero(amb) > 0
+    changed = 0
+    for f in (1.0 - eps, 1.0 + eps):
+        pert = oracle.backproject(tx, rx, SIG, e, 8, 4.0, pix, beam_width=width * f, **kw)
+        assert np.all(np.abs(pert - sure) <= amb + 1e-9)
+        changed += np.count_nonzero(np.abs(pert - plain) > 1e-9)
+    assert changed > 0
+    _, amb_small = oracle.backproject_beam_split(tx, rx, SIG, e, 8, 4.0, pix, att, width, 1, eps=eps / 10)
+    assert np.all(amb_small <= amb + 1e-12) and amb_small.sum() < amb.sum()
