@@ -191,7 +191,7 @@ def config_of(w, args):
     g = w.grid
     return {"workload": w.name, "pings": w.n_pings, "rx": w.n_rx, "samples": w.n_samples,
             "pixels": "%dx%dx%d" % (g.nx, g.ny, g.nz), "pixel_m": g.dx, "taps": 8,
-            "interp": "kaiser_sinc beta=%g (Farrow degree 7)" % BETA, "echo": args.echo,
+            "interp": "kaiser_sinc beta=%g (Farrow degree 5)" % BETA, "echo": args.echo,
             "updates_per_step": w.updates, "l2": l2_note(w, args), "parallelism": "replicas",
             **({"beam_deg": args.beam_deg,
                 "beam_note": "value counts every pixel.ping.channel term of the image, culled ones included; "

@@ -32,7 +32,7 @@ enum : uint32_t { DEV_TIMEOUT = 1u };
 // so the interpolated value is a polynomial in g whose coefficients are FIR
 // outputs of the echo:  s = sum_p g^p E_p[i0],  E_p[i] = sum_m coef[m][p] e[i + k_m].
 constexpr int TAPS = 8;
-constexpr int NP = 8;            // polynomial degree 7
+constexpr int NP = 6;            // polynomial degree 5
 struct FarrowCoef {
     float c[TAPS][NP];
 };

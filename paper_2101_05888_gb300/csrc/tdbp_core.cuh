@@ -19,21 +19,20 @@
 //    Samples outside the row are zero-filled by the copy engine.
 //  * consumers, 8 pixels a thread:
 //    - Farrow expansion for 4 pairs at a time: the interpolator's taps are
-//      degree-7 polynomials of g = f - 1/2, so s = sum_p g^p E_p[floor u] with
+//      degree-5 polynomials of g = f - 1/2, so s = sum_p g^p E_p[floor u] with
 //      E_p[i] = sum_m coef[m][p] e[i + k_m], computed once per (pair, tile)
 //      for every integer position the tile can reach.  Complex64 echoes:
-//      E_0..E_3 are kept in FP32 and E_4..E_7 (weighted by |g|^p <= 1/16) in
-//      BF16 (FP32 exponent range, so no overflow at any echo amplitude), and
-//      the forward pass evaluates that tail in packed BF16.  16-bit echoes
-//      (rows normalised to |e| <= 1, so |E_p| <= 5.2): all eight in FP16 and
-//      the forward Horner in packed FP16, the row scale applied afterwards in
-//      FP32.  One 48-byte row per position either way.
+//      E_0..E_5 in FP32, one 48-byte row per position, Horner in packed
+//      FP32.  16-bit echoes (rows normalised to |e| <= 1, so |E_p| stays
+//      near 1): E_0..E_5 in FP16 (24 bytes of the row) and the forward
+//      Horner in packed FP16, the row scale applied afterwards in FP32.
 //    - per pixel and pair, with the pair's reference terms broadcast by warp
 //      shuffle: differential range dr = (2 R.d + |d|^2) / (|R + d| + |R|), an
 //      exact identity evaluated in FP32 on small quantities (d = x - x0); u
 //      and the phase from the reference values plus dr-derived offsets;
-//      floor/fraction on the FP32 pipe; three 16-byte shared loads; Horner in
-//      g; SFU rsqrt, rcp, sin, cos.
+//      floor/fraction on the FP32 pipe; three 16-byte shared loads (one 16-
+//      and one 8-byte load for FP16 rows); Horner in g; SFU rsqrt, rcp, sin,
+//      cos.
 //  * every mbarrier wait is bounded in wall time: on expiry the CTA records a
 //    timeout in the status word, stops, and the producer waits (bounded) for
 //    the copies it has in flight before exiting.
@@ -54,9 +53,9 @@ constexpr int NSTAGE = 3;               // copy ring depth
 constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
-constexpr int EROW = 48;                // bytes per Farrow row: E0..E3 float2, E4..E7 bfloat162
+constexpr int EROW = 48;                // bytes per Farrow row: E0..E5 float2 (FP16 rows: E0..E5 half2)
 constexpr int RUN = 10;                 // Farrow positions per expansion run
-constexpr int NRUNSLOT = NCONS / 8;     // expansion runs in flight (one power p per thread)
+constexpr int NRUNSLOT = NCONS / NP;    // expansion runs in flight (one power p per thread)
 constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
 enum { MODE_FORWARD = 0, MODE_OFFSET_GRAD = 1 };
@@ -161,16 +160,11 @@ __device__ __forceinline__ void sincos_2pi(float x, float& sn, float& cs) {
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(a));
 }
 
-__device__ __forceinline__ uint32_t bits_of(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
-__device__ __forceinline__ uint32_t bits_of(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
 
 __device__ __forceinline__ __half2 h2_of_bits(uint32_t b) {
     return *reinterpret_cast<__half2*>(&b);
 }
 
-__device__ __forceinline__ __nv_bfloat162 b2_of_bits(uint32_t b) {
-    return *reinterpret_cast<__nv_bfloat162*>(&b);
-}
 
 // FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
 // R_T = x0 - x_TX (ping i = q / C), R_R = x0 - x_RX (pair q).
@@ -466,15 +460,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // RUN consecutive positions of one pair of the group from a sliding window
     // of RUN + 7 samples.  Runs never need a bounds test: the Farrow buffer and
     // the echo slot are padded to whole runs (padding values are never read).
-    const int Ep = ct & 7;
-    const int Erun = ct >> 3;                       // 0 .. NRUNSLOT - 1
+    const int Ep = ct % NP;
+    const int Erun = ct < NRUNSLOT * NP ? ct / NP : (1 << 30);   // 0 .. NRUNSLOT - 1; the rest idle
     const int runs_per_pair = (p.npos + RUN - 1) / RUN;
     float2 cc2[TAPS];                               // this thread's coefficients, packed (c, c)
 #pragma unroll
     for (int m = 0; m < TAPS; ++m) cc2[m] = make_float2(coef_s[m * NP + Ep], coef_s[m * NP + Ep]);
-    // byte offset of E_p in a row and its format (FP32 pair, or a packed 16-bit pair)
-    const bool e_wide = !E16 && Ep < 4;
-    const int e_off = E16 ? Ep * 4 : (Ep < 4 ? Ep * 8 : 32 + (Ep - 4) * 4);
+    // byte offset of E_p in a row (FP32 pair, or a packed FP16 pair)
+    const int e_off = E16 ? Ep * 4 : Ep * 8;
 
     // Farrow rows of group gi of stage kst (npairs pairs in the stage) into buffer b
     auto expand = [&](int kst, int gi, int npairs, int b) {
@@ -499,9 +492,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 float2 e = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
-                const uint32_t narrow = E16 ? bits_of(__floats2half2_rn(e.x, e.y)) : bits_of(__floats2bfloat162_rn(e.x, e.y));
-                if (e_wide) *reinterpret_cast<float2*>(dst + kq * EROW) = e;
-                if (!e_wide) *reinterpret_cast<uint32_t*>(dst + kq * EROW) = narrow;
+                if (E16)
+                    *reinterpret_cast<__half2*>(dst + kq * EROW) = __floats2half2_rn(e.x, e.y);
+                else
+                    *reinterpret_cast<float2*>(dst + kq * EROW) = e;
             }
         }
     };
@@ -633,12 +627,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 cs = 0.f;
             }
             if (E16) {
-                // packed FP16 Horner over E_7 .. E_0, scale and accumulate in FP32
-                const uint4 lo = *reinterpret_cast<const uint4*>(e), hi = *reinterpret_cast<const uint4*>(e + 1);
+                // packed FP16 Horner over E_5 .. E_0, scale and accumulate in FP32
+                const uint4 lo = *reinterpret_cast<const uint4*>(e);
+                const uint2 hi = *reinterpret_cast<const uint2*>(e + 1);
                 const __half2 g16 = __float2half2_rn(g);
-                __half2 h = __hfma2(h2_of_bits(hi.w), g16, h2_of_bits(hi.z));
-                h = __hfma2(h, g16, h2_of_bits(hi.y));
-                h = __hfma2(h, g16, h2_of_bits(hi.x));
+                __half2 h = __hfma2(h2_of_bits(hi.y), g16, h2_of_bits(hi.x));
                 h = __hfma2(h, g16, h2_of_bits(lo.w));
                 h = __hfma2(h, g16, h2_of_bits(lo.z));
                 h = __hfma2(h, g16, h2_of_bits(lo.y));
@@ -649,16 +642,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 acc[s].y = fmaf(vx, sn, fmaf(vy, cs, acc[s].y));
                 continue;
             }
-            const float4 e01 = e[0], e23 = e[1];
-            const uint4 eh = *reinterpret_cast<const uint4*>(e + 2);
+            const float4 e01 = e[0], e23 = e[1], e45 = e[2];
             const float2 gg2 = make_float2(g, g);
             if (MODE == MODE_FORWARD) {
-                // high-order part in packed BF16: h = ((E7 g + E6) g + E5) g + E4
-                const __nv_bfloat162 g16 = __float2bfloat162_rn(g);
-                __nv_bfloat162 h = __hfma2(b2_of_bits(eh.w), g16, b2_of_bits(eh.z));
-                h = __hfma2(h, g16, b2_of_bits(eh.y));
-                h = __hfma2(h, g16, b2_of_bits(eh.x));
-                float2 v = __bfloat1622float2(h);
+                // packed FP32 Horner over E_5 .. E_0
+                float2 v = ffma2(make_float2(e45.z, e45.w), gg2, make_float2(e45.x, e45.y));
                 v = ffma2(v, gg2, make_float2(e23.z, e23.w));
                 v = ffma2(v, gg2, make_float2(e23.x, e23.y));
                 v = ffma2(v, gg2, make_float2(e01.z, e01.w));
@@ -666,14 +654,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
                 acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
             } else {
-                // value and derivative in g (FP32): b = s(g), d = s'(g)
-                float2 b = __bfloat1622float2(b2_of_bits(eh.w));
+                // value and derivative in g: b = s(g), d = s'(g)
+                float2 b = make_float2(e45.z, e45.w);
                 float2 d = make_float2(0.f, 0.f);
-                const float2 c6 = __bfloat1622float2(b2_of_bits(eh.z)), c5 = __bfloat1622float2(b2_of_bits(eh.y)),
-                             c4 = __bfloat1622float2(b2_of_bits(eh.x));
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, c6);
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, c5);
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, c4);
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e45.x, e45.y));
                 d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.z, e23.w));
                 d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.x, e23.y));
                 d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.z, e01.w));
