@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
         // s steps, in FP32), so that both take identical beam decisions
         const float dv0 = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : dyv_c;
         const float dvstep = DIM3 ? (float)p.dz : (float)(4.0 * p.dy);
-        d2c = DIM3 ? dxv * dxv + dyv_c * dyv_c : dxv * dxv;
+        d2c = fixed_d2<DIM3>(dxv, dyv_c);
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
             T::pixel(ct, s, lx, ly, lz);
@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                         const float tT2 = __shfl_sync(0xffffffffu, r[F_TZ], pr);
                         const float nT2 = __shfl_sync(0xffffffffu, r[F_NT2], pr);
                         const float nT = __shfl_sync(0xffffffffu, r[F_NT], pr);
-                        const float Ax = DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv;
+                        const float Ax = fixed_dot<DIM3>(tT0, tT1, dxv, dyv_c);
 #pragma unroll
                         for (int s = 0; s < PX; ++s) {
                             const float d2 = fmaf(dvar[s], dvar[s], d2c);
-                            const float a = DIM3 ? fmaf(tT2, dvar[s], d2) + Ax : fmaf(tT1, dvar[s], d2) + Ax;
+                            const float a = __fadd_rn(fmaf(DIM3 ? tT2 : tT1, dvar[s], d2), Ax);
                             const float sm = nT2 + a;
                             dT[s] = a * rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nT));
                         }
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                     const float nR = __shfl_sync(0xffffffffu, r[F_NR], pr);
                     const float ufc = __shfl_sync(0xffffffffu, r[F_UF], pr);
                     const float phr = __shfl_sync(0xffffffffu, r[F_PH], pr);
-                    const float Ax = DIM3 ? fmaf(tRx, dxv, tRy * dyv_c) : tRx * dxv;
+                    const float Ax = fixed_dot<DIM3>(tRx, tRy, dxv, dyv_c);
                     float2* Aj = A + j * p.npos * NP;
                     float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                                 continue;
                         }
                         const float d2 = fmaf(dvar[s], dvar[s], d2c);
-                        const float a = DIM3 ? fmaf(tRz, dvar[s], d2) + Ax : fmaf(tRy, dvar[s], d2) + Ax;
+                        const float a = __fadd_rn(fmaf(DIM3 ? tRz : tRy, dvar[s], d2), Ax);
                         const float sm = nR2 + a;
                         const float D = fmaf(a, rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nR)), dT[s]);
                         const float v = fmaf(D, p.fs_c, ufc);              // u - 1/2

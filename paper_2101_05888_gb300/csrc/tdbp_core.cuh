@@ -87,6 +87,7 @@ struct KParams {
     int P, C;
     double t0, fs, fc, inv_c;
     float fs_c, fc_c;       // fs/c, fc/c
+    float2 fs_c2, fc_c2;    // the same, duplicated for packed pixel pairs
     float fs_f, wfc;        // fs, 2 pi fc
     float grad_scale;       // -2/c (factor 2 of dL/dp = 2 Re(...), -1/c of dtau/dp)
     // beam field of view (Sec. II-C): sensor sees x iff b = R^T (x - sensor) has
@@ -152,13 +153,16 @@ __device__ __forceinline__ float rcp_sfu(float x) {
     return y;
 }
 
-// sin and cos of 2 pi x on the SFU; callers reduce x to [-1/2, 1/2] first
-// (the SFU approximations are accurate on [-pi, pi])
-__device__ __forceinline__ void sincos_2pi(float x, float& sn, float& cs) {
-    const float a = x * 6.28318530717958647f;
+// sin and cos on the SFU; callers reduce the argument to [-pi, pi] first
+// (the range on which the SFU approximations are accurate)
+__device__ __forceinline__ void sincos_sfu(float a, float& sn, float& cs) {
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(a));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(a));
 }
+__device__ __forceinline__ void sincos_2pi(float x, float& sn, float& cs) {
+    sincos_sfu(x * 6.28318530717958647f, sn, cs);
+}
+constexpr float TWO_PI_F = 6.28318530717958647f;
 
 
 __device__ __forceinline__ __half2 h2_of_bits(uint32_t b) {
@@ -239,6 +243,19 @@ __device__ __forceinline__ bool beam_sees(const KParams& p, float wx, float wy, 
     const float bx = fmaf(c[0], wx, fmaf(c[1], wy, c[2] * wz));
     const float by = p.beam_side * fmaf(c[3], wx, fmaf(c[4], wy, c[5] * wz));
     return by > 0.f && fabsf(bx) <= p.beam_tan * by;
+}
+
+// Pixel offsets d from the tile centre: the fixed part of |d|^2 and of 2R.d
+// (x, and y in 3D; the varying coordinate is added per slot as
+// a = fma(2R_var, d_var, fma(d_var, d_var, fixed_d2)) + fixed_dot).  Written
+// with explicit roundings so that every kernel evaluates the same FP32 path.
+template <bool DIM3>
+__device__ __forceinline__ float fixed_d2(float dx, float dy) {
+    return DIM3 ? fmaf(dx, dx, __fmul_rn(dy, dy)) : __fmul_rn(dx, dx);
+}
+template <bool DIM3>
+__device__ __forceinline__ float fixed_dot(float tx, float ty, float dx, float dy) {
+    return DIM3 ? fmaf(tx, dx, __fmul_rn(ty, dy)) : __fmul_rn(tx, dx);
 }
 
 // Shared-memory size and launch geometry, host side.
@@ -426,7 +443,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // pixel offsets from the tile centre: x (and y in 3D) fixed per thread; the
     // slot s moves along y (2D, 4 rows a slot) or z (3D): d_var(s) = dv0 + s dvstep
     float dxv, dyv_c, dv0, dvstep;
-    float d2[PX], dT[PX];                 // |d|^2 per pixel; transmitter differential range of the ping
+    // per slot s: the varying offset d_var(s), |d|^2 and the transmitter
+    // differential range of the current ping, held as pairs of slots (2k, 2k+1)
+    // for the packed geometry.  The offsets are formed exactly as the adjoint
+    // kernel forms them (slot_offsets), so both evaluate identical paths.
+    float2 dvp[PX / 2], d2p[PX / 2], dTp[PX / 2];
+#define PXS(arr, s) (((s) & 1) ? arr[(s) >> 1].y : arr[(s) >> 1].x)
     float2 acc[PX];                       // forward: image accumulators; gradient: G(x)
     float rsum[MODE == MODE_OFFSET_GRAD ? PX : 1];
     {
@@ -436,13 +458,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         dyv_c = (float)((ty0 + ly - cy) * p.dy);
         dv0 = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : dyv_c;
         dvstep = DIM3 ? (float)p.dz : (float)(4.0 * p.dy);
+        const float d2c = fixed_d2<DIM3>(dxv, dyv_c);
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
             T::pixel(ct, s, lx, ly, lz);
-            const double ddx = (tx0 + lx - cx) * p.dx, ddy = (ty0 + ly - cy) * p.dy;
-            const double ddz = DIM3 ? (tz0 + lz - cz) * p.dz : 0.0;
-            d2[s] = (float)(ddx * ddx + ddy * ddy + ddz * ddz);
-            dT[s] = 0.f;
+            const float dvs = fmaf((float)s, dvstep, dv0);
+            PXS(dvp, s) = dvs;
+            PXS(d2p, s) = fmaf(dvs, dvs, d2c);
+            PXS(dTp, s) = 0.f;
             if (MODE == MODE_FORWARD) {
                 acc[s] = make_float2(0.f, 0.f);
             } else {
@@ -528,15 +551,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     auto flush_ping = [&](int ping) {
         if (MODE != MODE_OFFSET_GRAD) return;
         const float tTv = DIM3 ? tT2 : tT1;
-        const float P0 = fmaf(tTv, dv0, DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv);
-        const float P1 = tTv * dvstep;
+        const float X = fixed_dot<DIM3>(tT0, tT1, dxv, dyv_c);
         float hx = 0.5f * tT0 + dxv;
         float hy = DIM3 ? 0.5f * tT1 + dyv_c : 0.f;
         float hz = DIM3 ? 0.f : 0.5f * tT2;
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
-            const float dvs = fmaf((float)s, dvstep, dv0);
-            const float a = fmaf((float)s, P1, P0) + d2[s];
+            const float dvs = PXS(dvp, s);
+            const float a = __fadd_rn(fmaf(tTv, dvs, PXS(d2p, s)), X);
             const float sm = tNT2 + a;
             const float kk = rsum[MODE == MODE_OFFSET_GRAD ? s : 0] * rsqrt_sfu(sm);   // r / |R_T + d|
             const float vy = DIM3 ? hy : 0.5f * tT1 + dvs;
@@ -585,7 +607,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
     };
 
-    // per-pixel work of one pair; MASKED: apply the beam test per pixel
+    // per-pixel work of one pair; MASKED: apply the beam test per pixel.  The
+    // geometry runs on pixel pairs (2k, 2k+1) in packed FP32x2: differential
+    // path, sample position and carrier phase, the fraction and phase
+    // reductions; the SFU, the Farrow rows and the accumulation per pixel.
     auto pixels = [&](auto masked, const float4 q0, const float4 q1, const float* rot, uint32_t rmask_needed,
                       const unsigned char* erow) {
         constexpr bool MASKED = decltype(masked)::value;
@@ -593,35 +618,45 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         const float nR = q1.x, ufc = q1.y, phr = q1.z;
         const float scl = E16 ? q1.w : 1.0f;
         const float tRv = DIM3 ? tRz : tRy;
-        const float P0 = fmaf(tRv, dv0, DIM3 ? fmaf(tRx, dxv, tRy * dyv_c) : tRx * dxv);
-        const float P1 = tRv * dvstep;
+        const float X = fixed_dot<DIM3>(tRx, tRy, dxv, dyv_c);
+        const float2 Xv = make_float2(X, X), tRvv = make_float2(tRv, tRv);
+        const float2 nR2v = make_float2(nR2, nR2), nRv = make_float2(nR, nR);
+        const float2 ufv = make_float2(ufc, ufc), phv = make_float2(phr, phr);
+        const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC), twopi2 = make_float2(TWO_PI_F, TWO_PI_F);
 #pragma unroll
-        for (int s = 0; s < PX; ++s) {
+        for (int k = 0; k < PX / 2; ++k) {
+            const float2 a = fadd2(ffma2(tRvv, dvp[k], d2p[k]), Xv);       // 2 R.d + |d|^2
+            const float2 sm = fadd2(a, nR2v);                             // |R_R + d|^2
+            const float2 rs = make_float2(rsqrt_sfu(sm.x), rsqrt_sfu(sm.y));
+            const float2 den = ffma2(sm, rs, nRv);                        // |R_R + d| + |R_R|
+            const float2 rc = make_float2(rcp_sfu(den.x), rcp_sfu(den.y));
+            const float2 D = ffma2(a, rc, dTp[k]);                        // two-way differential path [m]
+            const float2 v = ffma2(D, p.fs_c2, ufv);                      // u - 1/2, rel. to floor(u_ref)
+            const float2 ph = ffma2(D, p.fc_c2, phv);                     // carrier phase [cycles]
+            // the nearest integer of u - 1/2 is floor(u): it sits in the mantissa of
+            // t = v + 1.5*2^23 (round to nearest), and g = v - that = frac(u) - 1/2;
+            // the phase is reduced to [-1/2, 1/2] cycles the same way
+            const float2 t = fadd2(v, magic2);
+            const float2 g2 = fsub2(v, fsub2(t, magic2));
+            const float2 x2 = fmul2(fsub2(ph, fsub2(fadd2(ph, magic2), magic2)), twopi2);   // [-pi, pi]
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+            const int s = 2 * k + j;
+            const float g = j ? g2.y : g2.x;
+            const float tj = j ? t.y : t.x;
             bool seen = true;
             if (MASKED) {
-                const float dvs = fmaf((float)s, dvstep, dv0);
+                const float dvs = PXS(dvp, s);
                 const float wx = fmaf(0.5f, tRx, dxv);
                 const float wy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvs);
                 const float wz = DIM3 ? fmaf(0.5f, tRz, dvs) : 0.5f * tRz;
                 seen = ((tmask >> s) & 1u) && (!rmask_needed || beam_sees(p, wx, wy, wz, rot));
             }
-            const float a = fmaf((float)s, P1, P0) + d2[s];       // 2 R.d + |d|^2
-            const float sm = nR2 + a;
-            const float rs = rsqrt_sfu(sm);                     // 1 / |R_R + d|
-            const float den = fmaf(sm, rs, nR);
-            const float D = fmaf(a, rcp_sfu(den), dT[s]);       // two-way differential path [m]
-            const float v = fmaf(D, p.fs_c, ufc);                // u - 1/2, rel. to floor(u_ref)
-            const float ph = fmaf(D, p.fc_c, phr);               // carrier phase [cycles]
-            // the nearest integer of u - 1/2 is floor(u): it sits in the mantissa of
-            // t = v + 1.5*2^23 (round to nearest), and g = v - that = frac(u) - 1/2
-            const float t = __fadd_rn(v, FLOOR_MAGIC);
-            const float g = v - (t - FLOOR_MAGIC);
-            const unsigned pos = min((unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - p.U)),
+            const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - p.U)),
                                      (unsigned)(p.npos - 1));
             const float4* e = reinterpret_cast<const float4*>(erow + pos * EROW);
-            const float pt = __fadd_rn(ph, FLOOR_MAGIC) - FLOOR_MAGIC;   // nearest integer
             float sn, cs;
-            sincos_2pi(ph - pt, sn, cs);                                // argument in [-pi, pi]
+            sincos_sfu(j ? x2.y : x2.x, sn, cs);
             if (MASKED && !seen) {
                 sn = 0.f;
                 cs = 0.f;
@@ -670,14 +705,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 const float r = fmaf(Hx, ax, -Hy * ay);
                 rsum[MODE == MODE_OFFSET_GRAD ? s : 0] += r;
                 // receiver unit vector (R_R + d) / |R_R + d| times r
-                const float kr = r * rs;
-                const float dvs = fmaf((float)s, dvstep, dv0);
+                const float kr = r * (j ? rs.y : rs.x);
+                const float dvs = PXS(dvp, s);
                 const float vx = fmaf(0.5f, tRx, dxv);
                 const float vy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvs);
                 const float vz = DIM3 ? fmaf(0.5f, tRz, dvs) : 0.5f * tRz;
                 gacc0 = fmaf(kr, vx, gacc0);
                 gacc1 = fmaf(kr, vy, gacc1);
                 gacc2 = fmaf(kr, vz, gacc2);
+            }
             }
         }
     };
@@ -757,17 +793,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 tNT2 = q2.w;
                 tNT = q3.x;
                 const float tTv = DIM3 ? tT2 : tT1;
-                const float P0 = fmaf(tTv, dv0, DIM3 ? fmaf(tT0, dxv, tT1 * dyv_c) : tT0 * dxv);
-                const float P1 = tTv * dvstep;
+                const float X = fixed_dot<DIM3>(tT0, tT1, dxv, dyv_c);
                 tmask = 0xffu;
 #pragma unroll
                 for (int s = 0; s < PX; ++s) {
-                    const float a = fmaf((float)s, P1, P0) + d2[s];
+                    const float a = __fadd_rn(fmaf(tTv, PXS(dvp, s), PXS(d2p, s)), X);
                     const float sm = tNT2 + a;
                     const float den = fmaf(sm, rsqrt_sfu(sm), tNT);
-                    dT[s] = a * rcp_sfu(den);
+                    PXS(dTp, s) = a * rcp_sfu(den);
                     if (BEAM && !(flags & FL_TX_FULL)) {
-                        const float dvs = fmaf((float)s, dvstep, dv0);
+                        const float dvs = PXS(dvp, s);
                         const float wx = fmaf(0.5f, tT0, dxv);
                         const float wy = DIM3 ? fmaf(0.5f, tT1, dyv_c) : fmaf(0.5f, tT1, dvs);
                         const float wz = DIM3 ? fmaf(0.5f, tT2, dvs) : 0.5f * tT2;

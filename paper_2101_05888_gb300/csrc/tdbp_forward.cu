@@ -52,6 +52,8 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     prm.t0 = h->sig.t0; prm.fs = h->sig.fs; prm.fc = h->sig.fc; prm.inv_c = 1.0 / h->sig.c;
     prm.fs_c = (float)(h->sig.fs / h->sig.c);
     prm.fc_c = (float)(h->sig.fc / h->sig.c);
+    prm.fs_c2 = make_float2(prm.fs_c, prm.fs_c);
+    prm.fc_c2 = make_float2(prm.fc_c, prm.fc_c);
     prm.fs_f = (float)h->sig.fs;
     prm.wfc = (float)(2.0 * M_PI * h->sig.fc);
     prm.grad_scale = (float)(-2.0 / h->sig.c);
