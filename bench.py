@@ -39,6 +39,11 @@ BETA = 4.0
 # 128 FP32 lanes/clk/SM and 4 SFU ops (rsqrt, rcp, sin, cos) on 16 SFU
 # lanes/clk/SM -> 4 updates per clock per SM from either pipe.
 UPDATES_PER_CLK_PER_SM = 4.0
+# DRAM bytes (read + write) per launch of the forward kernel, beam off, from an
+# ncu capture of the same kernel on 64 pings of the stripmap workload: reads
+# 131.3 MB (scaled by 2048 / 64 pings: each ping's rows are read once) plus the
+# 114.4 MB image write.  Only the configurations captured are listed.
+TRAFFIC_BYTES = {("stripmap_2d", "c64"): 131.3e6 * 2048 / 64 + 114.4e6}
 
 
 def parse():
@@ -139,12 +144,13 @@ def cpu_baseline(w, nav, echo, seconds: float, rank_seed=0):
     tx, rx = oracle.sensor_positions(nav["pos"], nav["att"], nav["tx_lever"], nav["rx_lever"])
     cores = oracle.max_threads()
     pairs = w.n_pings * w.n_rx
-    idx = synth.random_pixel_indices(w.grid, 4096, seed=99 + rank_seed)
+    idx = synth.random_pixel_indices(w.grid, 65536, seed=99 + rank_seed)
     g = w.grid
     pts = oracle.grid_index_points(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, idx)
-    # warm the thread pool, calibrate with a few pixels, then size the sample
-    # to the time budget
-    n0 = max(cores, 4)
+    # warm the thread pool, calibrate with enough pixels to keep every thread
+    # busy (the oracle hands out pixels 8 at a time), then size the sample to
+    # the time budget
+    n0 = 16 * cores
     oracle.backproject(tx, rx, sig, echo, 8, BETA, pts[:cores])
     t = time.perf_counter()
     oracle.backproject(tx, rx, sig, echo, 8, BETA, pts[:n0])
@@ -275,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
     work = computed_updates if args.beam_deg > 0 else w.updates
     achieved = work / (statistics.mean(launch_ms) / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-            "traffic": None,
+            "traffic": (TRAFFIC_BYTES.get((w.name, args.echo)) if args.beam_deg <= 0 and not args.pings else None),
             "peak_basis": "%d SMs x %.0f MHz x %.0f updates/clk/SM (FP32 128 lanes / 32 ops, SFU 16 lanes / 4 ops)"
                           % (props.multi_processor_count, sm_max, UPDATES_PER_CLK_PER_SM)}
     if clk.get("sm_mhz"):

@@ -59,15 +59,16 @@ def lib():
             L.oracle_bessel_i1_over_x.argtypes = [D]
             L.oracle_bessel_i1_over_x.restype = D
             L.oracle_kaiser_sinc_weights.argtypes = [D, I, D, P, P]
-            L.oracle_backproject.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, P, D, I, I]
+            L.oracle_backproject.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, P, D, I, P, I]
             L.oracle_backproject_beam_split.argtypes = [I, I, P, P, D, D, D, D, I, P, I, I, D, Lg, P, P, D, I, D,
-                                                        P, P, I]
-            L.oracle_backproject_adjoint.argtypes = [I, I, P, P, D, D, D, D, I, I, D, Lg, P, P, P, P, D, I, I]
-            L.oracle_vjp_offsets.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, P, P, D, I, I]
+                                                        P, P, P, I]
+            L.oracle_backproject_adjoint.argtypes = [I, I, P, P, D, D, D, D, I, I, D, Lg, P, P, P, P, D, I, P, I]
+            L.oracle_vjp_offsets.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, P, P, D, I, P, I]
+            L.oracle_delay_eval.argtypes = [P, P, P, P, D, P]
             L.oracle_sharpness.argtypes = [Lg, P, P, P]
             L.oracle_lfm_compressed_pulse.argtypes = [D, D, D]
             L.oracle_lfm_compressed_pulse.restype = D
-            L.oracle_simulate_points.argtypes = [I, I, P, P, D, D, D, D, I, D, D, Lg, P, I, P, I]
+            L.oracle_simulate_points.argtypes = [I, I, P, P, D, D, D, D, I, D, D, Lg, P, I, P, P, I]
             _lib = L
     return _lib
 
@@ -166,12 +167,27 @@ def _echo_c128(echo) -> np.ndarray:
     return e
 
 
+def _vel(vel, P):
+    return None if vel is None else _p(_f64(vel).reshape(P, 3))
+
+
+def delay(x, t, r, v, c):
+    """(tau, kappa) of one (pixel, transmitter, receiver): stop-and-hop for
+    v None, else the receiver moving with velocity v during reception."""
+    out = np.zeros(2)
+    vv = None if v is None else _f64(v)
+    lib().oracle_delay_eval(_p(_f64(x)), _p(_f64(t)), _p(_f64(r)), None if vv is None else _p(vv), float(c), _p(out))
+    return float(out[0]), float(out[1])
+
+
 def backproject(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, nthreads: int = 0,
-                att=None, beam_width: float = 0.0, side: int = 1):
+                att=None, beam_width: float = 0.0, side: int = 1, vel=None):
     """I(x) at the given pixels [n,3]; returns complex128 [n].  A complex64
     echo is read in place (widened exactly to FP64), others as complex128.
     att [P,3] and beam_width (full azimuth width, radians) > 0 apply the
-    beam field of view looking to ``side`` (+1 starboard, -1 port)."""
+    beam field of view looking to ``side`` (+1 starboard, -1 port).  vel
+    [P,3]: receiver velocity during reception (continuous motion), None =
+    stop-and-hop."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
     if isinstance(echo, np.ndarray) and echo.dtype == np.complex64 and echo.flags.c_contiguous:
         e, f32 = echo, 1
@@ -184,12 +200,12 @@ def backproject(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, nthreads
     btan = float(np.tan(0.5 * beam_width)) if (beam_width and beam_width > 0) else 0.0
     lib().oracle_backproject(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
                              _p(e), f32, int(taps), float(beta), pix.shape[0], _p(pix), _p(out),
-                             None if a is None else _p(a), btan, int(side), int(nthreads))
+                             None if a is None else _p(a), btan, int(side), _vel(vel, P), int(nthreads))
     return out[:, 0] + 1j * out[:, 1]
 
 
 def backproject_beam_split(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, att, beam_width: float,
-                           side: int = 1, eps: float = 2e-6, nthreads: int = 0):
+                           side: int = 1, eps: float = 2e-6, nthreads: int = 0, vel=None):
     """Beam-limited image split by decision margin: (sure [n] complex128,
     amb [n] float64).  ``sure`` sums the terms whose transmitter and receiver
     see the pixel by a relative margin above eps, ``amb`` the magnitudes of
@@ -208,7 +224,7 @@ def backproject_beam_split(tx, rx, sig: Signal, echo, taps: int, beta: float, pi
     lib().oracle_backproject_beam_split(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
                                         _p(e), f32, int(taps), float(beta), pix.shape[0], _p(pix), _p(a),
                                         float(np.tan(0.5 * beam_width)), int(side), float(eps), _p(out), _p(amb),
-                                        int(nthreads))
+                                        _vel(vel, P), int(nthreads))
     return out[:, 0] + 1j * out[:, 1], amb
 
 
@@ -219,7 +235,7 @@ def _beam_args(att, beam_width, P):
 
 
 def backproject_adjoint(tx, rx, sig: Signal, img, taps: int, beta: float, pix, nthreads: int = 0,
-                        att=None, beam_width: float = 0.0, side: int = 1):
+                        att=None, beam_width: float = 0.0, side: int = 1, vel=None):
     """Linear adjoint: image values at pixels -> echo [P,C,Ns] complex128."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
     im = np.ascontiguousarray(np.asarray(img, dtype=np.complex128).reshape(-1))
@@ -229,12 +245,12 @@ def backproject_adjoint(tx, rx, sig: Signal, img, taps: int, beta: float, pix, n
     lib().oracle_backproject_adjoint(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0,
                                      sig.n_samples, int(taps), float(beta), pix.shape[0], _p(pix),
                                      _p(im), _p(out), None if a is None else _p(a), btan, int(side),
-                                     int(nthreads))
+                                     _vel(vel, P), int(nthreads))
     return out
 
 
 def vjp_offsets(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, g, nthreads: int = 0,
-                att=None, beam_width: float = 0.0, side: int = 1):
+                att=None, beam_width: float = 0.0, side: int = 1, vel=None):
     """dL/d(dp) [P,3] given g = dL/dI* at the pixels."""
     tx, rx, pix = _f64(tx), _f64(rx), _f64(pix).reshape(-1, 3)
     e = _echo_c128(echo)
@@ -244,7 +260,7 @@ def vjp_offsets(tx, rx, sig: Signal, echo, taps: int, beta: float, pix, g, nthre
     a, btan = _beam_args(att, beam_width, P)
     lib().oracle_vjp_offsets(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0, sig.n_samples,
                              _p(e), int(taps), float(beta), pix.shape[0], _p(pix), _p(gg),
-                             _p(out), None if a is None else _p(a), btan, int(side), int(nthreads))
+                             _p(out), None if a is None else _p(a), btan, int(side), _vel(vel, P), int(nthreads))
     return out
 
 
@@ -265,7 +281,7 @@ def lfm_compressed_pulse(t: float, B: float, T: float) -> float:
 
 
 def simulate_points(tx, rx, sig: Signal, B: float, T: float, scat, half_width: int = 0,
-                    nthreads: int = 0, echo=None):
+                    nthreads: int = 0, echo=None, vel=None):
     """Matched-filtered echo of point scatterers scat [n,5] = (x,y,z,ReA,ImA).
     Accumulates into ``echo`` (complex128 [P,C,Ns]) if given."""
     tx, rx = _f64(tx), _f64(rx)
@@ -276,7 +292,7 @@ def simulate_points(tx, rx, sig: Signal, B: float, T: float, scat, half_width: i
     assert echo.dtype == np.complex128 and echo.flags.c_contiguous
     lib().oracle_simulate_points(P, C, _p(tx), _p(rx), sig.fc, sig.fs, sig.c, sig.t0,
                                  sig.n_samples, float(B), float(T), sc.shape[0], _p(sc),
-                                 int(half_width), _p(echo), int(nthreads))
+                                 int(half_width), _p(echo), _vel(vel, P), int(nthreads))
     return echo
 
 

@@ -184,12 +184,20 @@ void oracle_kaiser_sinc_weights(double f, int taps, double beta, double* w, doub
 typedef struct {
     double tau, u, f;
     long j0;
-    double rt, rr;           /* one-way ranges */
+    double rt, rr;           /* one-way ranges (receiver: at the time of reception) */
     double ut[3], ur[3];     /* unit vectors sensor -> pixel */
+    double kappa;            /* c / (c + ur . v): dtau/d(dp) = -(ut + ur) kappa / c */
 } oracle_delay;
 
-static void delay_eval(const double* x, const double* t, const double* r, double c, double t0,
-                       double fs, oracle_delay* o) {
+/* Two-way delay of pixel x for transmitter t and receiver r (Sec. II-A).
+ * v == NULL: stop-and-hop, tau = (|x - t| + |x - r|) / c.
+ * v != NULL: the transmitter sends at time 0 from t and the receiver moves
+ * on during reception, r(t') = r + v t' (the motion model of Sec. II-D,
+ * transmission instantaneous): tau solves c tau = |x - t| + |x - r - v tau|,
+ * found by fixed-point iteration (a contraction with factor |v|/c) until
+ * the update is below 1e-15 tau.                                          */
+static void delay_eval(const double* x, const double* t, const double* r, const double* v, double c,
+                       double t0, double fs, oracle_delay* o) {
     double dt[3], dr[3];
     for (int a = 0; a < 3; ++a) {
         dt[a] = x[a] - t[a];
@@ -197,15 +205,39 @@ static void delay_eval(const double* x, const double* t, const double* r, double
     }
     o->rt = sqrt(dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2]);
     o->rr = sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+    o->tau = (o->rt + o->rr) / c;
+    o->kappa = 1.0;
+    if (v) {
+        for (int it = 0; it < 100; ++it) {
+            double w[3];
+            for (int a = 0; a < 3; ++a) w[a] = dr[a] - v[a] * o->tau;
+            const double rr = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            const double tau = (o->rt + rr) / c;
+            const double step = fabs(tau - o->tau);
+            o->tau = tau;
+            o->rr = rr;
+            if (step <= 1e-15 * tau) break;
+        }
+        for (int a = 0; a < 3; ++a) dr[a] -= v[a] * o->tau;
+        o->rr = sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+    }
     for (int a = 0; a < 3; ++a) {
         o->ut[a] = dt[a] / o->rt;
         o->ur[a] = dr[a] / o->rr;
     }
-    o->tau = (o->rt + o->rr) / c;
+    if (v) o->kappa = c / (c + o->ur[0] * v[0] + o->ur[1] * v[1] + o->ur[2] * v[2]);
     o->u = (o->tau - t0) * fs;
     const double fl = floor(o->u);
     o->j0 = (long)fl;
     o->f = o->u - fl;
+}
+
+/* Exported for tests: tau and kappa of delay_eval (v may be NULL). */
+void oracle_delay_eval(const double* x, const double* t, const double* r, const double* v, double c, double* out2) {
+    oracle_delay d;
+    delay_eval(x, t, r, v, c, 0.0, 1.0, &d);
+    out2[0] = d.tau;
+    out2[1] = d.kappa;
 }
 
 /* Beam field of view (Sec. II-C: each pixel is tested against the
@@ -228,11 +260,11 @@ static int sensor_sees(const double* R, const double* x, const double* s, double
 /* One term of the backprojection sum: pixel x, ping i, channel ch
  * (Sec. II-A): s = sum_m w_m(f) e[i][ch][j0 + k_m] (zero outside the row)
  * rotated by exp(+j 2 pi fc tau).  w: scratch of at least taps doubles.      */
-static void term_eval(const double* x, int i, int ch, int C, const double* tx, const double* rx, double fc,
-                      double fs, double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
-                      double beta, double* w, double* tre, double* tim) {
+static void term_eval(const double* x, int i, int ch, int C, const double* tx, const double* rx,
+                      const double* vel, double fc, double fs, double c, double t0, int Ns, const void* echo,
+                      int echo_f32, int taps, double beta, double* w, double* tre, double* tim) {
     oracle_delay d;
-    delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
+    delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), vel ? vel + 3 * i : NULL, c, t0, fs, &d);
     oracle_kaiser_sinc_weights(d.f, taps, beta, w, NULL);
     const size_t row = 2 * ((size_t)i * C + ch) * (size_t)Ns;
     double sr = 0.0, si = 0.0;
@@ -264,7 +296,7 @@ static void term_eval(const double* x, int i, int ch, int C, const double* tx, c
 void oracle_backproject(int P, int C, const double* tx, const double* rx, double fc, double fs,
                         double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
                         double beta, long npix, const double* pix, double* out,
-                        const double* att, double beam_tan, int side, int nthreads) {
+                        const double* att, double beam_tan, int side, const double* vel, int nthreads) {
     set_threads(nthreads);
     const int beam = att != NULL && beam_tan > 0.0;
 #pragma omp parallel for schedule(dynamic, 8)
@@ -281,7 +313,7 @@ void oracle_backproject(int P, int C, const double* tx, const double* rx, double
             for (int ch = 0; ch < C; ++ch) {
                 if (beam && !sensor_sees(R, x, rx + 3 * ((size_t)i * C + ch), beam_tan, side)) continue;
                 double tre, tim;
-                term_eval(x, i, ch, C, tx, rx, fc, fs, c, t0, Ns, echo, echo_f32, taps, beta, w, &tre, &tim);
+                term_eval(x, i, ch, C, tx, rx, vel, fc, fs, c, t0, Ns, echo, echo_f32, taps, beta, w, &tre, &tim);
                 acc_re += tre;
                 acc_im += tim;
             }
@@ -322,7 +354,7 @@ void oracle_backproject_beam_split(int P, int C, const double* tx, const double*
                                    double c, double t0, int Ns, const void* echo, int echo_f32, int taps,
                                    double beta, long npix, const double* pix, const double* att,
                                    double beam_tan, int side, double eps, double* out_sure, double* amb,
-                                   int nthreads) {
+                                   const double* vel, int nthreads) {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 8)
     for (long p = 0; p < npix; ++p) {
@@ -338,7 +370,7 @@ void oracle_backproject_beam_split(int P, int C, const double* tx, const double*
                 const int kr = sensor_class(R, x, rx + 3 * ((size_t)i * C + ch), beam_tan, side, eps);
                 if (kr < 0) continue;
                 double tre, tim;
-                term_eval(x, i, ch, C, tx, rx, fc, fs, c, t0, Ns, echo, echo_f32, taps, beta, w, &tre, &tim);
+                term_eval(x, i, ch, C, tx, rx, vel, fc, fs, c, t0, Ns, echo, echo_f32, taps, beta, w, &tre, &tim);
                 if (kt > 0 && kr > 0) {
                     acc_re += tre;
                     acc_im += tim;
@@ -361,7 +393,7 @@ void oracle_backproject_beam_split(int P, int C, const double* tx, const double*
 void oracle_backproject_adjoint(int P, int C, const double* tx, const double* rx, double fc,
                                 double fs, double c, double t0, int Ns, int taps, double beta,
                                 long npix, const double* pix, const double* img, double* echo_adj,
-                                const double* att, double beam_tan, int side, int nthreads) {
+                                const double* att, double beam_tan, int side, const double* vel, int nthreads) {
     set_threads(nthreads);
     const long rows = (long)P * C;
     const int beam = att != NULL && beam_tan > 0.0;
@@ -378,7 +410,8 @@ void oracle_backproject_adjoint(int P, int C, const double* tx, const double* rx
                           sensor_sees(R, pix + 3 * p, rx + 3 * ((size_t)i * C + ch), beam_tan, side)))
                 continue;
             oracle_delay d;
-            delay_eval(pix + 3 * p, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
+            delay_eval(pix + 3 * p, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), vel ? vel + 3 * i : NULL, c, t0,
+                       fs, &d);
             oracle_kaiser_sinc_weights(d.f, taps, beta, w, NULL);
             double ph = fc * d.tau;
             ph -= floor(ph);
@@ -402,14 +435,15 @@ void oracle_backproject_adjoint(int P, int C, const double* tx, const double* rx
  *   I_ic(x) = s(u) exp(j 2 pi fc tau),   s(u) = sum_m w_m(f) e[j0 + k_m],
  *   dI_ic/dtau = (fs s'(u) + j 2 pi fc s(u)) exp(j 2 pi fc tau),
  *   s'(u) = sum_m w'_m(f) e[j0 + k_m],
- *   dtau/d(dp_i) = -(u_T + u_R,c) / c  (unit vectors sensor -> pixel).
+ *   dtau/d(dp_i) = -(u_T + u_R,c) / (c + u_R,c . v_i)  (unit vectors sensor -> pixel;
+ *   v_i = 0 for stop-and-hop; with receiver motion u_R is taken at reception).
  * grad: [P][3].  One thread owns one ping.
  * Pinned by: central finite differences of the sharpness through
  * oracle_backproject with offsets applied by oracle_sensor_positions.      */
 void oracle_vjp_offsets(int P, int C, const double* tx, const double* rx, double fc, double fs,
                         double c, double t0, int Ns, const double* echo, int taps, double beta,
                         long npix, const double* pix, const double* g, double* grad,
-                        const double* att, double beam_tan, int side, int nthreads) {
+                        const double* att, double beam_tan, int side, const double* vel, int nthreads) {
     set_threads(nthreads);
     const int beam = att != NULL && beam_tan > 0.0;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -424,7 +458,7 @@ void oracle_vjp_offsets(int P, int C, const double* tx, const double* rx, double
             for (int ch = 0; ch < C; ++ch) {
                 if (beam && !sensor_sees(R, x, rx + 3 * ((size_t)i * C + ch), beam_tan, side)) continue;
                 oracle_delay d;
-                delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
+                delay_eval(x, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), vel ? vel + 3 * i : NULL, c, t0, fs, &d);
                 oracle_kaiser_sinc_weights(d.f, taps, beta, w, dw);
                 const double* row = echo + 2 * ((size_t)i * C + ch) * (size_t)Ns;
                 double sr = 0.0, si = 0.0, dr = 0.0, di = 0.0;
@@ -446,7 +480,7 @@ void oracle_vjp_offsets(int P, int C, const double* tx, const double* rx, double
                 const double br = ar * cs - ai * sn, bi = ar * sn + ai * cs;
                 /* Re(conj(g) * dI/dtau) */
                 const double re = g[2 * p] * br + g[2 * p + 1] * bi;
-                const double k = 2.0 * re * (-1.0 / c);
+                const double k = 2.0 * re * (-d.kappa / c);
                 gx += k * (d.ut[0] + d.ur[0]);
                 gy += k * (d.ut[1] + d.ur[1]);
                 gz += k * (d.ut[2] + d.ur[2]);
@@ -506,7 +540,7 @@ double oracle_lfm_compressed_pulse(double t, double B, double T) {
 void oracle_simulate_points(int P, int C, const double* tx, const double* rx, double fc,
                             double fs, double c, double t0, int Ns, double B, double T,
                             long nscat, const double* scat, int half_width, double* echo,
-                            int nthreads) {
+                            const double* vel, int nthreads) {
     set_threads(nthreads);
     const long rows = (long)P * C;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -516,7 +550,7 @@ void oracle_simulate_points(int P, int C, const double* tx, const double* rx, do
         for (long s = 0; s < nscat; ++s) {
             const double* q = scat + 5 * s;
             oracle_delay d;
-            delay_eval(q, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), c, t0, fs, &d);
+            delay_eval(q, tx + 3 * i, rx + 3 * ((size_t)i * C + ch), vel ? vel + 3 * i : NULL, c, t0, fs, &d);
             double ph = fc * d.tau;
             ph -= floor(ph);
             const double cs = cos(2.0 * ORACLE_PI * ph), sn = -sin(2.0 * ORACLE_PI * ph);
