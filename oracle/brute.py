@@ -72,13 +72,20 @@ def beam_mask(att, tx, rx, pix, beam_width, side):
     return sees(tx) & sees(rx)
 
 
-def terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix):
-    """Every term of the sum: [n,P,C] complex."""
+def stop_and_hop_tau(tx, rx, c, pix):
+    """[n,P,C] two-way delays with one position per ping for TX and RX."""
     pix = np.asarray(pix, dtype=np.float64)
-    P, C, Ns = echo.shape
     rt = np.linalg.norm(pix[:, None, :] - tx[None, :, :], axis=-1)                 # [n,P]
     rr = np.linalg.norm(pix[:, None, None, :] - rx[None, :, :, :], axis=-1)        # [n,P,C]
-    tau = (rt[:, :, None] + rr) / c
+    return (rt[:, :, None] + rr) / c
+
+
+def terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix, tau=None):
+    """Every term of the sum: [n,P,C] complex.  tau [n,P,C] overrides the
+    stop-and-hop delays (e.g. delays found by a root finder)."""
+    P, C, Ns = echo.shape
+    if tau is None:
+        tau = stop_and_hop_tau(tx, rx, c, pix)
     u = (tau - t0) * fs
     j0 = np.floor(u)
     f = u - j0
@@ -93,10 +100,28 @@ def terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix):
     return s * np.exp(2j * np.pi * fc * tau)
 
 
-def backproject(tx, rx, fc, fs, c, t0, echo, taps, beta, pix, mask=None):
+def backproject(tx, rx, fc, fs, c, t0, echo, taps, beta, pix, mask=None, tau=None):
     """Direct broadcast evaluation; pix [n,3], echo [P,C,Ns]; optional mask
-    [n,P,C] of the terms that count; returns [n]."""
-    t = terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix)
+    [n,P,C] of the terms that count and delays tau [n,P,C]; returns [n]."""
+    t = terms(tx, rx, fc, fs, c, t0, echo, taps, beta, pix, tau=tau)
     if mask is not None:
         t = np.where(mask, t, 0.0)
     return t.sum(axis=(1, 2))
+
+
+def moving_receiver_tau(tx, rx, vel, c, pix):
+    """[n,P,C] delays with the receiver moving at vel [P,3] during reception:
+    the root of c tau - |x - t| - |x - r - v tau| on a bracket, by Brent's
+    method (scipy), term by term (tiny grids only)."""
+    from scipy.optimize import brentq
+    pix = np.asarray(pix, dtype=np.float64)
+    n, P, C = pix.shape[0], tx.shape[0], rx.shape[1]
+    out = np.zeros((n, P, C))
+    for a in range(n):
+        for i in range(P):
+            rt = np.linalg.norm(pix[a] - tx[i])
+            for ch in range(C):
+                f = lambda t: c * t - rt - np.linalg.norm(pix[a] - rx[i, ch] - vel[i] * t)
+                t0 = (rt + np.linalg.norm(pix[a] - rx[i, ch])) / c
+                out[a, i, ch] = brentq(f, 0.5 * t0, 2.0 * t0, xtol=1e-18, rtol=8.9e-16, maxiter=200)
+    return out

@@ -64,6 +64,7 @@ class Workload:
     lattice: int = 0               # >0: pings on a lattice x lattice grid (3D collection)
     lattice_pitch: float = 0.64
     motion: bool = False
+    speed: float = 1.95            # along-track speed [m/s] (sets the ping interval and the velocity)
     nav_error: float = 0.0         # std of per-axis position error added to nav [m]
     n_points: int = 10
     point_patch: tuple = ()        # (x_lo, x_hi, y_lo, y_hi, z)
@@ -125,8 +126,12 @@ def scaled(w: Workload, n_pings: int | None = None, n_rx: int | None = None,
 
 def nav(w: Workload, seed_offset: int = 0):
     """Returns dict(pos [P,3], att [P,3] (roll, pitch, yaw rad), tx_lever [3],
-    rx_lever [C,3], true_pos [P,3]).  ``pos`` includes the navigation error
-    (if any); ``true_pos`` is what the echoes are simulated from."""
+    rx_lever [C,3], true_pos [P,3], vel [P,3]).  ``pos`` includes the
+    navigation error (if any); ``true_pos`` is what the echoes are simulated
+    from; ``vel`` is the platform velocity at each ping [m/s] (along-track
+    speed plus the rates of the sway and heave sinusoids; zero on a lattice),
+    the receiver velocity during reception when continuous motion is
+    modelled."""
     rng = np.random.default_rng(w.seed + 17 * seed_offset)
     P, C = w.n_pings, w.n_rx
     if w.lattice:
@@ -137,6 +142,9 @@ def nav(w: Workload, seed_offset: int = 0):
     else:
         pos = np.stack([np.arange(P) * w.ping_spacing, np.zeros(P), np.full(P, -w.altitude)], 1)
     att = np.zeros((P, 3))
+    vel = np.zeros((P, 3))
+    if not w.lattice:
+        vel[:, 0] = w.speed
     if w.motion:
         i = np.arange(P)
         t_sway, t_heave = rng.uniform(20.0, 60.0, size=2)
@@ -144,6 +152,10 @@ def nav(w: Workload, seed_offset: int = 0):
         pos[:, 1] += 0.05 * np.sin(2.0 * np.pi * i / t_sway + p_sway)
         pos[:, 2] += 0.05 * np.sin(2.0 * np.pi * i / t_heave + p_heave)
         att[:, 2] = np.cumsum(rng.normal(0.0, np.deg2rad(0.01), size=P))
+        if not w.lattice:
+            pings_per_s = w.speed / w.ping_spacing
+            vel[:, 1] = 0.05 * 2.0 * np.pi / t_sway * pings_per_s * np.cos(2.0 * np.pi * i / t_sway + p_sway)
+            vel[:, 2] = 0.05 * 2.0 * np.pi / t_heave * pings_per_s * np.cos(2.0 * np.pi * i / t_heave + p_heave)
     if w.array == "planar":
         n = int(round(np.sqrt(C)))
         assert n * n == C
@@ -156,7 +168,7 @@ def nav(w: Workload, seed_offset: int = 0):
     true_pos = pos.copy()
     if w.nav_error > 0:
         pos = pos + rng.normal(0.0, w.nav_error, size=pos.shape)
-    return dict(pos=pos, att=att, tx_lever=tx, rx_lever=rx, true_pos=true_pos)
+    return dict(pos=pos, att=att, tx_lever=tx, rx_lever=rx, true_pos=true_pos, vel=vel)
 
 
 def scatterers(w: Workload, seed_offset: int = 0) -> np.ndarray:
