@@ -148,6 +148,19 @@ int sas_geometry_set_offsets(sas_geometry_t h, const double* offsets, int on_dev
  * the per-pixel definition.  Errors: SAS_ERR_ARG (beam_width >= pi, bad side). */
 int sas_geometry_set_beam(sas_geometry_t h, double beam_width, int side);
 
+/* Receiver motion during reception (Sec. II-D: transmission is
+ * instantaneous and the platform keeps moving while the echo comes in; the
+ * stop-and-hop approximation drops that motion).  vel [P][3] (FP64, m/s,
+ * NED): the velocity of ping i's receivers during its reception; host
+ * (on_device = 0, read before the call returns) or device (on_device = 1,
+ * copied on the stream).  With a velocity the two-way delay of pixel x solves
+ * c tau = |x - x_TX,i| + |x - x_RX,i,c - v_i tau| (transmitter fixed at the
+ * ping time); every later backprojection, adjoint, offset gradient and
+ * simulation uses it.  vel == NULL returns to stop-and-hop (the default).
+ * Beam tests keep the ping-time sensor positions.  Errors: SAS_ERR_ARG,
+ * SAS_ERR_CUDA. */
+int sas_geometry_set_velocity(sas_geometry_t h, const double* vel, int on_device, void* cuda_stream);
+
 /* Copies the current sensor positions to device arrays d_tx [P][3] and
  * d_rx [P][C][3] (FP64).  Either may be NULL. */
 int sas_geometry_positions(sas_geometry_t h, double* d_tx, double* d_rx, void* cuda_stream);

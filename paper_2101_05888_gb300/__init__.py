@@ -39,6 +39,7 @@ SAS_MLP_NPARAMS = 4808
 
 ENTRY_POINTS = [
     "sas_version", "sas_last_error", "sas_geometry_create", "sas_geometry_set_offsets", "sas_geometry_set_beam",
+    "sas_geometry_set_velocity",
     "sas_geometry_positions", "sas_geometry_destroy", "sas_echo_upload", "sas_echo_download",
     "sas_backproject_2d", "sas_backproject_3d", "sas_backproject_adjoint", "sas_sharpness",
     "sas_sharpness_static", "sas_simulate_points",
@@ -97,6 +98,7 @@ def lib():
                 "sas_geometry_create": ([P(sas_nav), P(sas_signal), V, P(V)], I),
                 "sas_geometry_set_offsets": ([V, V, I, V], I),
                 "sas_geometry_set_beam": ([V, D, I], I),
+                "sas_geometry_set_velocity": ([V, V, I, V], I),
                 "sas_geometry_positions": ([V, V, V, V], I),
                 "sas_geometry_destroy": ([V], I),
                 "sas_echo_upload": ([V, V, I, I, V], I),
@@ -171,6 +173,10 @@ def sas_geometry_create(nav: sas_nav, sig: sas_signal, stream=None) -> int:
 
 def sas_geometry_set_offsets(h, offsets, on_device: int, stream=None):
     _check(lib().sas_geometry_set_offsets(h, _ptr(offsets), on_device, _stream(stream)))
+
+
+def sas_geometry_set_velocity(h, vel, on_device: int, stream=None):
+    _check(lib().sas_geometry_set_velocity(h, _ptr(vel), on_device, _stream(stream)))
 
 
 def sas_geometry_set_beam(h, beam_width: float, side: int = 1):
@@ -332,6 +338,15 @@ class Geometry:
         else:
             a = np.ascontiguousarray(offsets, dtype=np.float64)
             sas_geometry_set_offsets(self.h, a, 0, stream)
+
+    def set_velocity(self, vel, stream=None):
+        """Receiver velocity during reception [P,3] m/s (None = stop-and-hop)."""
+        if vel is None:
+            sas_geometry_set_velocity(self.h, None, 0, stream)
+        elif hasattr(vel, "is_cuda") and vel.is_cuda:
+            sas_geometry_set_velocity(self.h, vel.contiguous(), 1, stream)
+        else:
+            sas_geometry_set_velocity(self.h, np.ascontiguousarray(vel, dtype=np.float64), 0, stream)
 
     def set_beam(self, beam_width: float, side: int = 1):
         """Beam field of view of full azimuth width beam_width [rad] (0 = off)."""

@@ -385,6 +385,7 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     const size_t o_tx = o;  o = align256(o + P * 3 * 8);
     const size_t o_rx = o;  o = align256(o + P * C * 3 * 8);
     const size_t o_rc = o;  o = align256(o + P * 6 * 4);
+    const size_t o_vl = o;  o = align256(o + P * 3 * 8);
     const size_t o_st = o;  o = align256(o + 16);
     const size_t o_cu = o;  o = align256(o + 4 * 8);
     const size_t o_cf = o;  o = align256(o + sizeof(FarrowCoef));
@@ -402,6 +403,7 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     h->d_tx = (double*)(b + o_tx);
     h->d_rx = (double*)(b + o_rx);
     h->d_rotc = (float*)(b + o_rc);
+    h->d_vel = (double*)(b + o_vl);
     h->d_status = (uint32_t*)(b + o_st);
     h->d_cull = (unsigned long long*)(b + o_cu);
     h->d_coef = (FarrowCoef*)(b + o_cf);
@@ -449,6 +451,22 @@ extern "C" int sas_geometry_set_beam(sas_geometry_t h, double beam_width, int si
     }
     h->beam_tan = beam_width > 0.0 ? tan(0.5 * beam_width) : 0.0;
     h->beam_side = side;
+    return SAS_OK;
+}
+
+extern "C" int sas_geometry_set_velocity(sas_geometry_t h, const double* vel, int on_device, void* stream) {
+    if (!h) {
+        set_error("null handle");
+        return SAS_ERR_ARG;
+    }
+    if (!vel) {
+        h->has_vel = 0;
+        return SAS_OK;
+    }
+    SAS_CUDA(cudaMemcpyAsync(h->d_vel, vel, (size_t)h->P * 3 * 8,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    if (!on_device) SAS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    h->has_vel = 1;
     return SAS_OK;
 }
 

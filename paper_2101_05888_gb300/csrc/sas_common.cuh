@@ -161,6 +161,8 @@ struct sas_geometry_s {
     double* d_tx;      // [P][3]
     double* d_rx;      // [P][C][3]
     float* d_rotc;     // [P][6]: columns 0 and 1 of the attitude matrix (beam tests)
+    double* d_vel;     // [P][3]: receiver velocity during reception (valid if has_vel)
+    int has_vel;       // 0: stop-and-hop
     double beam_tan;   // tan(beam width / 2); <= 0: no beam field of view
     int beam_side;     // +1 starboard, -1 port
     uint32_t* d_status;

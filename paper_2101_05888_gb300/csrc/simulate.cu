@@ -5,6 +5,7 @@
 //   q(t) = (1 - |t|/T) sinc(B t (1 - |t|/T)),  |t| < T,
 // the autocorrelation of a linear FM pulse of length T and bandwidth B with a
 // rectangular envelope, normalised to a unit peak (T <= 0 selects sinc(B t)).
+// With a receiver velocity set, tau solves c tau = |x_s - x_TX| + |x_s - x_RX - v tau|.
 // One block per (ping, channel) row; FP64 delay and carrier phase per
 // (row, scatterer); FP32 pulse samples accumulated with global atomics.
 #include "sas_common.cuh"
@@ -12,9 +13,10 @@
 namespace sas {
 namespace {
 
-__global__ void simulate_points_kernel(const double* __restrict__ tx, const double* __restrict__ rx, int C, int Ns,
-                                       double t0, double fs, double fc, double inv_c, const double* __restrict__ scat,
-                                       long long nscat, float B, float T, int half_width, float2* __restrict__ echo) {
+__global__ void simulate_points_kernel(const double* __restrict__ tx, const double* __restrict__ rx,
+                                       const double* __restrict__ vel, int C, int Ns, double t0, double fs,
+                                       double fc, double inv_c, const double* __restrict__ scat, long long nscat,
+                                       float B, float T, int half_width, float2* __restrict__ echo) {
     const long long row = blockIdx.x;
     const int i = (int)(row / C);
     const double* t = tx + 3 * (size_t)i;
@@ -25,7 +27,19 @@ __global__ void simulate_points_kernel(const double* __restrict__ tx, const doub
         const double* q = scat + 5 * s;
         const double ax = q[0] - t[0], ay = q[1] - t[1], az = q[2] - t[2];
         const double bx = q[0] - r[0], by = q[1] - r[1], bz = q[2] - r[2];
-        const double tau = (sqrt(ax * ax + ay * ay + az * az) + sqrt(bx * bx + by * by + bz * bz)) * inv_c;
+        const double rt = sqrt(ax * ax + ay * ay + az * az);
+        double tau = (rt + sqrt(bx * bx + by * by + bz * bz)) * inv_c;
+        if (vel) {
+            // receiver moving during reception: c tau = |x - x_TX| + |x - x_RX - v tau|
+            const double* v = vel + 3 * (size_t)i;
+            for (int it = 0; it < 12; ++it) {
+                const double wx = bx - v[0] * tau, wy = by - v[1] * tau, wz = bz - v[2] * tau;
+                const double t2 = (rt + sqrt(wx * wx + wy * wy + wz * wz)) * inv_c;
+                const double step = fabs(t2 - tau);
+                tau = t2;
+                if (step <= 1e-16 * tau) break;
+            }
+        }
         const double u = (tau - t0) * fs;
         double ph = fc * tau;
         ph -= floor(ph);
@@ -71,7 +85,7 @@ extern "C" int sas_simulate_points(sas_geometry_t h, const double* d_scat, int64
     if (n == 0) return SAS_OK;
     const unsigned rows = (unsigned)((long long)h->P * h->C);
     simulate_points_kernel<<<rows, 256, 0, (cudaStream_t)stream>>>(
-        h->d_tx, h->d_rx, h->C, h->Ns, h->sig.t0, h->sig.fs, h->sig.fc, 1.0 / h->sig.c, d_scat, n, (float)bandwidth,
+        h->d_tx, h->d_rx, h->has_vel ? h->d_vel : nullptr, h->C, h->Ns, h->sig.t0, h->sig.fs, h->sig.fc, 1.0 / h->sig.c, d_scat, n, (float)bandwidth,
         (float)pulse_T, half_width, (float2*)d_echo);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;

@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
         __syncthreads();   // previous stage's records no longer in use
         if (warp == 0 && qs + lane < q1) {
             const int i = (int)((qs + lane) / p.C);
-            base_s[lane] = pair_record(p, pair_geo(p, X0, Y0, Z0, qs + lane, i), rec + lane, PAIRS);
+            base_s[lane] = pair_record(p, pair_geo(p, X0, Y0, Z0, qs + lane, i), rec + lane, PAIRS,
+                                       p.vel ? p.vel + 3 * (size_t)i : nullptr);
         }
         __syncthreads();
         float r[F_NT + 1];
@@ -115,6 +116,18 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                     const float ufc = __shfl_sync(0xffffffffu, r[F_UF], pr);
                     const float phr = __shfl_sync(0xffffffffu, r[F_PH], pr);
                     const float Ax = fixed_dot<DIM3>(tRx, tRy, dxv, dyv_c);
+                    // receiver motion: (R_R + d).v / c = Km + d_var v_var / c, as the forward
+                    // kernel forms it; the beam test keeps the ping-time receiver vector
+                    float Km = 0.f, vv = 0.f, bRx = tRx, bRy = tRy, bRz = tRz;
+                    if (p.vel) {
+                        const float* rp = rec + pr;
+                        Km = DIM3 ? fmaf(rp[F_VX * PAIRS], dxv, fmaf(rp[F_VY * PAIRS], dyv_c, rp[F_RV * PAIRS]))
+                                  : fmaf(rp[F_VX * PAIRS], dxv, rp[F_RV * PAIRS]);
+                        vv = DIM3 ? rp[F_VZ * PAIRS] : rp[F_VY * PAIRS];
+                        bRx = rp[F_BRX * PAIRS];
+                        bRy = rp[F_BRY * PAIRS];
+                        bRz = rp[F_BRZ * PAIRS];
+                    }
                     float2* Aj = A + j * p.npos * NP;
                     float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f;
@@ -131,13 +144,18 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                             // both beams must see the pixel (sensor-to-pixel vectors R + d)
                             const float dy = DIM3 ? dyv_c : dvar[s], dz = DIM3 ? dvar[s] : 0.f;
                             if (!beam_sees(p, fmaf(0.5f, tT0, dxv), fmaf(0.5f, tT1, dy), fmaf(0.5f, tT2, dz), rot) ||
-                                !beam_sees(p, fmaf(0.5f, tRx, dxv), fmaf(0.5f, tRy, dy), fmaf(0.5f, tRz, dz), rot))
+                                !beam_sees(p, fmaf(0.5f, bRx, dxv), fmaf(0.5f, bRy, dy), fmaf(0.5f, bRz, dz), rot))
                                 continue;
                         }
                         const float d2 = fmaf(dvar[s], dvar[s], d2c);
                         const float a = __fadd_rn(fmaf(DIM3 ? tRz : tRy, dvar[s], d2), Ax);
                         const float sm = nR2 + a;
-                        const float D = fmaf(a, rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nR)), dT[s]);
+                        const float rs = rsqrt_sfu(sm);
+                        float D = fmaf(a, rcp_sfu(fmaf(sm, rs, nR)), dT[s]);
+                        if (p.vel) {
+                            const float eps = fmaf(dvar[s], vv, Km) * rs;         // u_R . v / c
+                            D = D * fmaf(eps, eps - 1.f, 1.f);                   // / (1 + eps)
+                        }
                         const float v = fmaf(D, p.fs_c, ufc);              // u - 1/2
                         const float ph = fmaf(D, p.fc_c, phr);             // carrier phase [cycles]
                         // nearest integer of u - 1/2 = floor(u); g = frac(u) - 1/2

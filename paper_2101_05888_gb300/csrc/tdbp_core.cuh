@@ -49,7 +49,7 @@ constexpr int NCW = 7;                  // consumer warps
 constexpr int NCONS = 32 * NCW;         // consumer threads
 constexpr int NTHREADS = NCONS + 32;    // + producer warp
 constexpr int PAIRS = 32;               // (ping, channel) pairs per stage
-constexpr int NSTAGE = 3;               // copy ring depth
+constexpr int NSTAGE = 2;               // copy ring depth
 constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
@@ -60,15 +60,19 @@ constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
 enum { MODE_FORWARD = 0, MODE_OFFSET_GRAD = 1 };
 
-// record fields of one (ping, channel) pair, in the order of the six float4
-// a consumer loads: {2R_R, |R_R|^2}, {|R_R|, frac u_ref - 1/2, phase, scale},
+// record fields of one (ping, channel) pair, in the order of the float4 a
+// consumer loads: {2R_R, |R_R|^2}, {|R_R|, frac u_ref - 1/2, phase, scale},
 // {2R_T, |R_T|^2}, {|R_T|, ping, flags, segment offset}, {c0, c1.x},
-// {c1.y, c1.z, -, -} (c0, c1: columns 0 and 1 of the attitude matrix)
+// {c1.y, c1.z, -, -} (c0, c1: columns 0 and 1 of the attitude matrix), and
+// with receiver motion {v/c, R_R.v/c}, {2R_R at the ping time, -} (R_R is
+// then taken from the receiver's position at the reception of the tile
+// centre's echo; the beam tests use the ping-time position)
 enum {
     F_RX, F_RY, F_RZ, F_NR2, F_NR, F_UF, F_PH, F_SCALE, F_TX, F_TY, F_TZ, F_NT2, F_NT, F_PING, F_FLAGS, F_OFF,
-    F_C0X, F_C0Y, F_C0Z, F_C1X, F_C1Y, F_C1Z, NREC = 24
+    F_C0X, F_C0Y, F_C0Z, F_C1X, F_C1Y, F_C1Z, F_PAD0, F_PAD1, F_VX, F_VY, F_VZ, F_RV, F_BRX, F_BRY, F_BRZ, F_PAD2,
+    NREC
 };
-constexpr int HROW = NREC;              // floats per record row (6 x float4)
+constexpr int HROW = NREC;              // floats per record row (8 x float4)
 // pair flags: the whole tile lies inside the transmitter / receiver beam
 enum { FL_TX_FULL = 1, FL_RX_FULL = 2 };
 
@@ -96,6 +100,8 @@ struct KParams {
     int beam;
     float beam_tan, beam_side;
     unsigned long long* cull;   // [3] candidate, computed, beam-edge (ping, channel, tile) blocks
+    // receiver motion during reception: velocity [P][3] (m/s) or null (stop-and-hop)
+    const double* vel;
     float hx, hy, hz;       // half extents of a tile's pixel-centre box [m]
     int U, npos, npos_pad, seglen, seg_align, slot_bytes;
     int accumulate, atomic_out, skip_copies;
@@ -187,9 +193,36 @@ __device__ __forceinline__ PairGeo pair_geo(const KParams& p, double X0, double 
 // nearest integer gives floor(u)) and the carrier phase fc tau_ref mod 1
 // (cycles).
 // Returns the raw sample index of Farrow position 0, tap 0: floor(u_ref) - U - 3.
-__device__ __forceinline__ int pair_record(const KParams& p, const PairGeo& G, float* rc, int stride) {
-    const double nT2 = G.Tx * G.Tx + G.Ty * G.Ty + G.Tz * G.Tz, nR2 = G.Rx * G.Rx + G.Ry * G.Ry + G.Rz * G.Rz;
-    const double nT = sqrt(nT2), nR = sqrt(nR2);
+__device__ __forceinline__ int pair_record(const KParams& p, PairGeo G, float* rc, int stride, const double* v) {
+    const double nT2 = G.Tx * G.Tx + G.Ty * G.Ty + G.Tz * G.Tz;
+    const double nT = sqrt(nT2);
+    if (v) {
+        // receiver moving during reception (Sec. II-D): the tile centre's
+        // echo arrives at tau with c tau = |R_T| + |R_R - v tau|; fixed-point
+        // iteration (contraction |v|/c), then R_R from the receiver's position
+        // at that time
+        const double vx = v[0], vy = v[1], vz = v[2];
+        rc[F_BRX * stride] = (float)(2.0 * G.Rx);
+        rc[F_BRY * stride] = (float)(2.0 * G.Ry);
+        rc[F_BRZ * stride] = (float)(2.0 * G.Rz);
+        double tau = (nT + sqrt(G.Rx * G.Rx + G.Ry * G.Ry + G.Rz * G.Rz)) * p.inv_c;
+        for (int it = 0; it < 12; ++it) {
+            const double wx = G.Rx - vx * tau, wy = G.Ry - vy * tau, wz = G.Rz - vz * tau;
+            const double t2 = (nT + sqrt(wx * wx + wy * wy + wz * wz)) * p.inv_c;
+            const double step = fabs(t2 - tau);
+            tau = t2;
+            if (step <= 1e-16 * tau) break;
+        }
+        G.Rx -= vx * tau;
+        G.Ry -= vy * tau;
+        G.Rz -= vz * tau;
+        rc[F_VX * stride] = (float)(vx * p.inv_c);
+        rc[F_VY * stride] = (float)(vy * p.inv_c);
+        rc[F_VZ * stride] = (float)(vz * p.inv_c);
+        rc[F_RV * stride] = (float)((G.Rx * vx + G.Ry * vy + G.Rz * vz) * p.inv_c);
+    }
+    const double nR2 = G.Rx * G.Rx + G.Ry * G.Ry + G.Rz * G.Rz;
+    const double nR = sqrt(nR2);
     const double tau = (nT + nR) * p.inv_c;
     double u = (tau - p.t0) * p.fs;
     u = fmin(fmax(u, -268435456.0), 268435456.0);  // keep sample coordinates in int range
@@ -278,7 +311,8 @@ inline size_t smem_bytes(int slot_bytes, int npos_pad) {
 // ----------------------------------------------------------------------------
 // BEAM: the beam field of view is on (culling in the producer, per-pixel tests
 // in tiles on a beam edge); without it every candidate pair is computed.
-template <typename ET, bool DIM3, int MODE, bool BEAM>
+// MOTION: the receivers move during reception (per-ping velocity).
+template <typename ET, bool DIM3, int MODE, bool BEAM, bool MOTION>
 __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant__ CUtensorMap tmap, const KParams p) {
     using T = Tile<DIM3>;
     // FP16 Farrow rows for 16-bit echoes in the forward pass
@@ -401,7 +435,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     const int s = (k - 1) % NSTAGE;
                     const int slot = fill + rank - done;
                     float* rc = rec + (s * PAIRS + slot) * NREC;
-                    const int base = pair_record(p, G, rc, 1);
+                    const int base = pair_record(p, G, rc, 1, MOTION ? p.vel + 3 * (size_t)i : nullptr);
                     const int seg_start = base - (((base % p.seg_align) + p.seg_align) % p.seg_align);
                     rc[F_OFF] = __int_as_float(base - seg_start);
                     rc[F_SCALE] = p.scale ? p.scale[q] : 1.0f;
@@ -526,9 +560,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // consumer copy of a stage's records (read by uniform 16-byte loads; the
     // producer's ring slot is recycled as soon as the stage's expansions are done)
     auto hold_records = [&](int kst) {
+        constexpr int NQ = MOTION ? HROW / 4 : 6;      // float4 per record the consumers read
         const float4* rc = reinterpret_cast<const float4*>(rec + (kst % NSTAGE) * PAIRS * NREC);
         float4* hd = reinterpret_cast<float4*>(hold + (kst & 1) * PAIRS * HROW);
-        for (int t = ct; t < PAIRS * HROW / 4; t += NCONS) hd[t] = rc[t];
+        for (int t = ct; t < PAIRS * NQ; t += NCONS) {
+            const int pr = t / NQ, qd = t - pr * NQ;
+            hd[pr * (HROW / 4) + qd] = rc[pr * (NREC / 4) + qd];
+        }
     };
 
     auto release = [&](int kst) {
@@ -611,8 +649,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // geometry runs on pixel pairs (2k, 2k+1) in packed FP32x2: differential
     // path, sample position and carrier phase, the fraction and phase
     // reductions; the SFU, the Farrow rows and the accumulation per pixel.
+    //
+    // Receiver motion: the reference vector R_R is from the receiver's position
+    // at the reception of the tile centre's echo (tau_ref); a pixel's echo
+    // arrives dtau later, when the receiver has moved on by v dtau (about a
+    // millimetre), which to first order shortens the receive path by
+    // u_R.v dtau: c dtau (1 + u_R.v / c) = dr_T + dr_R, so the differential
+    // path is D / (1 + eps), eps = u_R.v / c ~ 1e-3, taken as
+    // D (1 - eps + eps^2) (neglected: eps^3 D ~ 1e-9 m and the curvature term
+    // |v dtau|^2 / (2 |R|) ~ 2e-8 m).
     auto pixels = [&](auto masked, const float4 q0, const float4 q1, const float* rot, uint32_t rmask_needed,
-                      const unsigned char* erow) {
+                      const unsigned char* erow, const float4 q6, const float4 q7) {
         constexpr bool MASKED = decltype(masked)::value;
         const float tRx = q0.x, tRy = q0.y, tRz = q0.z, nR2 = q0.w;
         const float nR = q1.x, ufc = q1.y, phr = q1.z;
@@ -623,6 +670,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         const float2 nR2v = make_float2(nR2, nR2), nRv = make_float2(nR, nR);
         const float2 ufv = make_float2(ufc, ufc), phv = make_float2(phr, phr);
         const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC), twopi2 = make_float2(TWO_PI_F, TWO_PI_F);
+        // motion: (R_R + d).v / c = Km + d_var v_var / c
+        float2 Kmv = make_float2(0.f, 0.f), vvv = make_float2(0.f, 0.f);
+        if constexpr (MOTION) {
+            const float Km = DIM3 ? fmaf(q6.x, dxv, fmaf(q6.y, dyv_c, q6.w)) : fmaf(q6.x, dxv, q6.w);
+            Kmv = make_float2(Km, Km);
+            vvv = DIM3 ? make_float2(q6.z, q6.z) : make_float2(q6.y, q6.y);
+        }
+        // ping-time receiver vector for the beam test
+        const float bRx = MOTION ? q7.x : tRx, bRy = MOTION ? q7.y : tRy, bRz = MOTION ? q7.z : tRz;
 #pragma unroll
         for (int k = 0; k < PX / 2; ++k) {
             const float2 a = fadd2(ffma2(tRvv, dvp[k], d2p[k]), Xv);       // 2 R.d + |d|^2
@@ -630,7 +686,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             const float2 rs = make_float2(rsqrt_sfu(sm.x), rsqrt_sfu(sm.y));
             const float2 den = ffma2(sm, rs, nRv);                        // |R_R + d| + |R_R|
             const float2 rc = make_float2(rcp_sfu(den.x), rcp_sfu(den.y));
-            const float2 D = ffma2(a, rc, dTp[k]);                        // two-way differential path [m]
+            float2 D = ffma2(a, rc, dTp[k]);                              // two-way differential path [m]
+            float2 kap = make_float2(1.f, 1.f);
+            if constexpr (MOTION) {
+                const float2 one2 = make_float2(1.f, 1.f);
+                const float2 eps = fmul2(ffma2(dvp[k], vvv, Kmv), rs);       // u_R . v / c
+                kap = ffma2(eps, fsub2(eps, one2), one2);                    // 1 / (1 + eps)
+                D = fmul2(D, kap);
+            }
             const float2 v = ffma2(D, p.fs_c2, ufv);                      // u - 1/2, rel. to floor(u_ref)
             const float2 ph = ffma2(D, p.fc_c2, phv);                     // carrier phase [cycles]
             // the nearest integer of u - 1/2 is floor(u): it sits in the mantissa of
@@ -647,9 +710,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             bool seen = true;
             if (MASKED) {
                 const float dvs = PXS(dvp, s);
-                const float wx = fmaf(0.5f, tRx, dxv);
-                const float wy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvs);
-                const float wz = DIM3 ? fmaf(0.5f, tRz, dvs) : 0.5f * tRz;
+                const float wx = fmaf(0.5f, bRx, dxv);
+                const float wy = DIM3 ? fmaf(0.5f, bRy, dyv_c) : fmaf(0.5f, bRy, dvs);
+                const float wz = DIM3 ? fmaf(0.5f, bRz, dvs) : 0.5f * bRz;
                 seen = ((tmask >> s) & 1u) && (!rmask_needed || beam_sees(p, wx, wy, wz, rot));
             }
             const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - p.U)),
@@ -702,7 +765,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 const float ay = fmaf(p.fs_f, d.y, p.wfc * b.x);
                 const float Hx = fmaf(acc[s].x, cs, acc[s].y * sn);       // conj(G) exp(j phase)
                 const float Hy = fmaf(acc[s].x, sn, -acc[s].y * cs);
-                const float r = fmaf(Hx, ax, -Hy * ay);
+                // dtau/d(dp) carries 1 / (1 + eps) with receiver motion
+                const float r = fmaf(Hx, ax, -Hy * ay) * (j ? kap.y : kap.x);
                 rsum[MODE == MODE_OFFSET_GRAD ? s : 0] += r;
                 // receiver unit vector (R_R + d) / |R_R + d| times r
                 const float kr = r * (j ? rs.y : rs.x);
@@ -811,11 +875,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 }
             }
             const float4 q0 = hr[0], q1 = hr[1];
+            const float4 q6 = MOTION ? hr[6] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 q7 = (MOTION && BEAM) ? hr[7] : make_float4(0.f, 0.f, 0.f, 0.f);
             const unsigned char* erow = eb + j * ebuf_pair;
             if (!BEAM || (flags & (FL_TX_FULL | FL_RX_FULL)) == (FL_TX_FULL | FL_RX_FULL))
-                pixels(std::integral_constant<bool, false>{}, q0, q1, rot, 0u, erow);
+                pixels(std::integral_constant<bool, false>{}, q0, q1, rot, 0u, erow, q6, q7);
             else
-                pixels(std::integral_constant<bool, BEAM>{}, q0, q1, rot, (flags & FL_RX_FULL) ? 0u : 1u, erow);
+                pixels(std::integral_constant<bool, BEAM>{}, q0, q1, rot, (flags & FL_RX_FULL) ? 0u : 1u, erow, q6,
+                       q7);
         }
         warp_arrive(&ebar[2 + (G & 1)]);
         if (!have_next) break;

@@ -63,6 +63,7 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     prm.beam_tan = (float)h->beam_tan;
     prm.beam_side = (float)h->beam_side;
     prm.cull = h->d_cull;
+    prm.vel = h->has_vel ? h->d_vel : nullptr;
     prm.hx = (float)hx;
     prm.hy = (float)hy;
     prm.hz = (float)hz;
@@ -93,7 +94,9 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
 
 template <typename ET, bool DIM3, int MODE>
 static int launch_one(const Setup& S, cudaStream_t st) {
-    auto kern = S.prm.beam ? tdbp_kernel<ET, DIM3, MODE, true> : tdbp_kernel<ET, DIM3, MODE, false>;
+    const bool mv = S.prm.vel != nullptr;
+    auto kern = S.prm.beam ? (mv ? tdbp_kernel<ET, DIM3, MODE, true, true> : tdbp_kernel<ET, DIM3, MODE, true, false>)
+                           : (mv ? tdbp_kernel<ET, DIM3, MODE, false, true> : tdbp_kernel<ET, DIM3, MODE, false, false>);
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());

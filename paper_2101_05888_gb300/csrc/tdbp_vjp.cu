@@ -8,7 +8,9 @@ namespace core {
 
 template <typename ET, bool DIM3, int MODE>
 static int launch_one_grad(const Setup& S, cudaStream_t st) {
-    auto kern = S.prm.beam ? tdbp_kernel<ET, DIM3, MODE, true> : tdbp_kernel<ET, DIM3, MODE, false>;
+    const bool mv = S.prm.vel != nullptr;
+    auto kern = S.prm.beam ? (mv ? tdbp_kernel<ET, DIM3, MODE, true, true> : tdbp_kernel<ET, DIM3, MODE, true, false>)
+                           : (mv ? tdbp_kernel<ET, DIM3, MODE, false, true> : tdbp_kernel<ET, DIM3, MODE, false, false>);
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());
