@@ -797,6 +797,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     warp_arrive(&ebar[0]);
     aborted = *abort_flag != 0;
     int prev_ping = -1;
+    int seq_ping = ping0, seq_ch = 0;               // candidate order (no culling)
     for (int G = 0; !aborted && nkc > 0; ++G) {
         // the group after (kc, gi)
         int kn = kc, gn = gi + 1, nkn = nkc, lastkn = lastkc;
@@ -839,9 +840,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         for (int j = 0; j < ng; ++j) {
             const int pr = gi * GROUP + j;
             const float4* hr = hq + pr * (HROW / 4);
-            const float4 q3 = hr[3];
-            const int ping = __float_as_int(q3.y);
-            const int flags = BEAM ? __float_as_int(q3.z) : (FL_TX_FULL | FL_RX_FULL);
+            // without culling the pairs arrive in candidate order, so the ping
+            // is tracked here; with culling it comes from the record
+            int ping, flags = FL_TX_FULL | FL_RX_FULL;
+            float4 q3;
+            if (BEAM) {
+                q3 = hr[3];
+                ping = __float_as_int(q3.y);
+                flags = __float_as_int(q3.z);
+            } else {
+                ping = seq_ping;
+                if (++seq_ch == p.C) {
+                    seq_ch = 0;
+                    ++seq_ping;
+                }
+            }
             float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (BEAM) {
                 const float4 q4 = hr[4], q5 = hr[5];
@@ -855,7 +868,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 tT1 = q2.y;
                 tT2 = q2.z;
                 tNT2 = q2.w;
-                tNT = q3.x;
+                tNT = BEAM ? q3.x : hr[3].x;
                 const float tTv = DIM3 ? tT2 : tT1;
                 const float X = fixed_dot<DIM3>(tT0, tT1, dxv, dyv_c);
                 tmask = 0xffu;
