@@ -298,6 +298,44 @@ int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, float* d_tabl
  * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check. */
 int sas_sync_status(sas_geometry_t h, void* cuda_stream);
 
+/* ---- Data conditioning (Sec. II-E) and range compression ----------------
+ * Rows are complex64 [rows][n], device, caller-owned; d_out may equal d_in.
+ * Calls are stream-ordered and allocate their scratch on the stream. */
+
+/* Range compression of raw echo rows by the transmitted replica p [L]
+ * (complex64, device): y[k] = sum_l e[k + l] conj(p[l]) / sum_l |p[l]|^2
+ * for k < n, samples past the row reading zero (an echo of A p(t - tau)
+ * peaks at the sample of tau with value A).  FP32 FFT overlap-save.
+ * 1 <= L <= 4096.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_matched_filter(const void* d_raw, int64_t rows, int32_t n, const void* d_replica, int32_t L, void* d_out,
+                       void* cuda_stream);
+
+/* Spectral whitening, Eq. 9: P(f) = mean over the rows of |FFT(e)(f)|^2,
+ * G(f) = 1 / (gamma mean_f P + P(f)) scaled so that max G = 1 (the smallest
+ * attenuation is 0 dB), applied as a power gain: rows = IFFT(FFT(e) sqrt G).
+ * n a power of two in [4, 16384]; gamma >= 0.  d_gain: optional device
+ * float [n] receiving sqrt G.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_whiten(const void* d_in, void* d_out, int64_t rows, int32_t n, double gamma, float* d_gain,
+               void* cuda_stream);
+
+/* Time-varying gain, Eq. 10: P(t) = median over the rows of the FP32 power
+ * |e(t)|^2 (re*re + im*im rounded to FP32; an even count takes the mean of
+ * the two middle values), G(t) = 1 / (alpha mean_t P + P(t)), applied as a
+ * power gain: rows times sqrt G(t) (no correction where alpha = 0 and the
+ * median is 0).  Optional outputs: d_gain float [n]
+ * (sqrt G), d_median double [n] (P).  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_tvg(const void* d_in, void* d_out, int64_t rows, int32_t n, double alpha, float* d_gain, double* d_median,
+            void* cuda_stream);
+
+/* Dynamic range compression, Eqs. 11-12: I_n = |I| / max |I| (FP32, |I| the
+ * correctly rounded magnitude), q = (b - b m) / (m - b m) with m the median
+ * of I_n (even count: mean of the two middle values), and
+ * d_out[i] = q I_n / ((q - 1) I_n + 1) (float, [0, 1], the median pixel
+ * maps to b; a median of 1 gives the identity map, a median of 0 sends every
+ * non-zero pixel to 1).  d_image complex64 [npix]; 0 < b < 1.  d_stats: optional
+ * device double [3] = {q, m, max |I|}.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_drc(const void* d_image, int64_t npix, double b, float* d_out, double* d_stats, void* cuda_stream);
+
 /* Ray-culling counts (Sec. II-C: blocks of pixels outside the beams are
  * pruned before the per-pixel test) accumulated by the forward and
  * offset-gradient backprojections of this handle since the last reset:

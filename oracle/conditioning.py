@@ -20,7 +20,10 @@ repository's design notes):
   values; for an even count the median is the FP64 mean of the two middle
   values.
 * Eq. 11: I is the magnitude |I| normalised by its maximum (FP32 division);
-  Eq. 12 uses the median of that normalised image.
+  Eq. 12 uses the median of that normalised image.  Where Eq. 12 has no
+  value (median 1: every pixel at the maximum; median 0) the limits are
+  taken: the identity map, and 1 for every non-zero pixel.  Eq. 10 with a
+  zero denominator (alpha = 0 and a silent median) applies no correction.
 * The replica of a pulse of length T and bandwidth B is the complex
   baseband up-chirp p(t) = exp(j pi (B/T) (t - T/2)^2) sampled at t = l/fs,
   l = 0 .. round(T fs) - 1; the matched filter output is
@@ -72,7 +75,9 @@ def tvg(e, alpha: float):
     """Eq. 10 on a batch e [rows, N]: returns (e sqrt(G), G, P_med)."""
     e = np.asarray(e)
     Pmed = median_of(power_f32(e), axis=0)
-    G = 1.0 / (alpha * np.mean(Pmed) + Pmed)
+    den = alpha * np.mean(Pmed) + Pmed
+    # a silent median with alpha = 0 leaves Eq. 10 without a value: no correction
+    G = np.where(den > 0, 1.0 / np.where(den > 0, den, 1.0), 1.0)
     return e.astype(np.complex128) * np.sqrt(G), G, Pmed
 
 
@@ -81,9 +86,16 @@ def drc(img, b: float):
     m = magnitude_f32(img).reshape(-1)
     In = (m / np.max(m)).astype(np.float32)
     med = median_of(In)
-    q = (b - b * med) / (med - b * med)
     In64 = In.astype(np.float64)
-    out = q * In64 / ((q - 1.0) * In64 + 1.0)
+    if med >= 1.0:            # every pixel at the maximum: Eq. 12 is 0/0, the identity map
+        q = 1.0
+        out = In64
+    elif med <= 0.0:          # the median pixel is dark: q -> infinity, every lit pixel to 1
+        q = np.inf
+        out = (In64 > 0).astype(np.float64)
+    else:
+        q = (b - b * med) / (med - b * med)
+        out = q * In64 / ((q - 1.0) * In64 + 1.0)
     return out.reshape(np.shape(img)), q, med
 
 

@@ -45,6 +45,7 @@ ENTRY_POINTS = [
     "sas_sharpness_static", "sas_simulate_points",
     "sas_interp_eval", "sas_mlp_make_windows", "sas_mlp_workspace_bytes", "sas_mlp_loss_grad",
     "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_cull_stats",
+    "sas_matched_filter", "sas_whiten", "sas_tvg", "sas_drc",
     "sas_debug_starve_copies",
 ]
 
@@ -117,6 +118,10 @@ def lib():
                 "sas_interp_tabulate_mlp": ([V, ctypes.c_int32, V, V], I),
                 "sas_sync_status": ([V, V], I),
                 "sas_cull_stats": ([V, ctypes.POINTER(ctypes.c_longlong), I, V], I),
+                "sas_matched_filter": ([V, I64, ctypes.c_int32, V, ctypes.c_int32, V, V], I),
+                "sas_whiten": ([V, V, I64, ctypes.c_int32, D, V, V], I),
+                "sas_tvg": ([V, V, I64, ctypes.c_int32, D, V, V, V], I),
+                "sas_drc": ([V, I64, D, V, V, V], I),
                 "sas_debug_starve_copies": ([V, I, ctypes.c_int32], I),
             }
             for name, (args, res) in sig.items():
@@ -269,6 +274,23 @@ def sas_cull_stats(h, reset: int = 0, stream=None):
     out = (ctypes.c_longlong * 3)()
     _check(lib().sas_cull_stats(h, out, reset, _stream(stream)))
     return tuple(int(v) for v in out)
+
+
+def sas_matched_filter(d_raw, rows: int, n: int, d_replica, L: int, d_out, stream=None):
+    _check(lib().sas_matched_filter(_ptr(d_raw), rows, n, _ptr(d_replica), L, _ptr(d_out), _stream(stream)))
+
+
+def sas_whiten(d_in, d_out, rows: int, n: int, gamma: float, d_gain=None, stream=None):
+    _check(lib().sas_whiten(_ptr(d_in), _ptr(d_out), rows, n, float(gamma), _ptr(d_gain), _stream(stream)))
+
+
+def sas_tvg(d_in, d_out, rows: int, n: int, alpha: float, d_gain=None, d_median=None, stream=None):
+    _check(lib().sas_tvg(_ptr(d_in), _ptr(d_out), rows, n, float(alpha), _ptr(d_gain), _ptr(d_median),
+                         _stream(stream)))
+
+
+def sas_drc(d_image, npix: int, b: float, d_out, d_stats=None, stream=None):
+    _check(lib().sas_drc(_ptr(d_image), npix, float(b), _ptr(d_out), _ptr(d_stats), _stream(stream)))
 
 
 def sas_debug_starve_copies(h, skip: int, wait_limit_ms: int):

@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsas.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
-SOURCES = ["sas_api.cu", "tdbp_forward.cu", "tdbp_vjp.cu", "tdbp_adjoint.cu", "sharpness.cu", "sharpness_static.cu", "mlp.cu", "simulate.cu"]
-HEADERS = ["sas_common.cuh", "tdbp_core.cuh"]
+SOURCES = ["sas_api.cu", "tdbp_forward.cu", "tdbp_vjp.cu", "tdbp_adjoint.cu", "sharpness.cu", "sharpness_static.cu", "mlp.cu",
+           "simulate.cu", "condition.cu"]
+HEADERS = ["sas_common.cuh", "tdbp_core.cuh", "fft.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

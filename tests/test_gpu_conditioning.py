@@ -1,0 +1,108 @@
+"""GPU parity of the conditioning kernels (Sec. II-E, Eqs. 9-12) and the
+matched filter against the FP64 oracle: FP32 FFT paths within 1e-5
+(relative L2), order statistics bit-exact (both sides select on the same
+FP32 values), gains and maps within 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import conditioning as cond
+import paper_2101_05888_gb300 as sas
+from paper_2101_05888_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _colored(rows, n, seed):
+    rng = np.random.default_rng(seed)
+    w = rng.normal(size=(rows, n + 4)) + 1j * rng.normal(size=(rows, n + 4))
+    h = np.array([1.0, 0.7 - 0.2j, 0.3, -0.1j, 0.05])
+    return np.stack([np.convolve(r, h, mode="valid") for r in w]).astype(np.complex64)
+
+
+@pytest.mark.parametrize("rows,n,L", [(6, 1000, 200), (3, 16384, 200), (4, 777, 1), (2, 5000, 4096)])
+def test_matched_filter_matches_oracle(rows, n, L):
+    """Ragged row lengths, a one-tap replica and the largest replica."""
+    rng = np.random.default_rng(n + L)
+    raw = (rng.normal(size=(rows, n)) + 1j * rng.normal(size=(rows, n))).astype(np.complex64)
+    rep = cond.lfm_replica(20e3, L / 40e3, 40e3).astype(np.complex64) if L > 1 else np.array([0.5 - 0.5j], np.complex64)
+    out = torch.empty((rows, n), dtype=torch.complex64, device="cuda")
+    sas.sas_matched_filter(torch.from_numpy(raw).cuda(), rows, n, torch.from_numpy(rep).cuda(), rep.size, out)
+    torch.cuda.synchronize()
+    ref = cond.matched_filter(raw, rep)
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5
+
+
+def test_matched_filter_compresses_simulated_raw_echo():
+    """Raw LFM echoes of the small-2D scene compress on the GPU to the same
+    rows as the oracle's matched filter of the same raw data."""
+    w = synth.scaled(synth.workload("small_2d"), n_pings=4, n_rx=2, n_samples=2048)
+    nav = synth.nav(w)
+    tx, rx = oracle.sensor_positions(nav["true_pos"], nav["att"], nav["tx_lever"], nav["rx_lever"])
+    sig = oracle.Signal(synth.FC, synth.FS, synth.C_SOUND, w.t0, w.n_samples)
+    scat = synth.scatterers(w)[:4]
+    raw = cond.simulate_raw_points(tx, rx, sig, synth.BANDWIDTH, synth.PULSE_T, scat).reshape(-1, w.n_samples)
+    rep = cond.lfm_replica(synth.BANDWIDTH, synth.PULSE_T, synth.FS)
+    out = torch.empty(raw.shape, dtype=torch.complex64, device="cuda")
+    sas.sas_matched_filter(torch.from_numpy(raw.astype(np.complex64)).cuda(), raw.shape[0], raw.shape[1],
+                           torch.from_numpy(rep.astype(np.complex64)).cuda(), rep.size, out)
+    torch.cuda.synchronize()
+    ref = cond.matched_filter(raw.astype(np.complex64), rep.astype(np.complex64))
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5
+    assert np.abs(ref).max() > 0.5          # the scatterers compressed to peaks
+
+
+@pytest.mark.parametrize("rows,n,gamma", [(40, 256, 0.0), (64, 1024, 0.1), (9, 16384, 0.05), (1, 8, 1.0)])
+def test_whitening_matches_oracle(rows, n, gamma):
+    e = _colored(rows, n, n + rows)
+    d_in = torch.from_numpy(e).cuda()
+    out = torch.empty_like(d_in)
+    gain = torch.empty(n, dtype=torch.float32, device="cuda")
+    sas.sas_whiten(d_in, out, rows, n, gamma, gain)
+    torch.cuda.synchronize()
+    ref, Gh = cond.whiten(e, gamma)
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5
+    assert np.abs(gain.cpu().numpy() - np.sqrt(Gh)).max() < 1e-6
+    assert gain.max().item() == 1.0
+    # in place
+    sas.sas_whiten(d_in, d_in, rows, n, gamma)
+    torch.cuda.synchronize()
+    assert oracle.rel_l2(d_in.cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("rows,n,alpha", [(41, 300, 0.0), (64, 333, 0.25), (1, 40, 0.1), (2, 65, 0.0)])
+def test_tvg_matches_oracle(rows, n, alpha):
+    rng = np.random.default_rng(rows * n)
+    env = np.exp(-np.linspace(0, 4, n))
+    e = ((rng.normal(size=(rows, n)) + 1j * rng.normal(size=(rows, n))) * env).astype(np.complex64)
+    e[0, :7] = 0.0                         # ties and zeros in the selection
+    e[1 % rows, 3:9] = e[0, 3:9]
+    d_in = torch.from_numpy(e).cuda()
+    out = torch.empty_like(d_in)
+    gain = torch.empty(n, dtype=torch.float32, device="cuda")
+    med = torch.empty(n, dtype=torch.float64, device="cuda")
+    sas.sas_tvg(d_in, out, rows, n, alpha, gain, med)
+    torch.cuda.synchronize()
+    ref, G, Pmed = cond.tvg(e, alpha)
+    assert np.array_equal(med.cpu().numpy(), Pmed)            # exact selection
+    assert np.abs(gain.cpu().numpy() - np.sqrt(G)).max() <= 1e-6 * np.sqrt(G).max()
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-6
+
+
+@pytest.mark.parametrize("shape,b", [((63, 63), 0.35), ((64, 64), 0.2), ((1, 1), 0.5), ((1000, 999), 0.3)])
+def test_drc_matches_oracle(shape, b):
+    rng = np.random.default_rng(shape[0])
+    img = (rng.standard_exponential(shape) ** 3 * np.exp(1j * rng.uniform(0, 6.28, shape))).astype(np.complex64)
+    if img.size > 4:
+        img.reshape(-1)[:5] = img.reshape(-1)[5]          # ties at one value
+    n = img.size
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    stats = torch.empty(3, dtype=torch.float64, device="cuda")
+    sas.sas_drc(torch.from_numpy(img).cuda(), n, b, out, stats)
+    torch.cuda.synchronize()
+    ref, q, med = cond.drc(img, b)
+    st = stats.cpu().numpy()
+    assert st[1] == med and st[2] == float(cond.magnitude_f32(img).max())    # exact selection and maximum
+    assert abs(st[0] - q) <= 1e-12 * abs(q)
+    assert np.abs(out.cpu().numpy() - ref.reshape(-1)).max() < 1e-6

@@ -110,3 +110,28 @@ def test_drc_median_maps_to_brightness():
         assert np.all(np.diff(o) >= 0)
         assert abs(o[-1] - 1.0) < 1e-12 and o[0] >= 0.0
         assert m.size % 2 == 1 and abs(o[(m.size - 1) // 2] - b) < 1e-12     # the median pixel
+
+
+def test_drc_degenerate_medians_take_the_limits():
+    """Median 1 (one pixel, or all pixels equal): the identity; median 0
+    (most pixels dark): every lit pixel maps to 1, as q -> infinity in
+    Eq. 11."""
+    out, q, med = cond.drc(np.array([[0.3 - 0.4j]], dtype=np.complex64), 0.4)
+    assert med == 1.0 and q == 1.0 and out[0, 0] == 1.0
+    img = np.array([0, 0, 0, 0.5, 2.0], dtype=np.complex64)
+    out, q, med = cond.drc(img, 0.4)
+    assert med == 0.0 and np.isinf(q) and list(out) == [0, 0, 0, 1, 1]
+    # the limit agrees with Eq. 11 at a large finite q
+    In = np.array([0.25, 1.0])
+    qq = 1e12
+    assert np.allclose(qq * In / ((qq - 1) * In + 1), 1.0)
+
+
+def test_tvg_silent_median_leaves_samples():
+    e = np.zeros((3, 4), dtype=np.complex64)
+    e[0, 1] = 1.0 + 1.0j
+    e[:, 2:] = 1.0
+    out, G, Pmed = cond.tvg(e, 0.0)
+    assert Pmed[0] == 0 and Pmed[1] == 0 and G[0] == 1.0 and G[1] == 1.0
+    assert np.array_equal(out[:, :2], e[:, :2].astype(np.complex128))
+    assert np.allclose(np.abs(out[:, 2:]) ** 2, 1.0)
