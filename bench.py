@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pings", type=int, default=0, help="profiling: fewer pings (same grid and tiles)")
+    ap.add_argument("--stage", default="backproject",
+                    choices=["backproject", "matched_filter", "whiten", "tvg", "drc"],
+                    help="conditioning stages: HBM throughput on the workload's echo rows (or image)")
     ap.add_argument("--motion", action="store_true",
                     help="receivers move during reception (per-ping velocity), not stop-and-hop")
     ap.add_argument("--beam-deg", type=float, default=0.0,
@@ -336,6 +339,84 @@ def run_ours(args, rank, world, local_rank):
     geom.close()
 
 
+# algorithmic bytes per element (complex64 rows, or pixels for DRC): what a
+# stage must move at least -- read its input and write its output once, plus
+# the extra full read the statistic needs (whitening: spectrum power; TVG:
+# column medians); DRC reads the complex image and writes a float image
+STAGE_BYTES = {"matched_filter": 16, "whiten": 24, "tvg": 24, "drc": 12}
+
+
+def run_stage(args, rank, world, local_rank):
+    """One conditioning stage over the workload's full echo (matched filter,
+    whitening, TVG) or its image grid (DRC); value in GB/s of algorithmic
+    traffic, roofline against the measured HBM copy rate."""
+    import torch
+    import paper_2101_05888_gb300 as sas
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workload_of(args)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + rank)
+    if args.stage == "drc":
+        n_el = w.grid.n
+        x = torch.randn(n_el, dtype=torch.complex64, device=dev, generator=g)
+        out = torch.empty(n_el, dtype=torch.float32, device=dev)
+        step = lambda: sas.sas_drc(x, n_el, 0.3, out)
+        shape = "%d pixels" % n_el
+    else:
+        rows, n = w.n_pings * w.n_rx, w.n_samples
+        n_el = rows * n
+        x = torch.randn((rows, n), dtype=torch.complex64, device=dev, generator=g)
+        out = torch.empty_like(x)
+        if args.stage == "matched_filter":
+            L = int(round(synth.PULSE_T * synth.FS))
+            t = torch.arange(L, dtype=torch.float64, device=dev) / synth.FS
+            rep = torch.exp(1j * np.pi * (synth.BANDWIDTH / synth.PULSE_T) * (t - 0.5 * synth.PULSE_T) ** 2)
+            rep = rep.to(torch.complex64)
+            step = lambda: sas.sas_matched_filter(x, rows, n, rep, L, out)
+        elif args.stage == "whiten":
+            step = lambda: sas.sas_whiten(x, out, rows, n, 0.1)
+        else:
+            step = lambda: sas.sas_tvg(x, out, rows, n, 0.5)
+        shape = "%d rows x %d samples" % (rows, n)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t_ = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t_.item())
+    gbs = STAGE_BYTES[args.stage] * n_el / (ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = float(peaks.get("hbm_gbs") or 6800.0)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "%s throughput (algorithmic bytes)" % args.stage, "value": world * gbs, "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded complex Gaussian rows)",
+            "config": {"workload": w.name, "stage": args.stage, "shape": shape,
+                       "bytes_per_element": STAGE_BYTES[args.stage], "parallelism": "replicas",
+                       "l2": "inputs larger than L2, no flush between steps"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": None, "peak_basis": "measured HBM copy rate"},
+            "clocks": clk, "gpu_launches": None}), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -349,7 +430,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        run_ours(args, rank, world, local_rank)
+        if args.stage != "backproject":
+            run_stage(args, rank, world, local_rank)
+        else:
+            run_ours(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

@@ -477,12 +477,16 @@ extern "C" int sas_drc(const void* d_image, int64_t npix, double b, float* d_out
         return SAS_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    // scratch: |I| [npix] floats, the selection state and three doubles, each
+    // part starting on a 256-byte boundary
+    auto up256 = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t off_ds = up256(sizeof(float) * (size_t)npix);
+    const size_t off_st = up256(off_ds + sizeof(DrcState));
     char* scratch = nullptr;
-    const size_t bytes = sizeof(float) * (size_t)npix + 256 + sizeof(DrcState) + 3 * sizeof(double);
-    SAS_CUDA(cudaMallocAsync((void**)&scratch, bytes, st));
+    SAS_CUDA(cudaMallocAsync((void**)&scratch, off_st + 3 * sizeof(double), st));
     float* mag = reinterpret_cast<float*>(scratch);
-    DrcState* ds = reinterpret_cast<DrcState*>(scratch + ((sizeof(float) * (size_t)npix + 255) / 256) * 256);
-    double* stats = d_stats ? d_stats : reinterpret_cast<double*>(ds + 1);
+    DrcState* ds = reinterpret_cast<DrcState*>(scratch + off_ds);
+    double* stats = d_stats ? d_stats : reinterpret_cast<double*>(scratch + off_st);
     cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(DrcState), st);
     if (e == cudaSuccess) {
         const unsigned klo = (unsigned)((npix - 1) / 2);

@@ -106,3 +106,14 @@ def test_drc_matches_oracle(shape, b):
     assert st[1] == med and st[2] == float(cond.magnitude_f32(img).max())    # exact selection and maximum
     assert abs(st[0] - q) <= 1e-12 * abs(q)
     assert np.abs(out.cpu().numpy() - ref.reshape(-1)).max() < 1e-6
+
+
+def test_drc_without_stats_output():
+    """The scratch-held statistics path (no d_stats) gives the same image."""
+    rng = np.random.default_rng(9)
+    img = (rng.standard_exponential((257, 130)) * np.exp(1j * rng.uniform(0, 6.28, (257, 130)))).astype(np.complex64)
+    out = torch.empty(img.size, dtype=torch.float32, device="cuda")
+    sas.sas_drc(torch.from_numpy(img).cuda(), img.size, 0.3, out)
+    torch.cuda.synchronize()
+    ref, _, _ = cond.drc(img, 0.3)
+    assert np.abs(out.cpu().numpy() - ref.reshape(-1)).max() < 1e-6
