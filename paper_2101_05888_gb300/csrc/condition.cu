@@ -34,6 +34,8 @@ __device__ __forceinline__ float power_f32(float2 v) { return __fadd_rn(__fmul_r
 // Pc[f] = conj(FFT(p zero-padded to NF))[f] / (NF sum |p|^2)
 __global__ void __launch_bounds__(1024) mf_replica_kernel(const float2* __restrict__ rep, int L, int NF, float2* __restrict__ Pc) {
     extern __shared__ float2 buf[];
+    float2* tw = buf + NF;
+    fftdev::fft_twiddles(tw, NF);
     __shared__ double esum[32];
     double e = 0.0;
     for (int j = threadIdx.x; j < NF; j += blockDim.x) {
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(1024) mf_replica_kernel(const float2* __restri
     for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
     if ((threadIdx.x & 31) == 0) esum[threadIdx.x >> 5] = e;
     __syncthreads();
-    fft_smem(buf, NF, -1.f);
+    fft_smem(buf, tw, NF, -1.f);
     double E = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) E += esum[w];
     const float s = (float)(1.0 / ((double)NF * E));
@@ -55,6 +57,8 @@ __global__ void __launch_bounds__(1024) mf_replica_kernel(const float2* __restri
 __global__ void __launch_bounds__(1024) mf_block_kernel(const float2* __restrict__ raw, int n, int NF, int M, int nblk,
                                 const float2* __restrict__ Pc, float2* __restrict__ out) {
     extern __shared__ float2 buf[];
+    float2* tw = buf + NF;
+    fftdev::fft_twiddles(tw, NF);
     const long long row = blockIdx.x / nblk;
     const int b = blockIdx.x % nblk;
     const long long k0 = (long long)b * M;
@@ -64,10 +68,10 @@ __global__ void __launch_bounds__(1024) mf_block_kernel(const float2* __restrict
         buf[j] = k < n ? src[k] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_smem(buf, NF, -1.f);
+    fft_smem(buf, tw, NF, -1.f);
     for (int j = threadIdx.x; j < NF; j += blockDim.x) buf[j] = fftdev::cmul(buf[j], Pc[j]);
     __syncthreads();
-    fft_smem(buf, NF, 1.f);
+    fft_smem(buf, tw, NF, 1.f);
     float2* dst = out + row * (long long)n;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const long long k = k0 + j;
@@ -82,10 +86,12 @@ __global__ void __launch_bounds__(1024) mf_block_kernel(const float2* __restrict
 __global__ void __launch_bounds__(1024) whiten_spectra_kernel(const float2* __restrict__ in, float2* __restrict__ out,
                                                               long long rows, int n) {
     extern __shared__ float2 buf[];
+    float2* tw = buf + n;
+    fftdev::fft_twiddles(tw, n);
     for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
         for (int j = threadIdx.x; j < n; j += blockDim.x) buf[j] = in[r * n + j];
         __syncthreads();
-        fft_smem(buf, n, -1.f);
+        fft_smem(buf, tw, n, -1.f);
         for (int j = threadIdx.x; j < n; j += blockDim.x) out[r * n + j] = buf[j];
         __syncthreads();
     }
@@ -141,6 +147,8 @@ __global__ void whiten_gain_kernel(const double* __restrict__ P, int n, double g
 // pass 2: out[r] = IFFT(out[r] * gain) (the spectra from pass 1)
 __global__ void __launch_bounds__(1024) whiten_apply_kernel(float2* __restrict__ out, long long rows, int n, const float* __restrict__ gain) {
     extern __shared__ float2 buf[];
+    float2* tw = buf + n;
+    fftdev::fft_twiddles(tw, n);
     const float inv = 1.f / (float)n;
     for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -149,7 +157,7 @@ __global__ void __launch_bounds__(1024) whiten_apply_kernel(float2* __restrict__
             buf[j] = make_float2(v.x * g, v.y * g);
         }
         __syncthreads();
-        fft_smem(buf, n, 1.f);
+        fft_smem(buf, tw, n, 1.f);
         for (int j = threadIdx.x; j < n; j += blockDim.x) out[r * n + j] = make_float2(buf[j].x * inv, buf[j].y * inv);
         __syncthreads();
     }
@@ -384,7 +392,7 @@ extern "C" int sas_matched_filter(const void* d_raw, int64_t rows, int32_t n, co
     float2* Pc = nullptr;
     SAS_CUDA(cudaMallocAsync((void**)&Pc, sizeof(float2) * NF, st));
     const int nt = fft_threads(NF);
-    const size_t sm = sizeof(float2) * NF;
+    const size_t sm = sizeof(float2) * (NF + NF / 2);       // row + twiddles
     int rc = SAS_OK;
     cudaError_t e = cudaFuncSetAttribute(mf_replica_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
@@ -424,7 +432,7 @@ extern "C" int sas_whiten(const void* d_in, void* d_out, int64_t rows, int32_t n
         gain = own_gain;
     }
     const int nt = fft_threads(n);
-    const size_t sm = sizeof(float2) * n;
+    const size_t sm = sizeof(float2) * (n + n / 2);          // row + twiddles
     cudaError_t e = cudaFuncSetAttribute(whiten_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(whiten_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

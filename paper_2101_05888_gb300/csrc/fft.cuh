@@ -4,8 +4,9 @@
 // reads the inputs of its butterflies into registers, the block
 // synchronises, then it writes the outputs.  Forward: X[f] = sum_n x[n]
 // exp(-2 pi i f n / N); inverse: the same with +i and no 1/N (callers scale).
-// Twiddles from sincospif (FP32, a few ulp).  N = 2^m, 4 <= N <= 16384,
-// blockDim.x a multiple of 32, at most 1024.
+// Twiddles from a table tw[j] = exp(-2 pi i j / N), j < N/2, that the block
+// fills once (fft_twiddles, sincospif: FP32, a few ulp).  N = 2^m,
+// 4 <= N <= 16384, blockDim.x a multiple of 32, at most 1024.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,9 +22,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// tw[j] = exp(-2 pi i j / N), j < N / 2 (shared memory, filled by the block)
+__device__ void fft_twiddles(float2* tw, int N) {
+    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
+        float s, c;
+        sincospif(-2.f * (float)j / (float)N, &s, &c);
+        tw[j] = make_float2(c, s);
+    }
+    __syncthreads();
+}
+
 // sign = -1 forward, +1 inverse.  Requires blockDim.x >= N / 16 (so every
 // butterfly of a stage is held in registers by the loops below).
-__device__ void fft_smem(float2* buf, int N, float sign) {
+__device__ void fft_smem(float2* buf, const float2* tw, int N, float sign) {
     const int nt = blockDim.x, tid = threadIdx.x;
     const int N4 = N >> 2;
     int L = 1;
@@ -34,9 +45,8 @@ __device__ void fft_smem(float2* buf, int N, float sign) {
             const int j = tid + c * nt;
             if (j < N4) {
                 const int k = j & (L - 1);
-                float s1, c1;
-                sincospif(sign * (float)k / (float)(2 * L), &s1, &c1);    // w1 = exp(sign 2 pi i k / (4L))
-                const float2 w1 = make_float2(c1, s1);
+                const float2 t1 = tw[k * (N / (4 * L))];                 // exp(-2 pi i k / (4L))
+                const float2 w1 = make_float2(t1.x, -sign * t1.y);        // exp(sign 2 pi i k / (4L))
                 const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
                 const float2 a0 = buf[j], b1 = cmul(w1, buf[j + N4]), b2 = cmul(w2, buf[j + 2 * N4]),
                              b3 = cmul(w3, buf[j + 3 * N4]);
@@ -70,9 +80,8 @@ __device__ void fft_smem(float2* buf, int N, float sign) {
             const int j = tid + c * nt;
             if (j < N2) {
                 const int k = j & (L - 1);
-                float s1, c1;
-                sincospif(sign * (float)k / (float)L, &s1, &c1);            // exp(sign 2 pi i k / (2L))
-                const float2 a = buf[j], b = cmul(make_float2(c1, s1), buf[j + N2]);
+                const float2 t1 = tw[k * (N / (2 * L))];                 // exp(-2 pi i k / (2L))
+                const float2 a = buf[j], b = cmul(make_float2(t1.x, -sign * t1.y), buf[j + N2]);
                 y[2 * c + 0] = make_float2(a.x + b.x, a.y + b.y);
                 y[2 * c + 1] = make_float2(a.x - b.x, a.y - b.y);
             }
