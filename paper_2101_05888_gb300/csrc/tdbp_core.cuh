@@ -15,10 +15,11 @@
 //    reference terms at the tile centre x0 (R = x0 - sensor, |R|, tau_ref,
 //    floor(u_ref), fraction, carrier phase mod 1) written to shared memory,
 //    and a 2D bulk tensor copy of the echo segment the tile can reach into a
-//    ring of NSTAGE stages, completion on an mbarrier (transaction bytes).
-//    Samples outside the row are zero-filled by the copy engine.
-//  * consumers, 8 pixels a thread:
-//    - Farrow expansion for 4 pairs at a time: the interpolator's taps are
+//    ring of NSEG stages, completion on an mbarrier (transaction bytes).
+//    Samples outside the row are zero-filled by the copy engine.  The
+//    producer also expands each stage's pairs, 4 at a time (a group), into a
+//    ring of NBUF Farrow buffers handed to the consumers by mbarriers:
+//    - Farrow expansion: the interpolator's taps are
 //      degree-5 polynomials of g = f - 1/2, so s = sum_p g^p E_p[floor u] with
 //      E_p[i] = sum_m coef[m][p] e[i + k_m], computed once per (pair, tile)
 //      for every integer position the tile can reach.  Complex64 echoes:
@@ -26,8 +27,9 @@
 //      FP32.  16-bit echoes (rows normalised to |e| <= 1, so |E_p| stays
 //      near 1): E_0..E_5 in FP16 (24 bytes of the row) and the forward
 //      Horner in packed FP16, the row scale applied afterwards in FP32.
-//    - per pixel and pair, with the pair's reference terms broadcast by warp
-//      shuffle: differential range dr = (2 R.d + |d|^2) / (|R + d| + |R|), an
+//  * consumers, 8 pixels a thread, group after group:
+//    - per pixel and pair, with the pair's reference terms read by uniform
+//      16-byte loads: differential range dr = (2 R.d + |d|^2) / (|R + d| + |R|), an
 //      exact identity evaluated in FP32 on small quantities (d = x - x0); u
 //      and the phase from the reference values plus dr-derived offsets;
 //      floor/fraction on the FP32 pipe; three 16-byte shared loads (one 16-
@@ -49,16 +51,19 @@ constexpr int NCW = 7;                  // consumer warps
 constexpr int NCONS = 32 * NCW;         // consumer threads
 constexpr int NTHREADS = NCONS + 32;    // + producer warp
 constexpr int PAIRS = 32;               // (ping, channel) pairs per stage
-constexpr int NSTAGE = 2;               // copy ring depth
+constexpr int NSEG = 2;                 // echo-segment ring depth (stages)
+constexpr int NRS = 3;                  // record ring depth (stages)
+constexpr int NBUF = 4;                 // Farrow buffers (groups)
 constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
 constexpr int EROW = 48;                // bytes per Farrow row: E0..E5 float2 (FP16 rows: E0..E5 half2)
 constexpr int RUN = 10;                 // Farrow positions per expansion run
-constexpr int NRUNSLOT = NCONS / NP;    // expansion runs in flight (one power p per thread)
 constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
 enum { MODE_FORWARD = 0, MODE_OFFSET_GRAD = 1 };
+// group descriptor flags: the group ends its stage / is the last one
+enum { GD_STAGE_END = 1, GD_LAST = 2 };
 
 // record fields of one (ping, channel) pair, in the order of the float4 a
 // consumer loads: {2R_R, |R_R|^2}, {|R_R|, frac u_ref - 1/2, phase, scale},
@@ -72,7 +77,6 @@ enum {
     F_C0X, F_C0Y, F_C0Z, F_C1X, F_C1Y, F_C1Z, F_PAD0, F_PAD1, F_VX, F_VY, F_VZ, F_RV, F_BRX, F_BRY, F_BRZ, F_PAD2,
     NREC
 };
-constexpr int HROW = NREC;              // floats per record row (8 x float4)
 // pair flags: the whole tile lies inside the transmitter / receiver beam
 enum { FL_TX_FULL = 1, FL_RX_FULL = 2 };
 
@@ -297,15 +301,21 @@ struct Layout {
     size_t smem;
 };
 
+// Shared-memory layout (in this order): echo segments, Farrow rows, records,
+// coefficients, reduction scratch, group descriptors, mbarriers, abort flag.
+// Every part before the descriptors has a size that is a multiple of 16
+// bytes (slot_bytes: of 128; a Farrow row is 48 bytes; 32-float records),
+// so the 16-byte descriptor loads and stores are aligned.
+static_assert((NRS * PAIRS * NREC * 4) % 16 == 0 && (TAPS * NP * 4) % 16 == 0 && (NCW * 4 * 8) % 16 == 0,
+              "shared-memory parts must keep 16-byte alignment");
 inline size_t smem_bytes(int slot_bytes, int npos_pad) {
-    return (size_t)NSTAGE * PAIRS * slot_bytes          // echo segments
-           + (size_t)2 * GROUP * npos_pad * EROW        // Farrow rows, double buffered
-           + (size_t)NSTAGE * PAIRS * NREC * 4          // producer records
+    return (size_t)NSEG * PAIRS * slot_bytes            // echo segments
+           + (size_t)NBUF * GROUP * npos_pad * EROW     // Farrow rows
+           + (size_t)NRS * PAIRS * NREC * 4             // records
            + (size_t)TAPS * NP * 4                      // coefficients
-           + (size_t)2 * PAIRS * HROW * 4               // consumer copy of the records
            + (size_t)NCW * 4 * 8                        // cross-warp reduction (gradient)
-           + (size_t)(2 * NSTAGE + 4) * 8 + 16          // mbarriers (copy ring, Farrow buffers), abort flag
-           + (size_t)2 * NSTAGE * 4;                    // pairs per stage, last-stage flags
+           + (size_t)NBUF * 16                          // group descriptors
+           + (size_t)(NSEG + NRS + 2 * NBUF) * 8 + 16;  // mbarriers, abort flag
 }
 
 // ----------------------------------------------------------------------------
@@ -321,18 +331,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
-    unsigned char* seg = smem;
-    unsigned char* ebuf = seg + (size_t)NSTAGE * PAIRS * p.slot_bytes;
+    unsigned char* seg = smem;                                           // [NSEG][PAIRS] echo segments
+    unsigned char* ebuf = seg + (size_t)NSEG * PAIRS * p.slot_bytes;     // [NBUF][GROUP] Farrow rows
     const int ebuf_pair = p.npos_pad * EROW;          // positions padded to whole expansion runs
-    float* rec = reinterpret_cast<float*>(ebuf + 2 * GROUP * ebuf_pair);
-    float* coef_s = rec + NSTAGE * PAIRS * NREC;
-    float* hold = coef_s + TAPS * NP;
-    double* wred = reinterpret_cast<double*>(hold + 2 * PAIRS * HROW);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wred + NCW * 4);      // full[NSTAGE], empty[NSTAGE]
-    uint64_t* ebar = bars + 2 * NSTAGE;                                   // Farrow buffers: efull[2], eempty[2]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(ebar + 4);
-    volatile int* st_count = abort_flag + 4;                              // pairs in ring stage s
-    volatile int* st_last = st_count + NSTAGE;                            // stage s is the final one
+    float* rec = reinterpret_cast<float*>(ebuf + (size_t)NBUF * GROUP * ebuf_pair);   // [NRS][PAIRS][NREC]
+    float* coef_s = rec + NRS * PAIRS * NREC;                            // [TAPS][NP]
+    // every part so far has a size that is a multiple of 16 bytes (see smem_bytes)
+    double* wred = reinterpret_cast<double*>(coef_s + TAPS * NP);         // [NCW][4]
+    // [NBUF] group descriptors (written before, read after the efull barrier)
+    int4* gdesc = reinterpret_cast<int4*>(wred + NCW * 4);
+    uint64_t* full = reinterpret_cast<uint64_t*>(gdesc + NBUF);          // [NSEG] copies landed + records
+    uint64_t* rempty = full + NSEG;                                      // [NRS] consumers done with records
+    uint64_t* efull = rempty + NRS;                                      // [NBUF] Farrow rows written
+    uint64_t* eempty = efull + NBUF;                                     // [NBUF] Farrow rows read
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(eempty + NBUF);
 
     const int ntiles = p.tiles_x * p.tiles_y * p.tiles_z;
     const int tile = blockIdx.x % ntiles;
@@ -348,11 +360,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     const double cx = tx0 + 0.5 * (T::TX - 1), cy = ty0 + 0.5 * (T::TY - 1), cz = tz0 + 0.5 * (T::TZ - 1);
 
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(smem_u32(&bars[s]), 1);
-            mbar_init(smem_u32(&bars[NSTAGE + s]), NCW);
+        for (int s = 0; s < NSEG; ++s) mbar_init(smem_u32(&full[s]), 1);
+        for (int s = 0; s < NRS; ++s) mbar_init(smem_u32(&rempty[s]), NCW);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(smem_u32(&efull[b]), 1);
+            mbar_init(smem_u32(&eempty[b]), NCW);
         }
-        for (int b = 0; b < 4; ++b) mbar_init(smem_u32(&ebar[b]), NCW);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -361,104 +374,175 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
 
     if (warp == 0) {
         // ================= producer =================
-        // Scans the candidate pairs 32 at a time, drops those whose beams
-        // cannot see the tile, and packs the rest into full stages of PAIRS
-        // pairs (the last stage may be partial or empty and carries the
-        // last-stage flag).  Each pair's copy is announced on the stage's full
-        // barrier (expect_tx) before it is issued; lane 0 arrives once the
-        // stage's records are written.
+        // Stages of up to PAIRS (ping, channel) pairs: the producer scans the
+        // candidates 32 at a time, drops those whose beams cannot see the tile,
+        // writes each surviving pair's record and issues the copy of its echo
+        // segment (announced on the stage's full barrier).  It fills stage k + 1
+        // before it expands stage k, group by group, into the Farrow buffers the
+        // consumers read; a descriptor per buffer tells them which pairs it holds.
         const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = p.z0 + (DIM3 ? cz * p.dz : 0.0);
         const uint32_t seg_bytes = (uint32_t)p.seglen * (uint32_t)sizeof(ET);
-        int k = 0;            // stages opened
-        int fill = 0;         // pairs in the open stage
-        bool open = false;
         unsigned n_cand = 0, n_act = 0, n_edge = 0;   // this lane's culling counts
+        bool failed = false;
         auto fail = [&]() {
             if (lane == 0) {
                 *abort_flag = 1;
                 atomicOr(p.status, DEV_TIMEOUT);
             }
             __syncwarp();
+            failed = true;
         };
-        auto open_stage = [&]() -> bool {
-            const int s = k % NSTAGE;
-            if (k >= NSTAGE && !mbar_wait_bounded(smem_u32(&bars[NSTAGE + s]), ((k / NSTAGE) - 1) & 1, p.wait_ns))
-                fail();
-            __syncwarp();
-            if (*abort_flag) return false;
-            ++k;
-            fill = 0;
-            open = true;
-            return true;
-        };
-        auto close_stage = [&](bool last) {
-            const int s = (k - 1) % NSTAGE;
-            __syncwarp();
-            if (lane == 0) {
-                st_count[s] = fill;
-                st_last[s] = last ? 1 : 0;
-                mbar_arrive(smem_u32(&bars[s]));
-            }
-            __syncwarp();
-            open = false;
-        };
-        for (long long qb = q0; qb < q1; qb += PAIRS) {
-            const long long q = qb + lane;
-            const bool valid = q < q1;
-            const int i = valid ? (int)(q / p.C) : 0;
-            PairGeo G{};
-            int flags = FL_TX_FULL | FL_RX_FULL;
+        // candidate scan state (persists across stages)
+        long long qb = q0;
+        unsigned amask = 0u;
+        int nact = 0, done = 0;
+        PairGeo Gv{};
+        int flv = FL_TX_FULL | FL_RX_FULL, iv = 0;
+        long long qv = 0;
+        float rc6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        auto load_batch = [&]() {
+            qv = qb + lane;
+            const bool valid = qv < q1;
+            iv = valid ? (int)(qv / p.C) : 0;
+            flv = FL_TX_FULL | FL_RX_FULL;
             bool active = valid;
-            float rc6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (valid) {
-                G = pair_geo(p, X0, Y0, Z0, q, i);
+                Gv = pair_geo(p, X0, Y0, Z0, qv, iv);
                 if (BEAM) {
 #pragma unroll
-                    for (int t = 0; t < 6; ++t) rc6[t] = p.rotc[6 * (size_t)i + t];
-                    const int ct_ = beam_class<DIM3>(p, (float)G.Tx, (float)G.Ty, (float)G.Tz, rc6);
-                    const int cr_ = beam_class<DIM3>(p, (float)G.Rx, (float)G.Ry, (float)G.Rz, rc6);
+                    for (int t = 0; t < 6; ++t) rc6[t] = p.rotc[6 * (size_t)iv + t];
+                    const int ct_ = beam_class<DIM3>(p, (float)Gv.Tx, (float)Gv.Ty, (float)Gv.Tz, rc6);
+                    const int cr_ = beam_class<DIM3>(p, (float)Gv.Rx, (float)Gv.Ry, (float)Gv.Rz, rc6);
                     active = ct_ != 0 && cr_ != 0;
-                    flags = (ct_ == 2 ? FL_TX_FULL : 0) | (cr_ == 2 ? FL_RX_FULL : 0);
+                    flv = (ct_ == 2 ? FL_TX_FULL : 0) | (cr_ == 2 ? FL_RX_FULL : 0);
                 }
             }
             n_cand += valid ? 1u : 0u;
             n_act += active ? 1u : 0u;
-            n_edge += (active && flags != (FL_TX_FULL | FL_RX_FULL)) ? 1u : 0u;
-            const unsigned amask = __ballot_sync(0xffffffffu, active);
-            const int n = __popc(amask);
-            const int rank = __popc(amask & ((1u << lane) - 1u));
-            int done = 0;
-            while (done < n) {
-                if (!open && !open_stage()) break;
-                const int take = min(PAIRS - fill, n - done);
-                if (active && rank >= done && rank < done + take) {
-                    const int s = (k - 1) % NSTAGE;
-                    const int slot = fill + rank - done;
-                    float* rc = rec + (s * PAIRS + slot) * NREC;
-                    const int base = pair_record(p, G, rc, 1, MOTION ? p.vel + 3 * (size_t)i : nullptr);
+            n_edge += (active && flv != (FL_TX_FULL | FL_RX_FULL)) ? 1u : 0u;
+            amask = __ballot_sync(0xffffffffu, active);
+            nact = __popc(amask);
+            done = 0;
+            qb += PAIRS;
+        };
+        // fills stage k; returns its pair count, sets last when no candidate remains
+        auto fill = [&](int k, bool& last) -> int {
+            const int rs = k % NRS, ss = k % NSEG;
+            if (k >= NRS && !mbar_wait_bounded(smem_u32(&rempty[rs]), ((k / NRS) - 1) & 1, p.wait_ns)) fail();
+            // the segment slot was last read by this warp's expansion of stage k - NSEG:
+            // order those generic-proxy reads before the copies that overwrite it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            int cnt = 0;
+            const uint32_t bar = smem_u32(&full[ss]);
+            while (!failed && cnt < PAIRS) {
+                if (done >= nact) {
+                    if (qb >= q1) break;
+                    load_batch();
+                    continue;
+                }
+                const int take = min(PAIRS - cnt, nact - done);
+                const bool act = (amask >> lane) & 1u;
+                const int rank = __popc(amask & ((1u << lane) - 1u));
+                if (act && rank >= done && rank < done + take) {
+                    const int slot = cnt + rank - done;
+                    float* rc = rec + (rs * PAIRS + slot) * NREC;
+                    const int base = pair_record(p, Gv, rc, 1, MOTION ? p.vel + 3 * (size_t)iv : nullptr);
                     const int seg_start = base - (((base % p.seg_align) + p.seg_align) % p.seg_align);
                     rc[F_OFF] = __int_as_float(base - seg_start);
-                    rc[F_SCALE] = p.scale ? p.scale[q] : 1.0f;
-                    rc[F_PING] = __int_as_float(i);
-                    rc[F_FLAGS] = __int_as_float(flags);
+                    rc[F_SCALE] = p.scale ? p.scale[qv] : 1.0f;
+                    rc[F_PING] = __int_as_float(iv);
+                    rc[F_FLAGS] = __int_as_float(flv);
 #pragma unroll
                     for (int t = 0; t < 6; ++t) rc[F_C0X + t] = rc6[t];
-                    const uint32_t bar = smem_u32(&bars[s]);
                     mbar_expect_tx(bar, seg_bytes);
                     if (!p.skip_copies)
-                        tma_load_2d(smem_u32(seg + ((size_t)s * PAIRS + slot) * p.slot_bytes), &tmap, seg_start,
-                                    (int32_t)q, bar);
+                        tma_load_2d(smem_u32(seg + ((size_t)ss * PAIRS + slot) * p.slot_bytes), &tmap, seg_start,
+                                    (int32_t)qv, bar);
                 }
-                fill += take;
+                cnt += take;
                 done += take;
-                if (fill == PAIRS) close_stage(false);
             }
-            if (*abort_flag) break;
+            last = qb >= q1 && done >= nact;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar);
+            return cnt;
+        };
+
+        // expansion: lane = (run slot, power); 5 run slots of 6 powers, lanes 30, 31 idle
+        constexpr int RSLOTS = 32 / NP;
+        const int Ep = lane % NP, Erun = lane < RSLOTS * NP ? lane / NP : (1 << 30);
+        const int runs_per_pair = (p.npos + RUN - 1) / RUN;
+        float2 cc2[TAPS];
+#pragma unroll
+        for (int m = 0; m < TAPS; ++m) cc2[m] = make_float2(coef_s[m * NP + Ep], coef_s[m * NP + Ep]);
+        const int e_off = E16 ? Ep * 4 : Ep * 8;
+        int G = 0;   // groups emitted
+        auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
+            const int b = G % NBUF;
+            if (G >= NBUF && !mbar_wait_bounded(smem_u32(&eempty[b]), ((G / NBUF) - 1) & 1, p.wait_ns)) fail();
+            if (!failed && ng > 0) {
+                const float* rc = rec + rs * PAIRS * NREC;
+                unsigned char* eb = ebuf + (size_t)b * GROUP * ebuf_pair;
+                const int total = ng * runs_per_pair;
+                for (int run = Erun; run < total; run += RSLOTS) {
+                    const int j = run / runs_per_pair;
+                    const int pos0 = (run - j * runs_per_pair) * RUN;
+                    const int pr = pr0 + j;
+                    const unsigned char* slot = seg + ((size_t)ss * PAIRS + pr) * p.slot_bytes;
+                    const int off = __float_as_int(rc[pr * NREC + F_OFF]) + pos0;
+                    const float sc = E16 ? 1.0f : rc[pr * NREC + F_SCALE];
+                    float2 w[RUN + TAPS - 1];
+#pragma unroll
+                    for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
+                    unsigned char* dst = eb + j * ebuf_pair + pos0 * EROW + e_off;
+#pragma unroll
+                    for (int kq = 0; kq < RUN; ++kq) {
+                        float2 e = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
+                        if (E16)
+                            *reinterpret_cast<__half2*>(dst + kq * EROW) = __floats2half2_rn(e.x, e.y);
+                        else
+                            *reinterpret_cast<float2*>(dst + kq * EROW) = e;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                gdesc[b] = make_int4(rs, pr0, ng, flags);
+                mbar_arrive(smem_u32(&efull[b]));
+            }
+            ++G;
+        };
+
+        bool last_cur = false, last_next = false;
+        int kf = 1, kw = 0;   // stages filled; stages whose copies were waited for
+        int n_cur = fill(0, last_cur), n_next = 0;
+        int k = 0;
+        while (!failed) {
+            if (!last_cur) {
+                n_next = fill(k + 1, last_next);
+                ++kf;
+            }
+            // stage k's copies (and its records) have landed
+            if (!failed && !mbar_wait_bounded(smem_u32(&full[k % NSEG]), (k / NSEG) & 1, p.wait_ns)) fail();
+            if (failed) break;
+            kw = k + 1;
+            const int ngrp = (n_cur + GROUP - 1) / GROUP;
+            if (ngrp == 0) emit(k % NRS, 0, 0, GD_STAGE_END | (last_cur ? GD_LAST : 0), k % NSEG);
+            for (int gi = 0; gi < ngrp && !failed; ++gi) {
+                const bool end = gi == ngrp - 1;
+                emit(k % NRS, gi * GROUP, min(GROUP, n_cur - gi * GROUP),
+                     (end ? GD_STAGE_END : 0) | (end && last_cur ? GD_LAST : 0), k % NSEG);
+            }
+            if (last_cur) break;
+            ++k;
+            n_cur = n_next;
+            last_cur = last_next;
         }
-        if (!*abort_flag && (open || open_stage())) close_stage(true);
-        // every issued stage must have landed before the CTA may exit
-        for (int kk = max(0, k - NSTAGE); kk < k; ++kk)
-            mbar_wait_bounded(smem_u32(&bars[kk % NSTAGE]), (kk / NSTAGE) & 1, p.wait_ns);
+        // copies issued for a stage that was never expanded must land before exit
+        for (int kk = kw; kk < kf; ++kk) mbar_wait_bounded(smem_u32(&full[kk % NSEG]), (kk / NSEG) & 1, p.wait_ns);
         if (p.cull) {
             n_cand = __reduce_add_sync(0xffffffffu, n_cand);
             n_act = __reduce_add_sync(0xffffffffu, n_act);
@@ -480,7 +564,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // per slot s: the varying offset d_var(s), |d|^2 and the transmitter
     // differential range of the current ping, held as pairs of slots (2k, 2k+1)
     // for the packed geometry.  The offsets are formed exactly as the adjoint
-    // kernel forms them (slot_offsets), so both evaluate identical paths.
+    // kernel forms them, so both evaluate identical paths.
     float2 dvp[PX / 2], d2p[PX / 2], dTp[PX / 2];
 #define PXS(arr, s) (((s) & 1) ? arr[(s) >> 1].y : arr[(s) >> 1].x)
     float2 acc[PX];                       // forward: image accumulators; gradient: G(x)
@@ -513,74 +597,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     float gacc0 = 0.f, gacc1 = 0.f, gacc2 = 0.f;   // gradient: receiver-side sum for the current ping
     uint32_t tmask = 0xffu;                         // pixels the current ping's transmitter sees
 
-    // Farrow expansion work split: thread (run slot r, power p) computes E_p at
-    // RUN consecutive positions of one pair of the group from a sliding window
-    // of RUN + 7 samples.  Runs never need a bounds test: the Farrow buffer and
-    // the echo slot are padded to whole runs (padding values are never read).
-    const int Ep = ct % NP;
-    const int Erun = ct < NRUNSLOT * NP ? ct / NP : (1 << 30);   // 0 .. NRUNSLOT - 1; the rest idle
-    const int runs_per_pair = (p.npos + RUN - 1) / RUN;
-    float2 cc2[TAPS];                               // this thread's coefficients, packed (c, c)
-#pragma unroll
-    for (int m = 0; m < TAPS; ++m) cc2[m] = make_float2(coef_s[m * NP + Ep], coef_s[m * NP + Ep]);
-    // byte offset of E_p in a row (FP32 pair, or a packed FP16 pair)
-    const int e_off = E16 ? Ep * 4 : Ep * 8;
-
-    // Farrow rows of group gi of stage kst (npairs pairs in the stage) into buffer b
-    auto expand = [&](int kst, int gi, int npairs, int b) {
-        const int s = kst % NSTAGE;
-        const float* rc = rec + s * PAIRS * NREC;
-        unsigned char* eb = ebuf + b * GROUP * ebuf_pair;
-        const int ng = min(GROUP, npairs - gi * GROUP);
-        const int total = ng * runs_per_pair;
-        for (int run = Erun; run < total; run += NRUNSLOT) {
-            const int j = run / runs_per_pair;
-            const int pos0 = (run - j * runs_per_pair) * RUN;
-            const int pr = gi * GROUP + j;
-            const unsigned char* slot = seg + ((size_t)s * PAIRS + pr) * p.slot_bytes;
-            const int off = __float_as_int(rc[pr * NREC + F_OFF]) + pos0;
-            const float sc = E16 ? 1.0f : rc[pr * NREC + F_SCALE];
-            float2 w[RUN + TAPS - 1];
-#pragma unroll
-            for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
-            unsigned char* dst = eb + j * ebuf_pair + pos0 * EROW + e_off;
-#pragma unroll
-            for (int kq = 0; kq < RUN; ++kq) {
-                float2 e = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
-                if (E16)
-                    *reinterpret_cast<__half2*>(dst + kq * EROW) = __floats2half2_rn(e.x, e.y);
-                else
-                    *reinterpret_cast<float2*>(dst + kq * EROW) = e;
-            }
-        }
-    };
-
-    // consumer copy of a stage's records (read by uniform 16-byte loads; the
-    // producer's ring slot is recycled as soon as the stage's expansions are done)
-    auto hold_records = [&](int kst) {
-        constexpr int NQ = MOTION ? HROW / 4 : 6;      // float4 per record the consumers read
-        const float4* rc = reinterpret_cast<const float4*>(rec + (kst % NSTAGE) * PAIRS * NREC);
-        float4* hd = reinterpret_cast<float4*>(hold + (kst & 1) * PAIRS * HROW);
-        for (int t = ct; t < PAIRS * NQ; t += NCONS) {
-            const int pr = t / NQ, qd = t - pr * NQ;
-            hd[pr * (HROW / 4) + qd] = rc[pr * (NREC / 4) + qd];
-        }
-    };
-
-    auto release = [&](int kst) {
+    auto warp_arrive = [&](uint64_t* bar) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars[NSTAGE + kst % NSTAGE]));
-    };
-
-    auto wait_stage = [&](int kst) -> bool {
-        const bool ok = mbar_wait_bounded(smem_u32(&bars[kst % NSTAGE]), (kst / NSTAGE) & 1, p.wait_ns);
-        if (!ok) {
-            *abort_flag = 1;
-            atomicOr(p.status, DEV_TIMEOUT);
-        }
-        return ok;
+        if (lane == 0) mbar_arrive(smem_u32(bar));
     };
 
     // gradient: fold the transmitter term of the finished ping into the
@@ -629,20 +648,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
         named_bar_sync(BAR_CONS, NCONS);
         (void)tNT;
-    };
-
-    // Farrow buffer handoff between consumer warps: efull[b] completes when all
-    // warps wrote their share of the rows of buffer b, eempty[b] when all warps
-    // finished reading it; warps may drift apart by one group.
-    auto warp_arrive = [&](uint64_t* bar) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(bar));
-    };
-    auto wait_bar = [&](uint64_t* bar, uint32_t parity) {
-        if (!mbar_wait_bounded(smem_u32(bar), parity, p.wait_ns)) {
-            *abort_flag = 1;
-            atomicOr(p.status, DEV_TIMEOUT);
-        }
     };
 
     // per-pixel work of one pair; MASKED: apply the beam test per pixel.  The
@@ -782,64 +787,28 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
     };
 
-    // ---- walk the stages group by group, expanding one group ahead
+    // ---- the groups in the order the producer emits them
     bool aborted = false;
-    int kc = 0, gi = 0, nkc = 0, lastkc = 1;
-    if (wait_stage(0)) {
-        nkc = st_count[0];
-        lastkc = st_last[0];
-        if (nkc > 0) {
-            hold_records(0);
-            expand(0, 0, nkc, 0);
-            if ((nkc + GROUP - 1) / GROUP == 1) release(0);
-        }
-    }
-    warp_arrive(&ebar[0]);
-    aborted = *abort_flag != 0;
     int prev_ping = -1;
     int seq_ping = ping0, seq_ch = 0;               // candidate order (no culling)
-    for (int G = 0; !aborted && nkc > 0; ++G) {
-        // the group after (kc, gi)
-        int kn = kc, gn = gi + 1, nkn = nkc, lastkn = lastkc;
-        bool have_next = true;
-        if (gn * GROUP >= nkc) {
-            if (lastkc) {
-                have_next = false;
-            } else {
-                kn = kc + 1;
-                gn = 0;
-                if (!wait_stage(kn)) {
-                    have_next = false;
-                } else {
-                    nkn = st_count[kn % NSTAGE];
-                    lastkn = st_last[kn % NSTAGE];
-                    have_next = nkn > 0;
-                }
-            }
+    for (int G = 0;; ++G) {
+        const int b = G % NBUF;
+        if (!mbar_wait_bounded(smem_u32(&efull[b]), (G / NBUF) & 1, p.wait_ns)) {
+            *abort_flag = 1;
+            atomicOr(p.status, DEV_TIMEOUT);
         }
-        if (have_next) {
-            if (G >= 1) wait_bar(&ebar[2 + ((G + 1) & 1)], ((G - 1) >> 1) & 1);   // readers of group G-1 done
-            if (!*abort_flag) {
-                // a new stage's records go to the hold buffer of stage kn - 2,
-                // whose last reader finished with group G - 1 at the latest
-                if (gn == 0) hold_records(kn);
-                expand(kn, gn, nkn, (G + 1) & 1);
-                if ((gn + 1) * GROUP >= nkn) release(kn);
-            }
-            warp_arrive(&ebar[(G + 1) & 1]);
-        }
-        wait_bar(&ebar[G & 1], (G >> 1) & 1);                  // rows of group G complete
         if (*abort_flag) {
             aborted = true;
             break;
         }
-        const float4* hq = reinterpret_cast<const float4*>(hold + (kc & 1) * PAIRS * HROW);
-        const unsigned char* eb = ebuf + (G & 1) * GROUP * ebuf_pair;
-        const int ng = min(GROUP, nkc - gi * GROUP);
+        const int4 d = gdesc[b];
+        const int rs = d.x, pr0 = d.y, ng = d.z, gflags = d.w;
+        const float4* hq = reinterpret_cast<const float4*>(rec + rs * PAIRS * NREC);
+        const unsigned char* eb = ebuf + (size_t)b * GROUP * ebuf_pair;
 #pragma unroll 1
         for (int j = 0; j < ng; ++j) {
-            const int pr = gi * GROUP + j;
-            const float4* hr = hq + pr * (HROW / 4);
+            const int pr = pr0 + j;
+            const float4* hr = hq + pr * (NREC / 4);
             // without culling the pairs arrive in candidate order, so the ping
             // is tracked here; with culling it comes from the record
             int ping, flags = FL_TX_FULL | FL_RX_FULL;
@@ -897,12 +866,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 pixels(std::integral_constant<bool, BEAM>{}, q0, q1, rot, (flags & FL_RX_FULL) ? 0u : 1u, erow, q6,
                        q7);
         }
-        warp_arrive(&ebar[2 + (G & 1)]);
-        if (!have_next) break;
-        kc = kn;
-        gi = gn;
-        nkc = nkn;
-        lastkc = lastkn;
+        warp_arrive(&eempty[b]);
+        if (gflags & GD_STAGE_END) warp_arrive(&rempty[rs]);
+        if (gflags & GD_LAST) break;
     }
     if (aborted) return;
     if constexpr (MODE == MODE_OFFSET_GRAD) {
