@@ -65,6 +65,7 @@ def lib():
             L.oracle_backproject_adjoint.argtypes = [I, I, P, P, D, D, D, D, I, I, D, Lg, P, P, P, P, D, I, P, I]
             L.oracle_vjp_offsets.argtypes = [I, I, P, P, D, D, D, D, I, P, I, D, Lg, P, P, P, P, D, I, P, I]
             L.oracle_delay_eval.argtypes = [P, P, P, P, D, P]
+            L.oracle_set_medium.argtypes = [D, D]
             L.oracle_sharpness.argtypes = [Lg, P, P, P]
             L.oracle_lfm_compressed_pulse.argtypes = [D, D, D]
             L.oracle_lfm_compressed_pulse.restype = D
@@ -169,6 +170,23 @@ def _echo_c128(echo) -> np.ndarray:
 
 def _vel(vel, P):
     return None if vel is None else _p(_f64(vel).reshape(P, 3))
+
+
+class medium:
+    """Context manager: the sediment-water interface at depth z_interface
+    (NED z) with sediment sound speed c_sediment for every oracle call inside
+    (refraction model; stop-and-hop delays only)."""
+
+    def __init__(self, z_interface: float, c_sediment: float):
+        self.z, self.c = float(z_interface), float(c_sediment)
+
+    def __enter__(self):
+        lib().oracle_set_medium(self.z, self.c)
+        return self
+
+    def __exit__(self, *exc):
+        lib().oracle_set_medium(0.0, 0.0)
+        return False
 
 
 def delay(x, t, r, v, c):

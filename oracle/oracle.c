@@ -189,6 +189,60 @@ typedef struct {
     double kappa;            /* c / (c + ur . v): dtau/d(dp) = -(ut + ur) kappa / c */
 } oracle_delay;
 
+/* Sediment-water interface (Sec. III-B: a refraction model in the
+ * propagation time for sub-bottom imaging).  This build's reading: a flat
+ * interface at z = g_zint (NED, z down), water above with the signal's sound
+ * speed c, sediment below with speed g_csed.  A leg from a sensor s in the
+ * water to a point x below the interface crosses it at the point P that
+ * makes the travel time |P - s|/c + |x - P|/c_sed stationary (Fermat), so
+ * its length in water metres is L = |P - s| + (c/c_sed) |x - P|; legs to
+ * points at or above the interface, or from sensors at or below it, are
+ * straight.  g_csed <= 0 switches the model off (the default).  Set by
+ * oracle_set_medium; read by every delay evaluation.
+ * Pinned by: c_sed = c gives the straight leg; a vertical leg has the
+ * closed form a + (c/c_sed) b; the bisection root against a bounded scalar
+ * minimiser of L (scipy); a point below the interface focuses to A P C only
+ * with the model.                                                          */
+static double g_zint = 0.0, g_csed = 0.0;
+
+void oracle_set_medium(double z_interface, double c_sediment) {
+    g_zint = z_interface;
+    g_csed = c_sediment;
+}
+
+/* One leg sensor s -> point x: length in water metres and the unit vector
+ * of its water part (from s; dL/ds = -u).                                  */
+static double leg_eval(const double* x, const double* s, double c, double* u) {
+    const double d0 = x[0] - s[0], d1 = x[1] - s[1], d2 = x[2] - s[2];
+    if (!(g_csed > 0.0) || x[2] <= g_zint || s[2] >= g_zint) {
+        const double L = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        u[0] = d0 / L;
+        u[1] = d1 / L;
+        u[2] = d2 / L;
+        return L;
+    }
+    const double n = c / g_csed;
+    const double a = g_zint - s[2], b = x[2] - g_zint;
+    const double rho = sqrt(d0 * d0 + d1 * d1);
+    /* horizontal distance xi of the crossing point from s: the root of
+     * xi / sqrt(xi^2 + a^2) - n (rho - xi) / sqrt((rho - xi)^2 + b^2), which
+     * increases from <= 0 at xi = 0 to >= 0 at xi = rho (bisection)        */
+    double lo = 0.0, hi = rho;
+    for (int it = 0; it < 200 && hi - lo > 1e-16 * (rho + a + b); ++it) {
+        const double m = 0.5 * (lo + hi);
+        const double f = m / sqrt(m * m + a * a) - n * (rho - m) / sqrt((rho - m) * (rho - m) + b * b);
+        if (f > 0.0) hi = m;
+        else lo = m;
+    }
+    const double xi = 0.5 * (lo + hi);
+    const double w0 = rho > 0.0 ? xi * d0 / rho : 0.0, w1 = rho > 0.0 ? xi * d1 / rho : 0.0, w2 = a;
+    const double lw = sqrt(w0 * w0 + w1 * w1 + w2 * w2);
+    u[0] = w0 / lw;
+    u[1] = w1 / lw;
+    u[2] = w2 / lw;
+    return lw + n * sqrt((rho - xi) * (rho - xi) + b * b);
+}
+
 /* Two-way delay of pixel x for transmitter t and receiver r (Sec. II-A).
  * v == NULL: stop-and-hop, tau = (|x - t| + |x - r|) / c.
  * v != NULL: the transmitter sends at time 0 from t and the receiver moves
@@ -203,10 +257,25 @@ static void delay_eval(const double* x, const double* t, const double* r, const 
         dt[a] = x[a] - t[a];
         dr[a] = x[a] - r[a];
     }
+    o->kappa = 1.0;
+    if (g_csed > 0.0) {
+        /* refraction model (stop-and-hop only) */
+        if (v) {
+            o->tau = 0.0 / 0.0;
+            return;
+        }
+        o->rt = leg_eval(x, t, c, o->ut);
+        o->rr = leg_eval(x, r, c, o->ur);
+        o->tau = (o->rt + o->rr) / c;
+        o->u = (o->tau - t0) * fs;
+        const double fl0 = floor(o->u);
+        o->j0 = (long)fl0;
+        o->f = o->u - fl0;
+        return;
+    }
     o->rt = sqrt(dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2]);
     o->rr = sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
     o->tau = (o->rt + o->rr) / c;
-    o->kappa = 1.0;
     if (v) {
         for (int it = 0; it < 100; ++it) {
             double w[3];
