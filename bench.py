@@ -65,6 +65,9 @@ def parse():
                     help="receivers move during reception (per-ping velocity), not stop-and-hop")
     ap.add_argument("--beam-deg", type=float, default=0.0,
                     help="azimuth beam width [deg] (ray culling on); 0 = omnidirectional")
+    ap.add_argument("--refraction", type=float, default=0.0, metavar="C_SEDIMENT",
+                    help="seabed refraction: sediment sound speed [m/s] below the interface z = 0 (the "
+                         "workloads' seafloor); 0 = straight paths")
     return ap.parse_args()
 
 
@@ -204,7 +207,9 @@ def config_of(w, args):
             "pixels": "%dx%dx%d" % (g.nx, g.ny, g.nz), "pixel_m": g.dx, "taps": 8,
             "interp": "kaiser_sinc beta=%g (Farrow degree 5)" % BETA, "echo": args.echo,
             "updates_per_step": w.updates, "l2": l2_note(w, args), "parallelism": "replicas",
-            "delay_model": "receiver moving during reception" if args.motion else "stop-and-hop",
+            "delay_model": ("receiver moving during reception" if args.motion else "stop-and-hop") +
+                           (", seabed refraction (interface z = 0, c_sediment = %g m/s)" % args.refraction
+                            if args.refraction > 0 else ""),
             **({"beam_deg": args.beam_deg,
                 "beam_note": "value counts every pixel.ping.channel term of the image, culled ones included; "
                              "roofline.achieved counts the updates of the computed (not culled) blocks"}
@@ -234,6 +239,8 @@ def run_ours(args, rank, world, local_rank):
         geom.set_beam(np.deg2rad(args.beam_deg), 1)
     if args.motion:
         geom.set_velocity(nav["vel"])
+    if args.refraction > 0:
+        geom.set_refraction(0.0, args.refraction)
     grid = sas.grid_from(w.grid)
     interp = sas.kaiser(BETA)
     image = torch.empty((w.grid.nz, w.grid.ny, w.grid.nx), dtype=torch.complex64, device=dev)
@@ -290,7 +297,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = work / (statistics.mean(launch_ms) / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
             "traffic": (TRAFFIC_BYTES.get((w.name, args.echo))
-                        if args.beam_deg <= 0 and not args.pings and not args.motion else None),
+                        if args.beam_deg <= 0 and not args.pings and not args.motion and args.refraction <= 0
+                        else None),
             "peak_basis": "%d SMs x %.0f MHz x %.0f updates/clk/SM (FP32 128 lanes / 32 ops, SFU 16 lanes / 4 ops)"
                           % (props.multi_processor_count, sm_max, UPDATES_PER_CLK_PER_SM)}
     if clk.get("sm_mhz"):

@@ -161,6 +161,21 @@ int sas_geometry_set_beam(sas_geometry_t h, double beam_width, int side);
  * SAS_ERR_CUDA. */
 int sas_geometry_set_velocity(sas_geometry_t h, const double* vel, int on_device, void* cuda_stream);
 
+/* Refraction at the seabed (Sec. III-B: imaging below the seafloor needs a
+ * refraction model in the propagation time).  A flat interface z = z_interface
+ * (NED, metres) with water above (the signal's sound speed c) and sediment
+ * below (sound speed c_sediment, m/s).  A leg from a sensor above the
+ * interface to a pixel strictly below it (z > z_interface) crosses the
+ * interface where its travel time is stationary (Fermat; Snell's law) and
+ * counts L = |P - s| + (c / c_sediment) |x - P| water metres; every other leg
+ * is straight.  Applies to the forward backprojection (2D and 3D) of every
+ * later call; c_sediment <= 0 switches the model off (the default).  The
+ * adjoint, the offset gradient and the simulator return SAS_ERR_UNSUPPORTED
+ * while it is on, and so does a backprojection that also has a velocity
+ * (sas_geometry_set_velocity) or a beam (sas_geometry_set_beam).
+ * Errors: SAS_ERR_ARG (null handle, non-finite arguments). */
+int sas_geometry_set_refraction(sas_geometry_t h, double z_interface, double c_sediment);
+
 /* Copies the current sensor positions to device arrays d_tx [P][3] and
  * d_rx [P][C][3] (FP64).  Either may be NULL. */
 int sas_geometry_positions(sas_geometry_t h, double* d_tx, double* d_rx, void* cuda_stream);

@@ -39,7 +39,7 @@ SAS_MLP_NPARAMS = 4808
 
 ENTRY_POINTS = [
     "sas_version", "sas_last_error", "sas_geometry_create", "sas_geometry_set_offsets", "sas_geometry_set_beam",
-    "sas_geometry_set_velocity",
+    "sas_geometry_set_velocity", "sas_geometry_set_refraction",
     "sas_geometry_positions", "sas_geometry_destroy", "sas_echo_upload", "sas_echo_download",
     "sas_backproject_2d", "sas_backproject_3d", "sas_backproject_adjoint", "sas_sharpness",
     "sas_sharpness_static", "sas_simulate_points",
@@ -100,6 +100,7 @@ def lib():
                 "sas_geometry_set_offsets": ([V, V, I, V], I),
                 "sas_geometry_set_beam": ([V, D, I], I),
                 "sas_geometry_set_velocity": ([V, V, I, V], I),
+                "sas_geometry_set_refraction": ([V, D, D], I),
                 "sas_geometry_positions": ([V, V, V, V], I),
                 "sas_geometry_destroy": ([V], I),
                 "sas_echo_upload": ([V, V, I, I, V], I),
@@ -182,6 +183,10 @@ def sas_geometry_set_offsets(h, offsets, on_device: int, stream=None):
 
 def sas_geometry_set_velocity(h, vel, on_device: int, stream=None):
     _check(lib().sas_geometry_set_velocity(h, _ptr(vel), on_device, _stream(stream)))
+
+
+def sas_geometry_set_refraction(h, z_interface: float, c_sediment: float):
+    _check(lib().sas_geometry_set_refraction(h, float(z_interface), float(c_sediment)))
 
 
 def sas_geometry_set_beam(h, beam_width: float, side: int = 1):
@@ -369,6 +374,11 @@ class Geometry:
             sas_geometry_set_velocity(self.h, vel.contiguous(), 1, stream)
         else:
             sas_geometry_set_velocity(self.h, np.ascontiguousarray(vel, dtype=np.float64), 0, stream)
+
+    def set_refraction(self, z_interface: float, c_sediment: float):
+        """Seabed refraction: flat interface at z_interface, sediment sound
+        speed c_sediment [m/s] (<= 0 = off)."""
+        sas_geometry_set_refraction(self.h, z_interface, c_sediment)
 
     def set_beam(self, beam_width: float, side: int = 1):
         """Beam field of view of full azimuth width beam_width [rad] (0 = off)."""

@@ -454,6 +454,16 @@ extern "C" int sas_geometry_set_beam(sas_geometry_t h, double beam_width, int si
     return SAS_OK;
 }
 
+extern "C" int sas_geometry_set_refraction(sas_geometry_t h, double z_interface, double c_sediment) {
+    if (!h || !std::isfinite(z_interface) || !std::isfinite(c_sediment)) {
+        set_error("sas_geometry_set_refraction: need a handle and finite arguments");
+        return SAS_ERR_ARG;
+    }
+    h->z_int = z_interface;
+    h->c_sed = c_sediment > 0.0 ? c_sediment : 0.0;
+    return SAS_OK;
+}
+
 extern "C" int sas_geometry_set_velocity(sas_geometry_t h, const double* vel, int on_device, void* stream) {
     if (!h) {
         set_error("null handle");
@@ -629,6 +639,10 @@ static int backproject(sas_geometry_t h, const sas_grid* g, const sas_interp* it
         set_error("backproject: no echo uploaded");
         return SAS_ERR_STATE;
     }
+    if (h->c_sed > 0.0 && (h->has_vel || h->beam_tan > 0.0)) {
+        set_error("backproject: the refraction model does not combine with receiver motion or a beam");
+        return SAS_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     rc = handle_fit(h, it, st);
     if (rc != SAS_OK) return rc;
@@ -655,6 +669,10 @@ extern "C" int sas_backproject_adjoint(sas_geometry_t h, const sas_grid* g, cons
     }
     int rc = check_grid(g, g && g->nz > 1);
     if (rc != SAS_OK) return rc;
+    if (h->c_sed > 0.0) {
+        set_error("sas_backproject_adjoint: not available with the refraction model");
+        return SAS_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (d_grad_offsets && h->echo_dtype < 0) {
         set_error("sas_backproject_adjoint: the offset gradient needs an uploaded echo");

@@ -165,6 +165,9 @@ struct sas_geometry_s {
     int has_vel;       // 0: stop-and-hop
     double beam_tan;   // tan(beam width / 2); <= 0: no beam field of view
     int beam_side;     // +1 starboard, -1 port
+    // seabed refraction (forward backprojection): interface depth, sediment sound speed (<= 0: off)
+    double z_int;
+    double c_sed;
     uint32_t* d_status;
     unsigned long long* d_cull;   // [4] ray-culling counts (candidate, computed, beam edge, -)
     sas::FarrowCoef* d_coef;

@@ -82,6 +82,10 @@ extern "C" int sas_simulate_points(sas_geometry_t h, const double* d_scat, int64
         set_error("sas_simulate_points: bad argument");
         return SAS_ERR_ARG;
     }
+    if (h->c_sed > 0.0) {
+        set_error("sas_simulate_points: not available with the refraction model");
+        return SAS_ERR_UNSUPPORTED;
+    }
     if (n == 0) return SAS_OK;
     const unsigned rows = (unsigned)((long long)h->P * h->C);
     simulate_points_kernel<<<rows, 256, 0, (cudaStream_t)stream>>>(

@@ -77,8 +77,17 @@ enum {
     F_C0X, F_C0Y, F_C0Z, F_C1X, F_C1Y, F_C1Z, F_PAD0, F_PAD1, F_VX, F_VY, F_VZ, F_RV, F_BRX, F_BRY, F_BRZ, F_PAD2,
     NREC
 };
-// pair flags: the whole tile lies inside the transmitter / receiver beam
-enum { FL_TX_FULL = 1, FL_RX_FULL = 2 };
+// pair flags: the whole tile lies inside the transmitter / receiver beam;
+// the transmitter / receiver leg refracts into the sediment for some pixel
+enum { FL_TX_FULL = 1, FL_RX_FULL = 2, FL_T_REFR = 4, FL_R_REFR = 8 };
+// With the seabed refraction model the record has two more blocks of RF_N
+// fields after the first sixteen (the receiver leg's, then the
+// transmitter leg's), in place of the beam and motion fields:
+// {a, rho_r^2, rho_r, xi_r}, {sigma_r, |W_r|, |V_r|, f_r}, {df/drho, df/db, K_r, K_s}
+// (see refr_leg_ref)
+enum { RF_A, RF_RHO2, RF_RHO, RF_XI, RF_SIG, RF_W, RF_V, RF_F, RF_DFR, RF_DFB, RF_KR, RF_KS, RF_N };
+enum { F_RREF = 16, F_TREF = F_RREF + RF_N, NREC_REFR = F_TREF + RF_N };
+static_assert(NREC_REFR % 4 == 0 && F_RREF % 4 == 0 && F_TREF % 4 == 0, "refraction blocks are float4-aligned");
 
 struct KParams {
     const double* tx;       // [P][3]
@@ -106,6 +115,12 @@ struct KParams {
     unsigned long long* cull;   // [3] candidate, computed, beam-edge (ping, channel, tile) blocks
     // receiver motion during reception: velocity [P][3] (m/s) or null (stop-and-hop)
     const double* vel;
+    // seabed refraction (forward pass): interface depth, n = c / c_s, and the
+    // constants of the crossing solve with r = max(n, 1/n): r^2, r^2 - 1,
+    // (r^2 - 1)^(-1/2); refr_tol: the crossing-point tolerance [m]
+    int refract, refr_fast_sed;    // refr_fast_sed: n < 1, the sediment is the faster medium
+    double z_int, refr_n;
+    float refr_nf, refr_r2, refr_M, refr_isM, refr_tol;
     float hx, hy, hz;       // half extents of a tile's pixel-centre box [m]
     int U, npos, npos_pad, seglen, seg_align, slot_bytes;
     int accumulate, atomic_out, skip_copies;
@@ -197,7 +212,10 @@ __device__ __forceinline__ PairGeo pair_geo(const KParams& p, double X0, double 
 // nearest integer gives floor(u)) and the carrier phase fc tau_ref mod 1
 // (cycles).
 // Returns the raw sample index of Farrow position 0, tap 0: floor(u_ref) - U - 3.
-__device__ __forceinline__ int pair_record(const KParams& p, PairGeo G, float* rc, int stride, const double* v) {
+// LT0, LR0 >= 0: leg lengths at x0 in water metres (seabed refraction) that
+// replace |R_T|, |R_R| in tau_ref; the differential fields stay the straight ones.
+__device__ __forceinline__ int pair_record(const KParams& p, PairGeo G, float* rc, int stride, const double* v,
+                                           double LT0 = -1.0, double LR0 = -1.0) {
     const double nT2 = G.Tx * G.Tx + G.Ty * G.Ty + G.Tz * G.Tz;
     const double nT = sqrt(nT2);
     if (v) {
@@ -227,7 +245,7 @@ __device__ __forceinline__ int pair_record(const KParams& p, PairGeo G, float* r
     }
     const double nR2 = G.Rx * G.Rx + G.Ry * G.Ry + G.Rz * G.Rz;
     const double nR = sqrt(nR2);
-    const double tau = (nT + nR) * p.inv_c;
+    const double tau = ((LT0 >= 0.0 ? LT0 : nT) + (LR0 >= 0.0 ? LR0 : nR)) * p.inv_c;
     double u = (tau - p.t0) * p.fs;
     u = fmin(fmax(u, -268435456.0), 268435456.0);  // keep sample coordinates in int range
     const double iref = floor(u);
@@ -282,6 +300,152 @@ __device__ __forceinline__ bool beam_sees(const KParams& p, float wx, float wy, 
     return by > 0.f && fabsf(bx) <= p.beam_tan * by;
 }
 
+// ---------------------------------------------------------------------------
+// Seabed refraction (Sec. III-B).  Interface z = z_int, water above (speed c),
+// sediment below (speed c_s), n = c / c_s.  A leg from a sensor at height
+// a = z_int - s_z > 0 above the interface to a pixel at depth b = x_z - z_int > 0
+// below it, at horizontal distance rho, crosses the interface at horizontal
+// distance xi from the sensor (Fermat: the travel time is stationary, which
+// is Snell's law) and has the length, in water metres,
+//   L = |W| + n |V|,  |W| = sqrt(xi^2 + a^2),  |V| = sqrt(sigma^2 + b^2),  sigma = rho - xi.
+// The crossing is solved in the slope v of the leg in the faster medium: with
+// r = max(n, 1/n), A the depth of the faster leg and B that of the slower one
+// (A = b, B = a for a faster sediment, n < 1), the faster leg runs A v and the
+// slower one B v q, q = (r^2 + (r^2 - 1) v^2)^(-1/2), so v solves
+//   F(v) = A v + B v q - rho = 0,   F'(v) = A + B r^2 q^3.
+// F increases and is concave on v >= 0; the slower leg runs less than
+// B / sqrt(r^2 - 1), so A v >= rho - B / sqrt(r^2 - 1) (and A v <= rho).
+// Newton's method from the left of the root increases monotonically to it.
+//
+// Each pair carries, per leg, the crossing at a reference point x_r below the
+// interface (the tile centre, or the deepest pixel layer when the centre is
+// above it); a pixel's leg is then evaluated as a difference from x_r with
+// the identity |U + e| - |U| = (2U.e + |e|^2) / (|U + e| + |U|) for each of
+// the two segments, where the crossing point only has to be close to the
+// stationary one (the length is stationary there: a crossing error e costs
+// L'' e^2 / 2).
+// ---------------------------------------------------------------------------
+
+// Crossing slope in the faster medium by Newton's method from the left bound
+// (FP32, producer).  Returns v; q and Sd = B r^2 q^3 at v.
+__device__ __forceinline__ float refr_solve(const KParams& p, float A, float B, float rho, float& q, float& Sd) {
+    const float flo = fmaxf(fmaf(-B, p.refr_isM, rho), 0.f);
+    const float vlo = flo / A;
+    float v = vlo, prev = 3.0e38f;
+    for (int it = 0; it < 64; ++it) {
+        q = rsqrtf(fmaf(p.refr_M, v * v, p.refr_r2));
+        const float F = fmaf(A, v, fmaf(B * v, q, -rho));
+        Sd = B * p.refr_r2 * (q * q * q);
+        const float dv = F / (Sd + A);
+        v = fmaxf(v - dv, vlo);
+        // stop at convergence, or when rounding stops the steps from shrinking
+        const float step = fabsf(dv) * fmaxf(A, Sd);
+        if (step <= 2e-7f * (rho + B) || step >= prev) break;
+        prev = step;
+    }
+    q = rsqrtf(fmaf(p.refr_M, v * v, p.refr_r2));
+    Sd = B * p.refr_r2 * (q * q * q);
+    return v;
+}
+
+// Reference terms of one leg (producer): hx, hy = horizontal part of x_r - s,
+// a = sensor height above the interface, br = depth of x_r below it (FP64).
+// Writes rc[RF_A .. RF_DFB] (stride) and returns L(x_r) in water metres.  The
+// crossing xi_r is solved in FP32 and L(x_r), sigma_r, |W_r|, |V_r| are then
+// evaluated in FP64 at exactly that crossing, so that the per-pixel
+// differences start from a consistent reference.  f_r is the faster leg's
+// run and df/drho, df/db its derivatives (implicit function of F = 0): the
+// per-pixel initial guess.
+__device__ __forceinline__ double refr_leg_ref(const KParams& p, double hx, double hy, double a, double br,
+                                               float* rc, int stride) {
+    const double rho2 = hx * hx + hy * hy;
+    const double rho = sqrt(rho2);
+    const bool fsed = p.refr_fast_sed;
+    const float A = (float)(fsed ? br : a), B = (float)(fsed ? a : br);
+    const float rhof = (float)rho;
+    float q, Sd;
+    const float v = refr_solve(p, A, B, rhof, q, Sd);
+    const float fast = A * v, slow = (B * v) * q;
+    // the crossing from the better-determined of the two runs
+    float xi_f = fsed ? (A < Sd ? rhof - fast : slow) : (A < Sd ? fast : rhof - slow);
+    xi_f = fminf(fmaxf(xi_f, 0.f), rhof);
+    const double xi = (double)xi_f, sig = rho - xi;
+    const double W = sqrt(xi * xi + a * a), V = sqrt(sig * sig + br * br);
+    const float Fd = Sd + A;
+    rc[RF_A * stride] = (float)a;
+    rc[RF_RHO2 * stride] = (float)rho2;
+    rc[RF_RHO * stride] = rhof;
+    rc[RF_XI * stride] = xi_f;
+    rc[RF_SIG * stride] = (float)sig;
+    rc[RF_W * stride] = (float)W;
+    rc[RF_V * stride] = (float)V;
+    rc[RF_F * stride] = fsed ? (float)sig : xi_f;
+    rc[RF_DFR * stride] = A / Fd;
+    rc[RF_DFB * stride] = fsed ? v * (1.f - A / Fd) : -(A * v) * q / Fd;
+    return W + p.refr_n * V;
+}
+
+// Refracted leg of one pixel minus the leg at x_r, plus K_r (consumers, FP32).
+// r0, r1, r2: the leg's record blocks; rho = rho_r + drho: the pixel's
+// horizontal distance; b = b_r + db: its depth below the interface.
+__device__ __forceinline__ float refr_leg_diff(const KParams& p, const float4 r0, const float4 r1, const float4 r2,
+                                               float rho, float drho, float b, float db, float br) {
+    const float a = r0.x;
+    const bool fsed = p.refr_fast_sed;
+    const float A = fsed ? b : a, B = fsed ? a : b;
+    const float flo = fmaxf(fmaf(-B, p.refr_isM, rho), 0.f);
+    float f = fmaf(r2.x, drho, fmaf(r2.y, db, r1.w));   // predicted run of the faster leg
+    f = fminf(fmaxf(f, flo), rho);
+    const float iA = rcp_sfu(A);
+    const float vlo = flo * iA;
+    float v = f * iA, Sd = 0.f;
+    for (int it = 0; it < 16; ++it) {
+        const float q = rsqrt_sfu(fmaf(p.refr_M, v * v, p.refr_r2));
+        const float F = fmaf(A, v, fmaf(B * v, q, -rho));
+        Sd = B * p.refr_r2 * (q * q * q);
+        const float dv = F * rcp_sfu(Sd + A);
+        v = fmaxf(v - dv, vlo);
+        // the crossing moved by less than the tolerance
+        if (fabsf(dv) * fminf(A, Sd) < p.refr_tol) break;
+    }
+    const float q = rsqrt_sfu(fmaf(p.refr_M, v * v, p.refr_r2));
+    const float fast = A * v, slow = (B * v) * q;
+    const bool use_fast = A < Sd;
+    float dxi, dsig;
+    if (fsed) {   // faster leg in the sediment: its run is sigma
+        dsig = use_fast ? fast - r1.x : drho - (slow - r0.w);
+        dxi = drho - dsig;
+    } else {      // faster leg in the water: its run is xi
+        dxi = use_fast ? fast - r0.w : drho - (slow - r1.x);
+        dsig = drho - dxi;
+    }
+    const float xi = r0.w + dxi, sg = r1.x + dsig;
+    const float W2 = fmaf(xi, xi, a * a), V2 = fmaf(sg, sg, b * b);
+    const float Dw = fmaf(W2, rsqrt_sfu(W2), r1.y), Ds = fmaf(V2, rsqrt_sfu(V2), r1.z);   // |W| + |W_r|, |V| + |V_r|
+    const float Nw = dxi * fmaf(2.f, r0.w, dxi);                                         // |W|^2 - |W_r|^2
+    const float Ns = p.refr_nf * fmaf(dsig, fmaf(2.f, r1.x, dsig), db * (br + b));        // n (|V|^2 - |V_r|^2)
+    return fmaf(fmaf(Nw, Ds, Ns * Dw), rcp_sfu(Dw * Ds), r2.z);
+}
+
+// Horizontal distance of a pixel from a sensor, rho = rho_r + drho, from
+// qh = 2 h_r.d_h + |d_h|^2 (h_r: horizontal part of x_r - s; d_h the
+// pixel's horizontal offset from x_r).
+// (A pixel straight below the sensor has rho = 0, which rounding may take
+// slightly negative: clamped.)
+__device__ __forceinline__ void refr_rho(const float4 r0, float qh, float& rho, float& drho) {
+    const float rho2 = r0.y + qh;
+    rho = rho2 > 0.f ? rho2 * rsqrt_sfu(rho2) : 0.f;
+    const float den = rho + r0.z;
+    drho = den > 0.f ? qh * rcp_sfu(den) : 0.f;
+}
+
+// Depth of pixel layer iz, formed as the oracle forms pixel coordinates
+// (z0 + iz dz, no fused multiply-add), so that both take the same decision at
+// the interface.
+__device__ __forceinline__ double layer_z(const KParams& p, int iz) {
+    return __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
+}
+
 // Pixel offsets d from the tile centre: the fixed part of |d|^2 and of 2R.d
 // (x, and y in 3D; the varying coordinate is added per slot as
 // a = fma(2R_var, d_var, fma(d_var, d_var, fixed_d2)) + fixed_dot).  Written
@@ -306,12 +470,13 @@ struct Layout {
 // Every part before the descriptors has a size that is a multiple of 16
 // bytes (slot_bytes: of 128; a Farrow row is 48 bytes; 32-float records),
 // so the 16-byte descriptor loads and stores are aligned.
-static_assert((NRS * PAIRS * NREC * 4) % 16 == 0 && (TAPS * NP * 4) % 16 == 0 && (NCW * 4 * 8) % 16 == 0,
+static_assert((NRS * PAIRS * NREC * 4) % 16 == 0 && (NRS * PAIRS * NREC_REFR * 4) % 16 == 0 &&
+                  (TAPS * NP * 4) % 16 == 0 && (NCW * 4 * 8) % 16 == 0,
               "shared-memory parts must keep 16-byte alignment");
-inline size_t smem_bytes(int slot_bytes, int npos_pad) {
+inline size_t smem_bytes(int slot_bytes, int npos_pad, int nrec = NREC) {
     return (size_t)NSEG * PAIRS * slot_bytes            // echo segments
            + (size_t)NBUF * GROUP * npos_pad * EROW     // Farrow rows
-           + (size_t)NRS * PAIRS * NREC * 4             // records
+           + (size_t)NRS * PAIRS * nrec * 4             // records
            + (size_t)TAPS * NP * 4                      // coefficients
            + (size_t)NCW * 4 * 8                        // cross-warp reduction (gradient)
            + (size_t)NBUF * 16                          // group descriptors
@@ -322,9 +487,12 @@ inline size_t smem_bytes(int slot_bytes, int npos_pad) {
 // BEAM: the beam field of view is on (culling in the producer, per-pixel tests
 // in tiles on a beam edge); without it every candidate pair is computed.
 // MOTION: the receivers move during reception (per-ping velocity).
-template <typename ET, bool DIM3, int MODE, bool BEAM, bool MOTION>
+// REFRACT: seabed refraction (forward pass, without BEAM and MOTION).
+template <typename ET, bool DIM3, int MODE, bool BEAM, bool MOTION, bool REFRACT = false>
 __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant__ CUtensorMap tmap, const KParams p) {
     using T = Tile<DIM3>;
+    static_assert(!REFRACT || (MODE == MODE_FORWARD && !BEAM && !MOTION), "refraction: forward pass only");
+    constexpr int KREC = REFRACT ? NREC_REFR : NREC;   // record fields
     // FP16 Farrow rows for 16-bit echoes in the forward pass
     constexpr bool E16 = (MODE == MODE_FORWARD) && (sizeof(ET) == 4);
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -334,8 +502,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     unsigned char* seg = smem;                                           // [NSEG][PAIRS] echo segments
     unsigned char* ebuf = seg + (size_t)NSEG * PAIRS * p.slot_bytes;     // [NBUF][GROUP] Farrow rows
     const int ebuf_pair = p.npos_pad * EROW;          // positions padded to whole expansion runs
-    float* rec = reinterpret_cast<float*>(ebuf + (size_t)NBUF * GROUP * ebuf_pair);   // [NRS][PAIRS][NREC]
-    float* coef_s = rec + NRS * PAIRS * NREC;                            // [TAPS][NP]
+    float* rec = reinterpret_cast<float*>(ebuf + (size_t)NBUF * GROUP * ebuf_pair);   // [NRS][PAIRS][KREC]
+    float* coef_s = rec + NRS * PAIRS * KREC;                            // [TAPS][NP]
     // every part so far has a size that is a multiple of 16 bytes (see smem_bytes)
     double* wred = reinterpret_cast<double*>(coef_s + TAPS * NP);         // [NCW][4]
     // [NBUF] group descriptors (written before, read after the efull barrier)
@@ -358,6 +526,24 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     const long long q0 = (long long)ping0 * p.C;
     const long long q1 = (long long)ping1 * p.C;
     const double cx = tx0 + 0.5 * (T::TX - 1), cy = ty0 + 0.5 * (T::TY - 1), cz = tz0 + 0.5 * (T::TZ - 1);
+    const double Zc = p.z0 + (DIM3 ? cz * p.dz : 0.0);   // tile centre depth
+    // seabed refraction: the slots (pixel layers in 3D; all of them in 2D)
+    // strictly below the interface, and the depth Zr of the reference point
+    // x_r = (x0, y0, Zr): the centre if it is below, else the deepest layer
+    unsigned bmask = 0u;
+    double Zr = Zc;
+    if constexpr (REFRACT) {
+        double zdeep = -1.0e300;
+#pragma unroll
+        for (int s = 0; s < PX; ++s) {
+            const double zs = DIM3 ? layer_z(p, tz0 + s) : p.z0;
+            if (zs > p.z_int) {
+                bmask |= 1u << s;
+                zdeep = fmax(zdeep, zs);
+            }
+        }
+        if (!(Zc > p.z_int)) Zr = zdeep;
+    }
 
     if (tid == 0) {
         for (int s = 0; s < NSEG; ++s) mbar_init(smem_u32(&full[s]), 1);
@@ -380,7 +566,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         // segment (announced on the stage's full barrier).  It fills stage k + 1
         // before it expands stage k, group by group, into the Farrow buffers the
         // consumers read; a descriptor per buffer tells them which pairs it holds.
-        const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = p.z0 + (DIM3 ? cz * p.dz : 0.0);
+        const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = Zc;
         const uint32_t seg_bytes = (uint32_t)p.seglen * (uint32_t)sizeof(ET);
         unsigned n_cand = 0, n_act = 0, n_edge = 0;   // this lane's culling counts
         bool failed = false;
@@ -446,15 +632,42 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 const int rank = __popc(amask & ((1u << lane) - 1u));
                 if (act && rank >= done && rank < done + take) {
                     const int slot = cnt + rank - done;
-                    float* rc = rec + (rs * PAIRS + slot) * NREC;
-                    const int base = pair_record(p, Gv, rc, 1, MOTION ? p.vel + 3 * (size_t)iv : nullptr);
+                    float* rc = rec + (rs * PAIRS + slot) * KREC;
+                    double LT0 = -1.0, LR0 = -1.0;
+                    int rfl = 0;
+                    if constexpr (REFRACT) {
+                        // per leg: crossing at x_r, and the offsets K_r, K_s of the refracted and the
+                        // straight slots from the leg at x0 (refracted if x0 is below the interface)
+#pragma unroll
+                        for (int leg = 0; leg < 2; ++leg) {
+                            const double hx = leg ? Gv.Tx : Gv.Rx, hy = leg ? Gv.Ty : Gv.Ry, hz = leg ? Gv.Tz : Gv.Rz;
+                            const double sz = leg ? p.tx[3 * (size_t)iv + 2] : p.rx[3 * (size_t)qv + 2];
+                            const double straight = sqrt(hx * hx + hy * hy + hz * hz);
+                            float* blk = rc + (leg ? F_TREF : F_RREF);
+                            double L0 = straight;
+                            if (bmask && sz < p.z_int) {
+                                const double Lr = refr_leg_ref(p, hx, hy, p.z_int - sz, Zr - p.z_int, blk, 1);
+                                if (Zc > p.z_int) L0 = Lr;
+                                blk[RF_KR] = (float)(Lr - L0);
+                                blk[RF_KS] = (float)(straight - L0);
+                                rfl |= leg ? FL_T_REFR : FL_R_REFR;
+                            } else {
+#pragma unroll
+                                for (int f = 0; f < RF_N; ++f) blk[f] = 0.f;
+                            }
+                            (leg ? LT0 : LR0) = L0;
+                        }
+                    }
+                    const int base = pair_record(p, Gv, rc, 1, MOTION ? p.vel + 3 * (size_t)iv : nullptr, LT0, LR0);
                     const int seg_start = base - (((base % p.seg_align) + p.seg_align) % p.seg_align);
                     rc[F_OFF] = __int_as_float(base - seg_start);
                     rc[F_SCALE] = p.scale ? p.scale[qv] : 1.0f;
                     rc[F_PING] = __int_as_float(iv);
-                    rc[F_FLAGS] = __int_as_float(flv);
+                    rc[F_FLAGS] = __int_as_float(REFRACT ? rfl : flv);
+                    if constexpr (!REFRACT) {
 #pragma unroll
-                    for (int t = 0; t < 6; ++t) rc[F_C0X + t] = rc6[t];
+                        for (int t = 0; t < 6; ++t) rc[F_C0X + t] = rc6[t];
+                    }
                     mbar_expect_tx(bar, seg_bytes);
                     if (!p.skip_copies)
                         tma_load_2d(smem_u32(seg + ((size_t)ss * PAIRS + slot) * p.slot_bytes), &tmap, seg_start,
@@ -482,7 +695,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             const int b = G % NBUF;
             if (G >= NBUF && !mbar_wait_bounded(smem_u32(&eempty[b]), ((G / NBUF) - 1) & 1, p.wait_ns)) fail();
             if (!failed && ng > 0) {
-                const float* rc = rec + rs * PAIRS * NREC;
+                const float* rc = rec + rs * PAIRS * KREC;
                 unsigned char* eb = ebuf + (size_t)b * GROUP * ebuf_pair;
                 const int total = ng * runs_per_pair;
                 for (int run = Erun; run < total; run += RSLOTS) {
@@ -490,8 +703,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     const int pos0 = (run - j * runs_per_pair) * RUN;
                     const int pr = pr0 + j;
                     const unsigned char* slot = seg + ((size_t)ss * PAIRS + pr) * p.slot_bytes;
-                    const int off = __float_as_int(rc[pr * NREC + F_OFF]) + pos0;
-                    const float sc = E16 ? 1.0f : rc[pr * NREC + F_SCALE];
+                    const int off = __float_as_int(rc[pr * KREC + F_OFF]) + pos0;
+                    const float sc = E16 ? 1.0f : rc[pr * KREC + F_SCALE];
                     float2 w[RUN + TAPS - 1];
 #pragma unroll
                     for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
@@ -596,6 +809,19 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     }
     float gacc0 = 0.f, gacc1 = 0.f, gacc2 = 0.f;   // gradient: receiver-side sum for the current ping
     uint32_t tmask = 0xffu;                         // pixels the current ping's transmitter sees
+    // seabed refraction: x_r's depth below the interface and offset from the
+    // tile centre; |d_h|^2 of this thread's column (3D)
+    float r_br = 0.f, r_zoff = 0.f, r_d2h = 0.f;
+    if constexpr (REFRACT) {
+        r_br = (float)(Zr - p.z_int);
+        r_zoff = (float)(Zr - Zc);
+        r_d2h = fixed_d2<true>(dxv, dyv_c);
+    }
+    // depth below the interface of slot s, and its offset from x_r's depth
+    auto slot_depth = [&](int s, float& b, float& db) {
+        db = DIM3 ? PXS(dvp, s) - r_zoff : 0.f;
+        b = fmaxf(r_br + db, 1e-7f);
+    };
 
     auto warp_arrive = [&](uint64_t* bar) {
         __syncwarp();
@@ -664,7 +890,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // D (1 - eps + eps^2) (neglected: eps^3 D ~ 1e-9 m and the curvature term
     // |v dtau|^2 / (2 |R|) ~ 2e-8 m).
     auto pixels = [&](auto masked, const float4 q0, const float4 q1, const float* rot, uint32_t rmask_needed,
-                      const unsigned char* erow, const float4 q6, const float4 q7) {
+                      const unsigned char* erow, const float4 q6, const float4 q7, const float4* hr, int rfl) {
         constexpr bool MASKED = decltype(masked)::value;
         const float tRx = q0.x, tRy = q0.y, tRz = q0.z, nR2 = q0.w;
         const float nR = q1.x, ufc = q1.y, phr = q1.z;
@@ -684,6 +910,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
         // ping-time receiver vector for the beam test
         const float bRx = MOTION ? q7.x : tRx, bRy = MOTION ? q7.y : tRy, bRz = MOTION ? q7.z : tRz;
+        // seabed refraction of the receiver leg: its record blocks and (3D) the
+        // column's horizontal distance from the receiver
+        const bool rrefr = REFRACT && (rfl & FL_R_REFR);
+        float4 rr0 = make_float4(0.f, 0.f, 0.f, 0.f), rr1 = rr0, rr2 = rr0;
+        float rhoR = 0.f, drhoR = 0.f;
+        if (REFRACT && rrefr) {
+            rr0 = hr[F_RREF / 4];
+            rr1 = hr[F_RREF / 4 + 1];
+            rr2 = hr[F_RREF / 4 + 2];
+            if (DIM3) refr_rho(rr0, X + r_d2h, rhoR, drhoR);
+        }
 #pragma unroll
         for (int k = 0; k < PX / 2; ++k) {
             const float2 a = fadd2(ffma2(tRvv, dvp[k], d2p[k]), Xv);       // 2 R.d + |d|^2
@@ -698,6 +935,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 const float2 eps = fmul2(ffma2(dvp[k], vvv, Kmv), rs);       // u_R . v / c
                 kap = ffma2(eps, fsub2(eps, one2), one2);                    // 1 / (1 + eps)
                 D = fmul2(D, kap);
+            }
+            if constexpr (REFRACT) {
+                if (rrefr) {
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int s = 2 * k + j;
+                        float& Dj = j ? D.y : D.x;
+                        if ((bmask >> s) & 1u) {
+                            if (!DIM3) refr_rho(rr0, j ? a.y : a.x, rhoR, drhoR);
+                            float b, db;
+                            slot_depth(s, b, db);
+                            Dj = refr_leg_diff(p, rr0, rr1, rr2, rhoR, drhoR, b, db, r_br) + PXS(dTp, s);
+                        } else {
+                            Dj += rr2.w;
+                        }
+                    }
+                }
             }
             const float2 v = ffma2(D, p.fs_c2, ufv);                      // u - 1/2, rel. to floor(u_ref)
             const float2 ph = ffma2(D, p.fc_c2, phv);                     // carrier phase [cycles]
@@ -803,16 +1057,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
         const int4 d = gdesc[b];
         const int rs = d.x, pr0 = d.y, ng = d.z, gflags = d.w;
-        const float4* hq = reinterpret_cast<const float4*>(rec + rs * PAIRS * NREC);
+        const float4* hq = reinterpret_cast<const float4*>(rec + rs * PAIRS * KREC);
         const unsigned char* eb = ebuf + (size_t)b * GROUP * ebuf_pair;
 #pragma unroll 1
         for (int j = 0; j < ng; ++j) {
             const int pr = pr0 + j;
-            const float4* hr = hq + pr * (NREC / 4);
+            const float4* hr = hq + pr * (KREC / 4);
             // without culling the pairs arrive in candidate order, so the ping
             // is tracked here; with culling it comes from the record
-            int ping, flags = FL_TX_FULL | FL_RX_FULL;
+            int ping, flags = FL_TX_FULL | FL_RX_FULL, rfl = 0;
             float4 q3;
+            if (REFRACT) {
+                q3 = hr[3];
+                rfl = __float_as_int(q3.z);
+            }
             if (BEAM) {
                 q3 = hr[3];
                 ping = __float_as_int(q3.y);
@@ -837,16 +1095,36 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 tT1 = q2.y;
                 tT2 = q2.z;
                 tNT2 = q2.w;
-                tNT = BEAM ? q3.x : hr[3].x;
+                tNT = (BEAM || REFRACT) ? q3.x : hr[3].x;
                 const float tTv = DIM3 ? tT2 : tT1;
                 const float X = fixed_dot<DIM3>(tT0, tT1, dxv, dyv_c);
                 tmask = 0xffu;
+                // seabed refraction of the transmitter leg
+                const bool trefr = REFRACT && (rfl & FL_T_REFR);
+                float4 tr0 = make_float4(0.f, 0.f, 0.f, 0.f), tr1 = tr0, tr2 = tr0;
+                float rhoT = 0.f, drhoT = 0.f;
+                if (REFRACT && trefr) {
+                    tr0 = hr[F_TREF / 4];
+                    tr1 = hr[F_TREF / 4 + 1];
+                    tr2 = hr[F_TREF / 4 + 2];
+                    if (DIM3) refr_rho(tr0, X + r_d2h, rhoT, drhoT);
+                }
 #pragma unroll
                 for (int s = 0; s < PX; ++s) {
                     const float a = __fadd_rn(fmaf(tTv, PXS(dvp, s), PXS(d2p, s)), X);
                     const float sm = tNT2 + a;
                     const float den = fmaf(sm, rsqrt_sfu(sm), tNT);
                     PXS(dTp, s) = a * rcp_sfu(den);
+                    if (REFRACT && trefr) {
+                        if ((bmask >> s) & 1u) {
+                            if (!DIM3) refr_rho(tr0, a, rhoT, drhoT);
+                            float b, db;
+                            slot_depth(s, b, db);
+                            PXS(dTp, s) = refr_leg_diff(p, tr0, tr1, tr2, rhoT, drhoT, b, db, r_br);
+                        } else {
+                            PXS(dTp, s) += tr2.w;
+                        }
+                    }
                     if (BEAM && !(flags & FL_TX_FULL)) {
                         const float dvs = PXS(dvp, s);
                         const float wx = fmaf(0.5f, tT0, dxv);
@@ -861,10 +1139,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             const float4 q7 = (MOTION && BEAM) ? hr[7] : make_float4(0.f, 0.f, 0.f, 0.f);
             const unsigned char* erow = eb + j * ebuf_pair;
             if (!BEAM || (flags & (FL_TX_FULL | FL_RX_FULL)) == (FL_TX_FULL | FL_RX_FULL))
-                pixels(std::integral_constant<bool, false>{}, q0, q1, rot, 0u, erow, q6, q7);
+                pixels(std::integral_constant<bool, false>{}, q0, q1, rot, 0u, erow, q6, q7, hr, rfl);
             else
                 pixels(std::integral_constant<bool, BEAM>{}, q0, q1, rot, (flags & FL_RX_FULL) ? 0u : 1u, erow, q6,
-                       q7);
+                       q7, hr, rfl);
         }
         warp_arrive(&eempty[b]);
         if (gflags & GD_STAGE_END) warp_arrive(&rempty[rs]);

@@ -17,7 +17,11 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     const double hx = 0.5 * (TXs - 1) * std::fabs(g.dx), hy = 0.5 * (TYs - 1) * std::fabs(g.dy),
                  hz = 0.5 * (TZs - 1) * std::fabs(dz);
     const double dmax = std::sqrt(hx * hx + hy * hy + hz * hz);
-    const int U = (int)std::ceil(2.0 * dmax * h->sig.fs / h->sig.c) + 2;
+    // with seabed refraction a leg's length in water metres is Lipschitz with
+    // constant max(1, n), n = c / c_s (a straight segment costs at most that much)
+    const bool refract = h->c_sed > 0.0;
+    const double n_refr = refract ? h->sig.c / h->c_sed : 1.0;
+    const int U = (int)std::ceil(2.0 * std::max(1.0, n_refr) * dmax * h->sig.fs / h->sig.c) + 2;
     const int elem = (h->echo_dtype == SAS_ECHO_C32_F16 || h->echo_dtype == SAS_ECHO_C32_BF16) ? 4 : 8;
     const int align = 16 / elem;
     const int npos = 2 * U + 1;
@@ -30,7 +34,7 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     const int npos_pad = (npos + RUN - 1) / RUN * RUN;
     // expansion runs read up to RUN + 7 samples past a run start: pad the slot
     const int slot_bytes = ((seglen + RUN + 8) * elem + 127) / 128 * 128;
-    const size_t smem = smem_bytes(slot_bytes, npos_pad);
+    const size_t smem = smem_bytes(slot_bytes, npos_pad, refract ? NREC_REFR : NREC);
     if (smem > 227 * 1024) {
         set_error("shared memory need %zu exceeds the per-block limit", smem);
         return SAS_ERR_UNSUPPORTED;
@@ -64,6 +68,19 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     prm.beam_side = (float)h->beam_side;
     prm.cull = h->d_cull;
     prm.vel = h->has_vel ? h->d_vel : nullptr;
+    prm.refract = refract;
+    if (refract) {
+        const double r = std::max(n_refr, 1.0 / n_refr), M = r * r - 1.0;
+        prm.refr_fast_sed = n_refr < 1.0;
+        prm.z_int = h->z_int;
+        prm.refr_n = n_refr;
+        prm.refr_nf = (float)n_refr;
+        prm.refr_r2 = (float)(r * r);
+        prm.refr_M = (float)M;
+        prm.refr_isM = M > 0.0 ? (float)(1.0 / std::sqrt(M)) : INFINITY;
+        // crossing-point tolerance: 1/2000 of a carrier wavelength
+        prm.refr_tol = (float)(5e-4 * h->sig.c / h->sig.fc);
+    }
     prm.hx = (float)hx;
     prm.hy = (float)hy;
     prm.hz = (float)hz;
@@ -97,6 +114,18 @@ static int launch_one(const Setup& S, cudaStream_t st) {
     const bool mv = S.prm.vel != nullptr;
     auto kern = S.prm.beam ? (mv ? tdbp_kernel<ET, DIM3, MODE, true, true> : tdbp_kernel<ET, DIM3, MODE, true, false>)
                            : (mv ? tdbp_kernel<ET, DIM3, MODE, false, true> : tdbp_kernel<ET, DIM3, MODE, false, false>);
+    if constexpr (MODE == MODE_FORWARD) {
+        if (S.prm.refract) {
+            if (S.prm.beam || mv) {
+                set_error("the refraction model does not combine with receiver motion or a beam");
+                return SAS_ERR_UNSUPPORTED;
+            }
+            kern = tdbp_kernel<ET, DIM3, MODE, false, false, true>;
+        }
+    } else if (S.prm.refract) {
+        set_error("the offset gradient is not available with the refraction model");
+        return SAS_ERR_UNSUPPORTED;
+    }
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());
