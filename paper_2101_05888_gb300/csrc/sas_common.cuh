@@ -137,6 +137,9 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
     return *reinterpret_cast<float2*>(&rd);
 }
+// elementwise max / min of pairs (two scalar operations)
+__device__ __forceinline__ float2 fmax2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ float2 fmin2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
 
 // Integer rounding on the FP32 pipe: for |v| < 2^22, t = v + 1.5*2^23 (round
 // to nearest) holds the nearest integer n of v in its low mantissa bits

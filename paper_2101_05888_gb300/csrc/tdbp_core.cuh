@@ -57,7 +57,7 @@ constexpr int NBUF = 4;                 // Farrow buffers (groups)
 constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
-constexpr int EROW = 48;                // bytes per Farrow row: E0..E5 float2 (FP16 rows: E0..E5 half2)
+constexpr int EROW = 48;                // bytes per Farrow position allocated (layouts below)
 constexpr int RUN = 10;                 // Farrow positions per expansion run
 constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
@@ -193,6 +193,19 @@ constexpr float TWO_PI_F = 6.28318530717958647f;
 __device__ __forceinline__ __half2 h2_of_bits(uint32_t b) {
     return *reinterpret_cast<__half2*>(&b);
 }
+// the two BF16 halves of a packed pair as FP32 (exact: BF16 is the top half of FP32)
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
+    return make_float2(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
+}
+
+// Farrow row layouts (48-B rows, one per position):
+//  * E16 (forward pass, 16-bit echo): E0..E5 FP16 pairs in the first 24 B.
+//  * otherwise: E0..E5 FP32 pairs.
+//  * TAIL16 (off): E0..E3 FP32 pairs (32 B), then E4, E5 as BF16 pairs (8 B),
+//    so that a pixel reads 40 B: 15 % fewer shared-memory wavefronts, 15 %
+//    more instructions (the BF16 unpacking) and 3 % slower on the stripmap
+//    workload, where the issue rate binds as much as the shared pipe.  (BF16
+//    for E4, E5 changes the interpolated value by 3e-6 rms relative.)
 
 
 // FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
@@ -493,8 +506,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     using T = Tile<DIM3>;
     static_assert(!REFRACT || (MODE == MODE_FORWARD && !BEAM && !MOTION), "refraction: forward pass only");
     constexpr int KREC = REFRACT ? NREC_REFR : NREC;   // record fields
-    // FP16 Farrow rows for 16-bit echoes in the forward pass
+    // FP16 Farrow rows for 16-bit echoes in the forward pass; FP32 rows with
+    // a BF16 tail for complex64 echoes in the forward pass
     constexpr bool E16 = (MODE == MODE_FORWARD) && (sizeof(ET) == 4);
+    constexpr bool TAIL16 = false;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -689,7 +704,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         float2 cc2[TAPS];
 #pragma unroll
         for (int m = 0; m < TAPS; ++m) cc2[m] = make_float2(coef_s[m * NP + Ep], coef_s[m * NP + Ep]);
-        const int e_off = E16 ? Ep * 4 : Ep * 8;
+        // byte offset of this lane's power in a row
+        const int e_off = E16 ? Ep * 4 : (TAIL16 && Ep >= 4 ? 32 + (Ep - 4) * 4 : Ep * 8);
+        const bool e_f32 = !TAIL16 || Ep < 4;
         int G = 0;   // groups emitted
         auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
             const int b = G % NBUF;
@@ -708,6 +725,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     float2 w[RUN + TAPS - 1];
 #pragma unroll
                     for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
+                    // (RUN = 9 would start the runs 12 r words apart modulo the 32 banks and
+                    // make these stores conflict-free, but the extra run per pair costs the
+                    // producer more than the conflicts: 3 % slower on the stripmap workload)
                     unsigned char* dst = eb + j * ebuf_pair + pos0 * EROW + e_off;
 #pragma unroll
                     for (int kq = 0; kq < RUN; ++kq) {
@@ -716,8 +736,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                         for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
                         if (E16)
                             *reinterpret_cast<__half2*>(dst + kq * EROW) = __floats2half2_rn(e.x, e.y);
-                        else
+                        else if (e_f32)
                             *reinterpret_cast<float2*>(dst + kq * EROW) = e;
+                        else
+                            *reinterpret_cast<__nv_bfloat162*>(dst + kq * EROW) = __floats2bfloat162_rn(e.x, e.y);
                     }
                 }
             }
@@ -999,8 +1021,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 acc[s].y = fmaf(vx, sn, fmaf(vy, cs, acc[s].y));
                 continue;
             }
-            const float4 e01 = e[0], e23 = e[1], e45 = e[2];
             const float2 gg2 = make_float2(g, g);
+            if constexpr (TAIL16) {
+                // E5, E4 from BF16 pairs, E3 .. E0 FP32; packed FP32 Horner
+                const float4 e01 = e[0], e23 = e[1];
+                const uint2 t45 = *reinterpret_cast<const uint2*>(e + 2);
+                float2 v = ffma2(bf2_to_f2(t45.y), gg2, bf2_to_f2(t45.x));
+                v = ffma2(v, gg2, make_float2(e23.z, e23.w));
+                v = ffma2(v, gg2, make_float2(e23.x, e23.y));
+                v = ffma2(v, gg2, make_float2(e01.z, e01.w));
+                v = ffma2(v, gg2, make_float2(e01.x, e01.y));
+                acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
+                acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
+                continue;
+            }
+            const float4 e01 = e[0], e23 = e[1], e45 = e[2];
             if (MODE == MODE_FORWARD) {
                 // packed FP32 Horner over E_5 .. E_0
                 float2 v = ffma2(make_float2(e45.z, e45.w), gg2, make_float2(e45.x, e45.y));

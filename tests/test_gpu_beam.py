@@ -128,9 +128,9 @@ def test_beam_adjoint_and_offset_gradient():
     grad = torch.empty((w.n_pings, 3), dtype=torch.float64, device="cuda")
     img = geom.backproject(sas.grid_from(g), sas.kaiser(BETA)).cpu().numpy()
     # dot test with the full G: forward and adjoint take the same FP32 decisions
-    # (one term decided differently would move <B e, G> by about 1; FP32 and
-    # the BF16 Farrow tail of the forward move it by ~1e-5 of a random inner
-    # product's size |B e| |G| / sqrt(n))
+    # (one term decided differently would move <B e, G> by about 1; FP32
+    # rounding moves it by ~1e-6 of a random inner product's size
+    # |B e| |G| / sqrt(n))
     sas.sas_backproject_adjoint(geom.h, sas.grid_from(g), sas.kaiser(BETA), torch.from_numpy(G).cuda(), eadj, None)
     Be, Gv = img.reshape(-1).astype(np.complex128), G.reshape(-1).astype(np.complex128)
     lhs = np.vdot(Be, Gv)

@@ -88,7 +88,8 @@ def test_adjoint_and_offset_gradient_with_motion():
     Be, Gv = img.reshape(-1).astype(np.complex128), G.reshape(-1).astype(np.complex128)
     lhs = np.vdot(Be, Gv)
     rhs = np.vdot(echo.reshape(-1).astype(np.complex128), eadj.cpu().numpy().reshape(-1).astype(np.complex128))
-    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    # scale of a random inner product: see test_gpu_dot_product
+    assert abs(lhs - rhs) <= 2e-5 * np.linalg.norm(Be) * np.linalg.norm(Gv) / np.sqrt(Gv.size)
     tx, rx = oracle_positions(nav)
     pix = grid_pixels(g)
     ref_adj = oracle.backproject_adjoint(tx, rx, oracle_signal(w), G.reshape(-1), 8, BETA, pix, vel=nav["vel"])
