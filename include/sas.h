@@ -367,6 +367,90 @@ int sas_cull_stats(sas_geometry_t h, long long* out, int reset, void* cuda_strea
  * timeout status set (no fault, no trap).  skip = 0 restores normal operation. */
 int sas_debug_starve_copies(sas_geometry_t h, int skip, int32_t wait_limit_ms);
 
+/* ---- Displaced-phase-centre (DPC) micronavigation (Sec. II-D, Eqs. 3-8) ----
+ *
+ * Kinematics: ping i leaves at T_i from the platform position p_i; while its
+ * echo comes in the platform moves with the constant velocity v_i (p = v t,
+ * transmission instantaneous), and p_{i+1} = p_i + v_i dt_i.  Transmitter:
+ * p_i + R_i l_TX; receiver c at time t after transmission: p_i + v_i t +
+ * R_i l_c (R_i of Eq. 2, attitude constant during the reception).  DPC pairs:
+ * receiver c + shift of ping i with receiver c of ping i + 1 (c = 0 .. C - 1 -
+ * shift): their phase centres overlap when the array advances shift half
+ * element pitches per ping.
+ *
+ * Measurement layout ("DPC layout"): index m = (i (C - shift) + c) K + k for
+ * ping pair i = 0 .. P - 2, receiver c = 0 .. C - shift - 1, window
+ * k = 0 .. K - 1; M = (P - 1)(C - shift) K. */
+
+/* Time-delay estimation between the DPC pairs of the echo stored in h (after
+ * the method the paper cites: coarse delay from the magnitude of the complex
+ * correlation, fine delay from its phase).  For every measurement:
+ * R(tau) = sum_n e[i+1][c][n] conj(e[i][c+shift][n - tau]) over the W samples
+ * n in [centre_k - W/2, centre_k - W/2 + W) and lags |tau| <= max_lag (samples
+ * outside a row read zero).  coarse = (lag of max |R|, refined by the
+ * parabola through |R| at the peak and its two neighbours; no refinement at
+ * the edge lags) / fs  [s]; fine = -arg R(coarse) / (2 pi fc) [s, in
+ * (-1/(2 fc), 1/(2 fc)]], R(coarse) by the same three-point interpolation of
+ * the complex values; rho = |R(peak lag)| / sqrt(sum |e2|^2 sum |e1 shifted|^2).
+ * The unwrapped delay is fine + k / fc for the integer k nearest to a
+ * reference (sas_dpc_model_delays of a coarse solution).  d_centres: [K]
+ * int32 device (sample indices); outputs: FP64 device arrays [M] in the DPC
+ * layout, any may be NULL.  FP32 correlation sums.  Constraints: 1 <= W <=
+ * 4096, 0 <= max_lag <= 15, 0 <= shift < C, P >= 2.  Errors: SAS_ERR_ARG,
+ * SAS_ERR_STATE (no echo), SAS_ERR_CUDA. */
+int sas_dpc_delays(sas_geometry_t h, int32_t shift, const int32_t* d_centres, int32_t K, int32_t W,
+                   int32_t max_lag, double* d_coarse, double* d_fine, double* d_rho, void* cuda_stream);
+
+/* The motion problem of Eq. 8 (all arrays FP64 on the device, caller-owned). */
+typedef struct sas_dpc_problem {
+    int32_t P, C, shift, K;     /* pings, receivers per ping, DPC shift, windows per ping pair */
+    int32_t side;               /* imaging side: +1 starboard (body +y), -1 port */
+    double c;                   /* sound speed [m/s] */
+    double lambda1, lambda2;    /* Eq. 8 weights of Eq. 6 (smoothness) and Eq. 7 (DVL) */
+    double huber;               /* > 0: Eq. 3 on r / huber, r = c g [m]; <= 0: squares (Eq. 5) */
+    const double* d_p0;         /* [3] platform position at ping 0 (NED) */
+    const double* d_vx;         /* [P] surge velocity (known) */
+    const double* d_att;        /* [P][3] roll, pitch, yaw */
+    const double* d_dt;         /* [P-1] ping intervals */
+    const double* d_tx_lever;   /* [3] */
+    const double* d_rx_lever;   /* [C][3] */
+    const double* d_t;          /* [K] window centre times [s after transmission] */
+    const double* d_delay;      /* [M] measured delays [s] (DPC layout) */
+    const double* d_weight;     /* [M] weights (e.g. rho) or NULL for 1 */
+    const double* d_z_dvl;      /* [P] platform depth from the DVL (Eq. 7) */
+    const double* d_ps;         /* [M][3] footprints (sas_dpc_footprints) */
+} sas_dpc_problem;
+
+/* Footprints p_s of Eq. 4: for measurement (i, c, k) the point of the flat
+ * seafloor z = 0 abeam of ping i's phase centre (midpoint of its transmitter
+ * and receiver c + shift) on the imaging side, at slant range c t_k / 2 from
+ * it, with the positions integrated from the velocities (d_vy, d_vz) [P]
+ * (the navigation prior).  d_ps: [M][3].  pr->d_ps, d_delay, d_weight and
+ * d_z_dvl are not read.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_dpc_footprints(const sas_dpc_problem* pr, const double* d_vy, const double* d_vz, double* d_ps,
+                       void* cuda_stream);
+
+/* The delays that make Eq. 4 vanish for the velocities (d_vy, d_vz):
+ * (path of ping i+1 - path of ping i) / c, with both receivers at t_k; [M]
+ * FP64.  d_delay and d_weight are not read.  Errors: SAS_ERR_ARG, SAS_ERR_CUDA. */
+int sas_dpc_model_delays(const sas_dpc_problem* pr, const double* d_vy, const double* d_vz, double* d_out,
+                         void* cuda_stream);
+
+/* Minimises Eq. 8 = sum_m w_m h(r_m) + lambda1 (Eq. 6) + lambda2 (Eq. 7) over the
+ * sway and heave velocities (d_vy, d_vz) [P] (in: start, out: solution) by
+ * Levenberg-Marquardt in FP64 (Gauss-Newton normal equations with
+ * Marquardt's diagonal damping; Huber by iteratively reweighted residuals).
+ * Eq. 6: v''[i] = v[i+1] - 2 v[i] + v[i-1]; Eq. 7: (p_z,i - z_dvl[i]) with
+ * p_z,i = p_z,0 + sum_{n<i} v_z[n] dt_n.  The normal equations are solved in
+ * the equivalent variables (positions p_1 .. p_{P-1} and the last velocity),
+ * where they are banded (half-bandwidth 7).  At most max_iter accepted steps;
+ * stops when the loss or the step stalls (relative 1e-14).  h_loss (host,
+ * may be NULL): the final Eq. 8 value; h_iters (host, may be NULL): accepted
+ * steps.  Synchronises the stream.  Errors: SAS_ERR_ARG, SAS_ERR_OOM,
+ * SAS_ERR_CUDA. */
+int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_vz, int32_t max_iter, double* h_loss,
+                  int32_t* h_iters, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,8 +30,9 @@ ambiguous or garbled (all recorded in the repository's design notes):
 * g is in seconds; the solver works with r = c g (metres).  Eq. 5 with
   h(a) = a^2 is plain least squares; Eq. 3 (Huber) is applied to r / s_h with
   a scale s_h in metres, i.e. the term is s_h^2 h(r / s_h) (up to the factor 2
-  of scipy's convention, which does not move the minimum).  Optional weights
-  (the correlation coefficients) multiply the squared residuals.
+  of the loss, which does not move the minimum), minimised by iteratively
+  reweighted least squares.  Optional weights (the correlation
+  coefficients) multiply the squared residuals.
 * Eq. 6: v''[i] = v[i+1] - 2 v[i] + v[i-1] (unscaled second differences of
   the per-ping velocities, i = 1 .. P-2), for v_y and v_z.
 * Eq. 7 (its index is garbled): the heave position of ping i,
@@ -210,29 +211,20 @@ def solve(pl: Platform, vy0, vz0, meas: Measurements, ps, c: float, z_dvl, lam1:
 
     x0 = np.concatenate([vy0, vz0])
     if huber > 0:
-        # the robust part and the quadratic regularisers: scipy applies one loss
-        # to all residuals, so the regularisers are passed through the Huber
-        # loss scaled far beyond their size (quadratic there)
-        big = 1e6 * huber
-
-        def fr(x):
-            return np.concatenate([f(x) / huber, reg(x) / big])
-
-        def rho(z):
-            # per-residual Huber on the DPC part, plain square on the rest
-            n = meas.ping.size
-            out = np.empty((3, z.size))
-            zd, zr = z[:n], z[n:]
-            s = np.sqrt(zd)
-            out[0, :n] = np.where(zd <= 1.0, zd, 2.0 * s - 1.0) * huber * huber
-            out[1, :n] = np.where(zd <= 1.0, 1.0, 1.0 / np.maximum(s, 1e-300)) * huber * huber
-            out[2, :n] = np.where(zd <= 1.0, 0.0, -0.5 / np.maximum(zd * s, 1e-300)) * huber * huber
-            out[0, n:] = zr * big * big
-            out[1, n:] = big * big
-            out[2, n:] = 0.0
-            return out
-
-        res = least_squares(fr, x0, loss=rho, method="trf", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=400)
+        # Huber by iteratively reweighted least squares: each pass minimises the
+        # weighted squares with the weights min(1, s_h / |r|) of the previous
+        # solution, whose fixed point is the minimum of the Huber loss
+        x = x0
+        for _ in range(100):
+            r = dpc_residuals(pl, x[:P], x[P:], meas, ps, c)
+            w = np.sqrt(np.minimum(1.0, huber / np.maximum(np.abs(r), 1e-300)))
+            res = least_squares(lambda x_: np.concatenate([w * f(x_), reg(x_)]), x, method="lm", xtol=1e-15,
+                                ftol=1e-15, gtol=1e-15, max_nfev=2000)
+            step = np.abs(res.x - x).max()
+            x = res.x
+            if step <= 1e-14 * max(np.abs(x).max(), 1e-3):
+                break
+        res.x = x
     else:
         res = least_squares(lambda x: np.concatenate([f(x), reg(x)]), x0, method="lm", xtol=1e-15,
                             ftol=1e-15, gtol=1e-15, max_nfev=2000)

@@ -47,6 +47,7 @@ ENTRY_POINTS = [
     "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_cull_stats",
     "sas_matched_filter", "sas_whiten", "sas_tvg", "sas_drc",
     "sas_debug_starve_copies",
+    "sas_dpc_delays", "sas_dpc_footprints", "sas_dpc_model_delays", "sas_dpc_solve",
 ]
 
 
@@ -70,6 +71,16 @@ class sas_grid(ctypes.Structure):
 class sas_interp(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("taps", ctypes.c_int32), ("kaiser_beta", ctypes.c_double),
                 ("table_n", ctypes.c_int32), ("d_table", ctypes.c_void_p)]
+
+
+class sas_dpc_problem(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int32), ("C", ctypes.c_int32), ("shift", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("side", ctypes.c_int32), ("c", ctypes.c_double), ("lambda1", ctypes.c_double),
+                ("lambda2", ctypes.c_double), ("huber", ctypes.c_double),
+                ("d_p0", ctypes.c_void_p), ("d_vx", ctypes.c_void_p), ("d_att", ctypes.c_void_p),
+                ("d_dt", ctypes.c_void_p), ("d_tx_lever", ctypes.c_void_p), ("d_rx_lever", ctypes.c_void_p),
+                ("d_t", ctypes.c_void_p), ("d_delay", ctypes.c_void_p), ("d_weight", ctypes.c_void_p),
+                ("d_z_dvl", ctypes.c_void_p), ("d_ps", ctypes.c_void_p)]
 
 
 class SasError(RuntimeError):
@@ -124,6 +135,12 @@ def lib():
                 "sas_tvg": ([V, V, I64, ctypes.c_int32, D, V, V, V], I),
                 "sas_drc": ([V, I64, D, V, V, V], I),
                 "sas_debug_starve_copies": ([V, I, ctypes.c_int32], I),
+                "sas_dpc_delays": ([V, ctypes.c_int32, V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, V, V, V,
+                                    V], I),
+                "sas_dpc_footprints": ([P(sas_dpc_problem), V, V, V, V], I),
+                "sas_dpc_model_delays": ([P(sas_dpc_problem), V, V, V, V], I),
+                "sas_dpc_solve": ([P(sas_dpc_problem), V, V, ctypes.c_int32, P(ctypes.c_double),
+                                   P(ctypes.c_int32), V], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -296,6 +313,29 @@ def sas_tvg(d_in, d_out, rows: int, n: int, alpha: float, d_gain=None, d_median=
 
 def sas_drc(d_image, npix: int, b: float, d_out, d_stats=None, stream=None):
     _check(lib().sas_drc(_ptr(d_image), npix, float(b), _ptr(d_out), _ptr(d_stats), _stream(stream)))
+
+
+def sas_dpc_delays(h, shift: int, d_centres, K: int, W: int, max_lag: int, d_coarse=None, d_fine=None, d_rho=None,
+                   stream=None):
+    _check(lib().sas_dpc_delays(h, shift, _ptr(d_centres), K, W, max_lag, _ptr(d_coarse), _ptr(d_fine), _ptr(d_rho),
+                                _stream(stream)))
+
+
+def sas_dpc_footprints(pr: sas_dpc_problem, d_vy, d_vz, d_ps, stream=None):
+    _check(lib().sas_dpc_footprints(ctypes.byref(pr), _ptr(d_vy), _ptr(d_vz), _ptr(d_ps), _stream(stream)))
+
+
+def sas_dpc_model_delays(pr: sas_dpc_problem, d_vy, d_vz, d_out, stream=None):
+    _check(lib().sas_dpc_model_delays(ctypes.byref(pr), _ptr(d_vy), _ptr(d_vz), _ptr(d_out), _stream(stream)))
+
+
+def sas_dpc_solve(pr: sas_dpc_problem, d_vy, d_vz, max_iter: int = 100, stream=None):
+    """Returns (final loss, accepted steps); d_vy, d_vz updated in place."""
+    loss = ctypes.c_double(0.0)
+    iters = ctypes.c_int32(0)
+    _check(lib().sas_dpc_solve(ctypes.byref(pr), _ptr(d_vy), _ptr(d_vz), int(max_iter), ctypes.byref(loss),
+                               ctypes.byref(iters), _stream(stream)))
+    return loss.value, iters.value
 
 
 def sas_debug_starve_copies(h, skip: int, wait_limit_ms: int):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libsas.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
 SOURCES = ["sas_api.cu", "tdbp_forward.cu", "tdbp_vjp.cu", "tdbp_adjoint.cu", "sharpness.cu", "sharpness_static.cu", "mlp.cu",
-           "simulate.cu", "condition.cu"]
+           "simulate.cu", "condition.cu", "micronav.cu"]
 HEADERS = ["sas_common.cuh", "tdbp_core.cuh", "fft.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

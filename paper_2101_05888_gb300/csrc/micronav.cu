@@ -1,0 +1,746 @@
+// Displaced-phase-centre (DPC) micronavigation (Sec. II-D, Eqs. 3-8):
+//  * time-delay estimation between the overlapping receivers of consecutive
+//    pings (one warp per measurement window, one lane per lag);
+//  * Eq. 4 residuals and their derivatives in FP64, Eqs. 6-7 regularisers;
+//  * Levenberg-Marquardt on Eq. 8 with Gauss-Newton normal equations.  In the
+//    velocity variables of the paper the normal matrix is dense (a ping's
+//    position integrates all earlier velocities); in the equivalent variables
+//    q_j = p_{j+1} (j < P-1, positions of pings 1 .. P-1) and q_{P-1} = v_{P-1}
+//    every residual touches at most four consecutive nodes, so the matrix is
+//    banded (half-bandwidth 7 over the 2P sway/heave unknowns) and a banded
+//    Cholesky solves it.  The minimiser is the same (a linear change of
+//    variables); Marquardt's diagonal damping is applied in these variables.
+#include "sas_common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+namespace sas {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int DPC_WARPS = 8;      // delay windows per block
+constexpr int BANDW = 7;          // half-bandwidth of the normal matrix
+constexpr int BROW = BANDW + 1;   // stored diagonals per row
+
+// ---------------------------------------------------------------------------
+// Time-delay estimation
+
+template <typename ET>
+__device__ __forceinline__ float2 echo_at(const ET* row, int n, float sc);
+template <>
+__device__ __forceinline__ float2 echo_at<float2>(const float2* row, int n, float) {
+    return row[n];
+}
+template <>
+__device__ __forceinline__ float2 echo_at<__half2>(const __half2* row, int n, float sc) {
+    const float2 v = __half22float2(row[n]);
+    return make_float2(v.x * sc, v.y * sc);
+}
+template <>
+__device__ __forceinline__ float2 echo_at<__nv_bfloat162>(const __nv_bfloat162* row, int n, float sc) {
+    const float2 v = __bfloat1622float2(row[n]);
+    return make_float2(v.x * sc, v.y * sc);
+}
+
+// One warp per measurement m = ((i (C - shift) + c) K + k); lane l holds the
+// lag tau = l - L.  e1 = ping i, receiver c + shift; e2 = ping i + 1, receiver c.
+template <typename ET>
+__global__ void __launch_bounds__(32 * DPC_WARPS)
+    dpc_delay_kernel(const ET* __restrict__ echo, const float* __restrict__ scale, int C, int Ns, int shift,
+                     const int* __restrict__ centres, int K, int W, int L, long long M, double fs, double fc,
+                     double* __restrict__ coarse, double* __restrict__ fine, double* __restrict__ rho) {
+    const long long m = (long long)blockIdx.x * DPC_WARPS + (threadIdx.x >> 5);
+    if (m >= M) return;   // whole warps
+    const int lane = threadIdx.x & 31;
+    const int nc = C - shift;
+    const int k = (int)(m % K);
+    const long long pr = m / K;
+    const int c = (int)(pr % nc);
+    const long long i = pr / nc;
+    const size_t r1 = (size_t)i * C + c + shift, r2 = (size_t)(i + 1) * C + c;
+    const float s1 = scale ? scale[r1] : 1.f, s2 = scale ? scale[r2] : 1.f;
+    const ET* e1 = echo + r1 * (size_t)Ns;
+    const ET* e2 = echo + r2 * (size_t)Ns;
+    const int n0 = centres[k] - W / 2;
+    const int tau = lane - L;
+    const bool lag = lane <= 2 * L;
+    float ar = 0.f, ai = 0.f, p1 = 0.f, p2 = 0.f;   // R(tau); sum |e1[n - tau]|^2; sum |e2[n]|^2
+    for (int n = n0; n < n0 + W; ++n) {
+        const float2 b2 = (n >= 0 && n < Ns) ? echo_at<ET>(e2, n, s2) : make_float2(0.f, 0.f);
+        const int n1 = n - tau;
+        const float2 b1 = (lag && n1 >= 0 && n1 < Ns) ? echo_at<ET>(e1, n1, s1) : make_float2(0.f, 0.f);
+        ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));       // e2 conj(e1)
+        ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
+        p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
+        p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
+    }
+    const float mag = lag ? sqrtf(fmaf(ar, ar, ai * ai)) : -1.f;
+    // largest |R|, the lowest lag on ties
+    float best = mag;
+    int bl = lane;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ob = __shfl_xor_sync(FULL, best, o);
+        const int ol = __shfl_xor_sync(FULL, bl, o);
+        if (ob > best || (ob == best && ol < bl)) {
+            best = ob;
+            bl = ol;
+        }
+    }
+    const int lm = max(bl - 1, 0), lp = min(bl + 1, 31);
+    const float mm = __shfl_sync(FULL, mag, lm), mp = __shfl_sync(FULL, mag, lp);
+    const float rr0 = __shfl_sync(FULL, ar, bl), ri0 = __shfl_sync(FULL, ai, bl);
+    const float rrm = __shfl_sync(FULL, ar, lm), rim = __shfl_sync(FULL, ai, lm);
+    const float rrp = __shfl_sync(FULL, ar, lp), rip = __shfl_sync(FULL, ai, lp);
+    const float q1 = __shfl_sync(FULL, p1, bl);
+    if (lane == 0) {
+        float d = 0.f, Rr = rr0, Ri = ri0;
+        if (bl > 0 && bl < 2 * L) {
+            const float den = mm - 2.f * best + mp;
+            d = den != 0.f ? 0.5f * (mm - mp) / den : 0.f;
+            Rr = rr0 + 0.5f * d * (rrp - rrm) + 0.5f * d * d * (rrp - 2.f * rr0 + rrm);
+            Ri = ri0 + 0.5f * d * (rip - rim) + 0.5f * d * d * (rip - 2.f * ri0 + rim);
+        }
+        if (coarse) coarse[m] = ((double)(bl - L) + (double)d) / fs;
+        if (fine) fine[m] = -(double)atan2f(Ri, Rr) / (2.0 * M_PI * fc);
+        if (rho) {
+            const double den = sqrt((double)p2 * (double)q1);
+            rho[m] = den > 0.0 ? (double)best / den : 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Motion model
+
+struct Prob {
+    int P, C, shift, K, nc, side;
+    long long M;
+    double c, lambda1, lambda2, huber;
+    const double *p0, *vx, *att, *dt, *ltx, *lrx, *t, *delay, *weight, *zdvl, *ps;
+    const double* lev;   // [P][C + 1][3] rotated lever arms R_i l (TX first)
+    const double* xpos;  // [P] along-track positions
+};
+
+struct V3 {
+    double x, y, z;
+};
+__device__ __forceinline__ V3 v3(const double* a) { return V3{a[0], a[1], a[2]}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(double s, V3 a) { return V3{s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double norm(V3 a) { return sqrt(a.x * a.x + a.y * a.y + a.z * a.z); }
+
+// Position and velocity of ping i from the nodes q (sway, heave) and the known
+// along-track terms.
+__device__ __forceinline__ void ping_pv(const Prob& pb, const double* q, int i, V3& p, V3& v) {
+    auto pos = [&](int j) -> V3 {
+        return j == 0 ? v3(pb.p0) : V3{pb.xpos[j], q[2 * (j - 1)], q[2 * (j - 1) + 1]};
+    };
+    p = pos(i);
+    if (i < pb.P - 1) {
+        const V3 pn = pos(i + 1);
+        const double r = 1.0 / pb.dt[i];
+        v = V3{pb.vx[i], (pn.y - p.y) * r, (pn.z - p.z) * r};
+    } else {
+        v = V3{pb.vx[i], q[2 * i], q[2 * i + 1]};
+    }
+}
+
+// Rotated lever arms R_i l_TX, R_i l_c and along-track positions (one thread per ping).
+__global__ void dpc_lever_kernel(Prob pb, double* lev) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pb.P) return;
+    double R[9];
+    attitude_rotation(pb.att[3 * i], pb.att[3 * i + 1], pb.att[3 * i + 2], R);
+    for (int c = -1; c < pb.C; ++c) {
+        const double* l = c < 0 ? pb.ltx : pb.lrx + 3 * c;
+        double* o = lev + 3 * ((size_t)i * (pb.C + 1) + (c + 1));
+        o[0] = R[0] * l[0] + R[1] * l[1] + R[2] * l[2];
+        o[1] = R[3] * l[0] + R[4] * l[1] + R[5] * l[2];
+        o[2] = R[6] * l[0] + R[7] * l[1] + R[8] * l[2];
+    }
+}
+
+// Nodes q from velocities (positions integrated from p_0), and the along-track positions.
+__global__ void dpc_nodes_kernel(Prob pb, const double* vy, const double* vz, double* q, double* xpos) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double x = pb.p0[0], y = pb.p0[1], z = pb.p0[2];
+    xpos[0] = x;
+    for (int i = 0; i + 1 < pb.P; ++i) {
+        x += pb.vx[i] * pb.dt[i];
+        y += vy[i] * pb.dt[i];
+        z += vz[i] * pb.dt[i];
+        xpos[i + 1] = x;
+        q[2 * i] = y;
+        q[2 * i + 1] = z;
+    }
+    q[2 * (pb.P - 1)] = vy[pb.P - 1];
+    q[2 * (pb.P - 1) + 1] = vz[pb.P - 1];
+}
+
+__global__ void dpc_velocities_kernel(Prob pb, const double* q, double* vy, double* vz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= pb.P) return;
+    V3 p, v;
+    ping_pv(pb, q, i, p, v);
+    vy[i] = v.y;
+    vz[i] = v.z;
+}
+
+// Footprint of measurement m from the nodes q (the prior).
+__global__ void dpc_footprint_kernel(Prob pb, const double* q, double* ps) {
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= pb.M) return;
+    const int k = (int)(m % pb.K);
+    const long long pr = m / pb.K;
+    const int c = (int)(pr % pb.nc);
+    const int i = (int)(pr / pb.nc);
+    V3 p, v;
+    ping_pv(pb, q, i, p, v);
+    const double* lv = pb.lev + 3 * (size_t)i * (pb.C + 1);
+    const V3 pc = p + 0.5 * (v3(lv) + v3(lv + 3 * (c + pb.shift + 1)));
+    double sy, cy;
+    sincos(pb.att[3 * i + 2], &sy, &cy);
+    const double rng = 0.5 * pb.c * pb.t[k];
+    const double ground = sqrt(fmax(rng * rng - pc.z * pc.z, 0.0));
+    ps[3 * m + 0] = pc.x + ground * (-sy) * pb.side;
+    ps[3 * m + 1] = pc.y + ground * cy * pb.side;
+    ps[3 * m + 2] = 0.0;
+}
+
+// r = c g (Eq. 4, metres) of measurement m with the measured delay (or 0), and
+// its derivatives with respect to the sway / heave of p_i, v_i, p_{i+1}, v_{i+1}.
+struct Res {
+    double r;
+    double dp1[2], dv1[2], dp2[2], dv2[2];
+};
+template <bool JAC>
+__device__ __forceinline__ Res dpc_residual(const Prob& pb, const double* q, long long m, bool with_delay) {
+    const int k = (int)(m % pb.K);
+    const long long pr = m / pb.K;
+    const int c = (int)(pr % pb.nc);
+    const int i = (int)(pr / pb.nc);
+    const double t = pb.t[k];
+    V3 p1, v1, p2, v2;
+    ping_pv(pb, q, i, p1, v1);
+    ping_pv(pb, q, i + 1, p2, v2);
+    const double* l1 = pb.lev + 3 * (size_t)i * (pb.C + 1);
+    const double* l2 = pb.lev + 3 * (size_t)(i + 1) * (pb.C + 1);
+    const V3 s = v3(pb.ps + 3 * m);
+    const V3 a1 = p1 + v3(l1) - s, b1 = p1 + t * v1 + v3(l1 + 3 * (c + pb.shift + 1)) - s;
+    const V3 a2 = p2 + v3(l2) - s, b2 = p2 + t * v2 + v3(l2 + 3 * (c + 1)) - s;
+    const double na1 = norm(a1), nb1 = norm(b1), na2 = norm(a2), nb2 = norm(b2);
+    Res o;
+    o.r = (na1 + nb1) - (na2 + nb2) + (with_delay ? pb.c * pb.delay[m] : 0.0);
+    if (JAC) {
+        const double ia1 = 1.0 / na1, ib1 = 1.0 / nb1, ia2 = 1.0 / na2, ib2 = 1.0 / nb2;
+        o.dp1[0] = a1.y * ia1 + b1.y * ib1;
+        o.dp1[1] = a1.z * ia1 + b1.z * ib1;
+        o.dv1[0] = t * b1.y * ib1;
+        o.dv1[1] = t * b1.z * ib1;
+        o.dp2[0] = -(a2.y * ia2 + b2.y * ib2);
+        o.dp2[1] = -(a2.z * ia2 + b2.z * ib2);
+        o.dv2[0] = -t * b2.y * ib2;
+        o.dv2[1] = -t * b2.z * ib2;
+    }
+    return o;
+}
+
+__global__ void dpc_model_kernel(Prob pb, const double* q, double* out) {
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= pb.M) return;
+    out[m] = -dpc_residual<false>(pb, q, m, false).r / pb.c;
+}
+
+// Eq. 5 / Eq. 3 term and the iteratively reweighted weight of a residual.
+__device__ __forceinline__ void robust(const Prob& pb, double r, double om, double& cost, double& w) {
+    if (pb.huber > 0.0) {
+        const double a = fabs(r);
+        if (a <= pb.huber) {
+            cost = om * r * r;
+            w = om;
+        } else {
+            cost = om * (2.0 * pb.huber * a - pb.huber * pb.huber);
+            w = om * pb.huber / a;
+        }
+    } else {
+        cost = om * r * r;
+        w = om;
+    }
+}
+
+// Band index of the normal matrix entry (a, b), a <= b <= a + BANDW.
+__device__ __forceinline__ size_t bidx(int a, int b) { return (size_t)a * BROW + (b - a); }
+
+// DPC part of the loss (acc[0]) and, with JAC, of the normal matrix and the
+// gradient: one block per ping pair, its (C - shift) K measurements over the
+// threads, a block reduction, one atomic per entry.
+template <bool JAC>
+__global__ void __launch_bounds__(256) dpc_assemble_kernel(Prob pb, const double* q, double* band, double* grad,
+                                                           double* acc) {
+    const int i = blockIdx.x;   // ping pair
+    const long long per = (long long)pb.nc * pb.K;
+    // local unknowns: nodes i-1 (absent for i = 0), i, i+1, sway and heave each
+    constexpr int NL = 6, NT = NL * (NL + 1) / 2;
+    double cst = 0.0, g[NL] = {0, 0, 0, 0, 0, 0}, H[NT];
+#pragma unroll
+    for (int e = 0; e < NT; ++e) H[e] = 0.0;
+    const double r1 = 1.0 / pb.dt[i];
+    const bool last = i + 1 == pb.P - 1;
+    const double r2 = last ? 1.0 : 1.0 / pb.dt[i + 1];
+    for (long long e = threadIdx.x; e < per; e += blockDim.x) {
+        const long long m = (long long)i * per + e;
+        const Res o = dpc_residual<JAC>(pb, q, m, true);
+        double cm, w;
+        robust(pb, o.r, pb.weight ? pb.weight[m] : 1.0, cm, w);
+        cst += cm;
+        if (JAC) {
+            double J[NL];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                J[a] = i > 0 ? o.dp1[a] - o.dv1[a] * r1 : 0.0;                            // node i-1 (p_i, v_i)
+                J[2 + a] = o.dp2[a] + o.dv1[a] * r1 - (last ? 0.0 : o.dv2[a] * r2);     // node i (p_{i+1}, v_i, v_{i+1})
+                J[4 + a] = o.dv2[a] * r2;                                               // node i+1 (v_{i+1})
+            }
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < NL; ++a) {
+                g[a] = fma(w * J[a], o.r, g[a]);
+#pragma unroll
+                for (int b = a; b < NL; ++b) {
+                    H[t] = fma(w * J[a], J[b], H[t]);
+                    ++t;
+                }
+            }
+        }
+    }
+    // block reduction: warps by shuffles, then across warps in shared memory
+    __shared__ double red[8][1 + NL + NT];
+    auto wsum = [&](double v) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        return v;
+    };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cst = wsum(cst);
+    if (JAC) {
+#pragma unroll
+        for (int a = 0; a < NL; ++a) g[a] = wsum(g[a]);
+#pragma unroll
+        for (int e = 0; e < NT; ++e) H[e] = wsum(H[e]);
+    }
+    if (lane == 0) {
+        red[warp][0] = cst;
+        if (JAC) {
+            for (int a = 0; a < NL; ++a) red[warp][1 + a] = g[a];
+            for (int e = 0; e < NT; ++e) red[warp][1 + NL + e] = H[e];
+        }
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    const int nval = JAC ? 1 + NL + NT : 1;
+    if ((int)threadIdx.x < nval) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < nw; ++w2) s += red[w2][threadIdx.x];
+        const int v = threadIdx.x;
+        if (v == 0) {
+            atomicAdd(&acc[0], s);
+        } else if (v <= NL) {
+            const int a = v - 1;
+            const int node = i - 1 + a / 2;
+            if (node >= 0) atomicAdd(&grad[2 * node + (a & 1)], s);
+        } else {
+            // entry e of the upper triangle -> (a, b)
+            int e = v - 1 - NL, a = 0;
+            while (e >= NL - a) {
+                e -= NL - a;
+                ++a;
+            }
+            const int b = a + e;
+            const int na = i - 1 + a / 2, nb = i - 1 + b / 2;
+            if (na >= 0 && nb >= 0) {
+                const int ga = 2 * na + (a & 1), gb = 2 * nb + (b & 1);
+                atomicAdd(&band[bidx(min(ga, gb), max(ga, gb))], s);
+            }
+        }
+    }
+}
+
+// Regularisers (Eqs. 6, 7): one thread per ping; loss into acc[0].
+template <bool JAC>
+__global__ void dpc_regular_kernel(Prob pb, const double* q, double* band, double* grad, double* acc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double cst = 0.0;
+    if (i < pb.P) {
+        // DVL: p_z,i - z_dvl[i]
+        const double pz = i == 0 ? pb.p0[2] : q[2 * (i - 1) + 1];
+        const double d = pz - pb.zdvl[i];
+        cst += pb.lambda2 * d * d;
+        if (JAC && i > 0) {
+            const int u = 2 * (i - 1) + 1;
+            atomicAdd(&band[bidx(u, u)], pb.lambda2);
+            atomicAdd(&grad[u], pb.lambda2 * d);
+        }
+        // smoothness: v[i+1] - 2 v[i] + v[i-1], sway (comp 0) and heave (comp 1)
+        if (i >= 1 && i + 1 < pb.P) {
+            for (int comp = 0; comp < 2; ++comp) {
+                // v_n = (P_{n+1} - P_n) / dt_n (n < P-1), v_{P-1} = q_{P-1}; P_0 = p0, P_j = q_{j-1}
+                int node[4];
+                double coef[4], s = 0.0;
+                int nn = 0;
+                auto add = [&](int nd, double cf) {
+                    if (nd < 0) return;
+                    for (int z = 0; z < nn; ++z)
+                        if (node[z] == nd) {
+                            coef[z] += cf;
+                            return;
+                        }
+                    node[nn] = nd;
+                    coef[nn] = cf;
+                    ++nn;
+                };
+                auto vel = [&](int n, double wgt) {
+                    if (n < pb.P - 1) {
+                        const double r = 1.0 / pb.dt[n];
+                        const double a = q[2 * n + comp];                                          // P_{n+1} = q_n
+                        const double b = n == 0 ? (comp ? pb.p0[2] : pb.p0[1]) : q[2 * (n - 1) + comp];   // P_n
+                        s += wgt * (a - b) * r;
+                        add(n, wgt * r);
+                        add(n - 1, -wgt * r);
+                    } else {
+                        s += wgt * q[2 * n + comp];
+                        add(n, wgt);
+                    }
+                };
+                vel(i + 1, 1.0);
+                vel(i, -2.0);
+                vel(i - 1, 1.0);
+                cst += pb.lambda1 * s * s;
+                if (JAC) {
+                    for (int a = 0; a < nn; ++a) {
+                        const int ga = 2 * node[a] + comp;
+                        atomicAdd(&grad[ga], pb.lambda1 * coef[a] * s);
+                        for (int b = 0; b < nn; ++b) {
+                            const int gb = 2 * node[b] + comp;
+                            if (gb >= ga) atomicAdd(&band[bidx(ga, gb)], pb.lambda1 * coef[a] * coef[b]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // block sum of the loss
+    __shared__ double red[32];
+    for (int o = 16; o; o >>= 1) cst += __shfl_xor_sync(FULL, cst, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cst;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(&acc[0], s);
+    }
+}
+
+// Damped banded Cholesky solve of (N + mu diag N) delta = -g and the trial
+// nodes q + delta (one thread; the system is small and banded).  acc[1] = 1
+// when the factorisation fails; acc[2] = max |delta|.
+__global__ void dpc_solve_kernel(int n, const double* band, const double* grad, double mu, double* work,
+                                 const double* q, double* q_try, double* acc) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double* U = work;            // [n][BROW]: U(j, j + d), A = U^T U
+    double* y = work + (size_t)n * BROW;
+    acc[1] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        for (int d = 0; d <= BANDW && j + d < n; ++d) {
+            double s = band[bidx(j, j + d)];
+            if (d == 0) s += mu * (band[bidx(j, j)] + 1e-12);   // Marquardt's scaling, Levenberg's floor
+            for (int k = max(0, j + d - BANDW); k < j; ++k) s -= U[(size_t)k * BROW + (j - k)] * U[(size_t)k * BROW + (j + d - k)];
+            if (d == 0) {
+                if (!(s > 0.0)) {
+                    acc[1] = 1.0;
+                    return;
+                }
+                U[(size_t)j * BROW] = sqrt(s);
+            } else {
+                U[(size_t)j * BROW + d] = s / U[(size_t)j * BROW];
+            }
+        }
+    }
+    // U^T y = -g
+    for (int j = 0; j < n; ++j) {
+        double s = -grad[j];
+        for (int k = max(0, j - BANDW); k < j; ++k) s -= U[(size_t)k * BROW + (j - k)] * y[k];
+        y[j] = s / U[(size_t)j * BROW];
+    }
+    // U delta = y
+    double dmax = 0.0;
+    for (int j = n - 1; j >= 0; --j) {
+        double s = y[j];
+        for (int d = 1; d <= BANDW && j + d < n; ++d) s -= U[(size_t)j * BROW + d] * y[j + d];
+        y[j] = s / U[(size_t)j * BROW];
+        dmax = fmax(dmax, fabs(y[j]));
+        q_try[j] = q[j] + y[j];
+    }
+    acc[2] = dmax;
+}
+
+inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+int check_problem(const sas_dpc_problem* pr) {
+    if (!pr || pr->P < 2 || pr->C < 1 || pr->shift < 0 || pr->shift >= pr->C || pr->K < 1 || !(pr->c > 0) ||
+        (pr->side != 1 && pr->side != -1) || !pr->d_p0 || !pr->d_vx || !pr->d_att || !pr->d_dt ||
+        !pr->d_tx_lever || !pr->d_rx_lever || !pr->d_t || !(pr->lambda1 >= 0) || !(pr->lambda2 >= 0)) {
+        set_error("sas_dpc: bad problem description");
+        return SAS_ERR_ARG;
+    }
+    return SAS_OK;
+}
+
+Prob make_prob(const sas_dpc_problem* pr) {
+    Prob pb{};
+    pb.P = pr->P;
+    pb.C = pr->C;
+    pb.shift = pr->shift;
+    pb.K = pr->K;
+    pb.nc = pr->C - pr->shift;
+    pb.side = pr->side;
+    pb.M = (long long)(pr->P - 1) * pb.nc * pr->K;
+    pb.c = pr->c;
+    pb.lambda1 = pr->lambda1;
+    pb.lambda2 = pr->lambda2;
+    pb.huber = pr->huber;
+    pb.p0 = pr->d_p0;
+    pb.vx = pr->d_vx;
+    pb.att = pr->d_att;
+    pb.dt = pr->d_dt;
+    pb.ltx = pr->d_tx_lever;
+    pb.lrx = pr->d_rx_lever;
+    pb.t = pr->d_t;
+    pb.delay = pr->d_delay;
+    pb.weight = pr->d_weight;
+    pb.zdvl = pr->d_z_dvl;
+    pb.ps = pr->d_ps;
+    return pb;
+}
+
+// Device scratch of one call: rotated levers, along-track positions, nodes.
+struct Scratch {
+    double* base = nullptr;
+    double *lev, *xpos, *q;
+    int alloc(const Prob& pb, size_t extra, cudaStream_t st) {
+        const size_t n = (size_t)pb.P * (pb.C + 1) * 3 + (size_t)pb.P + 2 * (size_t)pb.P + extra;
+        if (cudaMallocAsync(&base, n * sizeof(double), st) != cudaSuccess) {
+            set_error("sas_dpc: device allocation failed");
+            return SAS_ERR_OOM;
+        }
+        lev = base;
+        xpos = lev + (size_t)pb.P * (pb.C + 1) * 3;
+        q = xpos + pb.P;
+        return SAS_OK;
+    }
+};
+
+// Rotated levers, along-track positions and nodes from the velocities.
+int setup(Prob& pb, Scratch& S, const double* vy, const double* vz, cudaStream_t st) {
+    dpc_lever_kernel<<<blocks_for(pb.P, 128), 128, 0, st>>>(pb, S.lev);
+    dpc_nodes_kernel<<<1, 1, 0, st>>>(pb, vy, vz, S.q, S.xpos);
+    SAS_CUDA(cudaGetLastError());
+    pb.lev = S.lev;
+    pb.xpos = S.xpos;
+    return SAS_OK;
+}
+
+}  // namespace
+}  // namespace sas
+
+using namespace sas;
+
+extern "C" int sas_dpc_delays(sas_geometry_t h, int32_t shift, const int32_t* d_centres, int32_t K, int32_t W,
+                              int32_t max_lag, double* d_coarse, double* d_fine, double* d_rho, void* stream) {
+    if (!h || !d_centres || K < 1 || W < 1 || W > 4096 || max_lag < 0 || max_lag > 15 || shift < 0 ||
+        shift >= h->C || h->P < 2) {
+        set_error("sas_dpc_delays: bad argument");
+        return SAS_ERR_ARG;
+    }
+    if (h->echo_dtype < 0) {
+        set_error("sas_dpc_delays: no echo uploaded");
+        return SAS_ERR_STATE;
+    }
+    const long long M = (long long)(h->P - 1) * (h->C - shift) * K;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = blocks_for(M, DPC_WARPS);
+    const double fs = h->sig.fs, fc = h->sig.fc;
+    switch (h->echo_dtype) {
+        case SAS_ECHO_C64:
+            dpc_delay_kernel<float2><<<grid, 32 * DPC_WARPS, 0, st>>>((const float2*)h->d_echo, nullptr, h->C, h->Ns,
+                                                                      shift, d_centres, K, W, max_lag, M, fs, fc,
+                                                                      d_coarse, d_fine, d_rho);
+            break;
+        case SAS_ECHO_C32_F16:
+            dpc_delay_kernel<__half2><<<grid, 32 * DPC_WARPS, 0, st>>>((const __half2*)h->d_echo, h->d_scale, h->C,
+                                                                       h->Ns, shift, d_centres, K, W, max_lag, M, fs,
+                                                                       fc, d_coarse, d_fine, d_rho);
+            break;
+        default:
+            dpc_delay_kernel<__nv_bfloat162><<<grid, 32 * DPC_WARPS, 0, st>>>(
+                (const __nv_bfloat162*)h->d_echo, h->d_scale, h->C, h->Ns, shift, d_centres, K, W, max_lag, M, fs, fc,
+                d_coarse, d_fine, d_rho);
+            break;
+    }
+    SAS_CUDA(cudaGetLastError());
+    return SAS_OK;
+}
+
+extern "C" int sas_dpc_footprints(const sas_dpc_problem* pr, const double* d_vy, const double* d_vz, double* d_ps,
+                                  void* stream) {
+    int rc = check_problem(pr);
+    if (rc != SAS_OK) return rc;
+    if (!d_vy || !d_vz || !d_ps) {
+        set_error("sas_dpc_footprints: null argument");
+        return SAS_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob pb = make_prob(pr);
+    Scratch S;
+    rc = S.alloc(pb, 0, st);
+    if (rc != SAS_OK) return rc;
+    rc = setup(pb, S, d_vy, d_vz, st);
+    if (rc == SAS_OK) {
+        dpc_footprint_kernel<<<blocks_for(pb.M, 256), 256, 0, st>>>(pb, S.q, d_ps);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "dpc_footprint_kernel");
+    }
+    cudaFreeAsync(S.base, st);
+    return rc;
+}
+
+extern "C" int sas_dpc_model_delays(const sas_dpc_problem* pr, const double* d_vy, const double* d_vz, double* d_out,
+                                    void* stream) {
+    int rc = check_problem(pr);
+    if (rc != SAS_OK) return rc;
+    if (!d_vy || !d_vz || !d_out || !pr->d_ps) {
+        set_error("sas_dpc_model_delays: null argument");
+        return SAS_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob pb = make_prob(pr);
+    Scratch S;
+    rc = S.alloc(pb, 0, st);
+    if (rc != SAS_OK) return rc;
+    rc = setup(pb, S, d_vy, d_vz, st);
+    if (rc == SAS_OK) {
+        dpc_model_kernel<<<blocks_for(pb.M, 256), 256, 0, st>>>(pb, S.q, d_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_fail(e, "dpc_model_kernel");
+    }
+    cudaFreeAsync(S.base, st);
+    return rc;
+}
+
+extern "C" int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_vz, int32_t max_iter, double* h_loss,
+                             int32_t* h_iters, void* stream) {
+    int rc = check_problem(pr);
+    if (rc != SAS_OK) return rc;
+    if (!d_vy || !d_vz || !pr->d_delay || !pr->d_ps || !pr->d_z_dvl || max_iter < 0) {
+        set_error("sas_dpc_solve: bad argument");
+        return SAS_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob pb = make_prob(pr);
+    const int n = 2 * pb.P;
+    // scratch after the nodes: q_try [n], band [n][BROW], grad [n], work [n][BROW + 1], acc [4]
+    const size_t extra = (size_t)n + (size_t)n * BROW + n + (size_t)n * (BROW + 1) + 4;
+    Scratch S;
+    rc = S.alloc(pb, extra, st);
+    if (rc != SAS_OK) return rc;
+    double* q_try = S.q + n;
+    double* band = q_try + n;
+    double* grad = band + (size_t)n * BROW;
+    double* work = grad + n;
+    double* acc = work + (size_t)n * (BROW + 1);
+    double hacc[4];
+    int iters = 0;
+    double cost = 0.0;
+    auto fail = [&](cudaError_t e, const char* what) {
+        rc = cuda_fail(e, what);
+        return rc;
+    };
+    auto loss_at = [&](const double* qq, double& out) -> int {
+        cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double), st);
+        if (e != cudaSuccess) return fail(e, "memset");
+        dpc_assemble_kernel<false><<<pb.P - 1, 256, 0, st>>>(pb, qq, band, grad, acc);
+        dpc_regular_kernel<false><<<blocks_for(pb.P, 128), 128, 0, st>>>(pb, qq, band, grad, acc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(e, "dpc loss");
+        e = cudaMemcpyAsync(hacc, acc, sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(e, "dpc loss readback");
+        out = hacc[0];
+        return SAS_OK;
+    };
+    rc = setup(pb, S, d_vy, d_vz, st);
+    if (rc == SAS_OK) rc = loss_at(S.q, cost);
+    double mu = 1e-3;
+    for (int it = 0; rc == SAS_OK && it < max_iter; ++it) {
+        // normal equations at the current nodes
+        cudaError_t e = cudaMemsetAsync(band, 0, sizeof(double) * ((size_t)n * BROW + n), st);
+        if (e != cudaSuccess) {
+            fail(e, "memset");
+            break;
+        }
+        e = cudaMemsetAsync(acc, 0, sizeof(double), st);
+        dpc_assemble_kernel<true><<<pb.P - 1, 256, 0, st>>>(pb, S.q, band, grad, acc);
+        dpc_regular_kernel<true><<<blocks_for(pb.P, 128), 128, 0, st>>>(pb, S.q, band, grad, acc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            fail(e, "dpc assemble");
+            break;
+        }
+        bool accepted = false, stalled = false;
+        double trial = cost;
+        for (int tries = 0; tries < 40 && rc == SAS_OK; ++tries) {
+            dpc_solve_kernel<<<1, 1, 0, st>>>(n, band, grad, mu, work, S.q, q_try, acc);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                fail(e, "dpc solve");
+                break;
+            }
+            if (hacc[1] != 0.0) {   // not positive definite at this damping
+                mu *= 10.0;
+                continue;
+            }
+            const double step = hacc[2];
+            if (loss_at(q_try, trial) != SAS_OK) break;
+            if (trial <= cost) {
+                std::swap(S.q, q_try);
+                accepted = true;
+                stalled = (cost - trial) <= 1e-14 * cost || step == 0.0;
+                mu = std::max(mu / 3.0, 1e-15);
+                break;
+            }
+            mu *= 4.0;
+        }
+        if (rc != SAS_OK || !accepted) break;
+        ++iters;
+        cost = trial;
+        if (stalled) break;
+    }
+    if (rc == SAS_OK) {
+        dpc_velocities_kernel<<<blocks_for(pb.P, 128), 128, 0, st>>>(pb, S.q, d_vy, d_vz);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "dpc velocities");
+    }
+    // S.q may point at the second node buffer after swaps: free the allocation base
+    cudaFreeAsync(S.base, st);
+    if (rc == SAS_OK) {
+        if (h_loss) *h_loss = cost;
+        if (h_iters) *h_iters = iters;
+    }
+    return rc;
+}

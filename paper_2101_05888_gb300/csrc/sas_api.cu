@@ -81,22 +81,14 @@ int encode_echo_map(CUtensorMap* map, const void* base, int elem_bytes, int Ns, 
 
 // ---------------------------------------------------------------------------
 // Sensor positions (Sec. II-C): x_TX,i = p_i + dp_i + R_i l_TX, x_RX,i,c = p_i + dp_i + R_i l_c,
-// with R_i the attitude rotation of Eq. 2 (roll phi, pitch theta, yaw psi):
-//   [ ct cps,  cps st sph - cph sps,  cph cps st + sph sps ]
-//   [ ct sps,  cph cps + st sph sps,  cph st sps - cps sph ]
-//   [ -st,     ct sph,                ct cph               ]
+// with R_i the attitude rotation of Eq. 2 (attitude_rotation).
 __global__ void geometry_kernel(int P, int C, const double* __restrict__ pos, const double* __restrict__ att,
                                 const double* __restrict__ lever, const double* __restrict__ off,
                                 double* __restrict__ tx, double* __restrict__ rx, float* __restrict__ rotc) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
-    double sph, cph, sth, cth, sps, cps;
-    sincos(att[3 * i + 0], &sph, &cph);
-    sincos(att[3 * i + 1], &sth, &cth);
-    sincos(att[3 * i + 2], &sps, &cps);
-    const double R[9] = {cth * cps, cps * sth * sph - cph * sps, cph * cps * sth + sph * sps,
-                         cth * sps, cph * cps + sth * sph * sps, cph * sth * sps - cps * sph,
-                         -sth,      cth * sph,                   cth * cph};
+    double R[9];
+    attitude_rotation(att[3 * i + 0], att[3 * i + 1], att[3 * i + 2], R);
     const double b0 = pos[3 * i] + off[3 * i], b1 = pos[3 * i + 1] + off[3 * i + 1],
                  b2 = pos[3 * i + 2] + off[3 * i + 2];
     // columns 0 and 1 of R: body-frame components (R^T v).x, (R^T v).y of a NED vector v

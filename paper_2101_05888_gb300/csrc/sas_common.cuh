@@ -31,6 +31,21 @@ enum : uint32_t { DEV_TIMEOUT = 1u };
 //   w_m(f) = sum_{p<NP} coef[m][p] g^p,  g = f - 1/2,
 // so the interpolated value is a polynomial in g whose coefficients are FIR
 // outputs of the echo:  s = sum_p g^p E_p[i0],  E_p[i] = sum_m coef[m][p] e[i + k_m].
+// ---------------------------------------------------------------------------
+// Attitude rotation of Eq. 2 (roll phi, pitch theta, yaw psi), row-major R:
+//   [ ct cps,  cps st sph - cph sps,  cph cps st + sph sps ]
+//   [ ct sps,  cph cps + st sph sps,  cph st sps - cps sph ]
+//   [ -st,     ct sph,                ct cph               ]
+__device__ __forceinline__ void attitude_rotation(double roll, double pitch, double yaw, double R[9]) {
+    double sph, cph, sth, cth, sps, cps;
+    sincos(roll, &sph, &cph);
+    sincos(pitch, &sth, &cth);
+    sincos(yaw, &sps, &cps);
+    R[0] = cth * cps; R[1] = cps * sth * sph - cph * sps; R[2] = cph * cps * sth + sph * sps;
+    R[3] = cth * sps; R[4] = cph * cps + sth * sph * sps; R[5] = cph * sth * sps - cps * sph;
+    R[6] = -sth;      R[7] = cth * sph;                   R[8] = cth * cph;
+}
+
 constexpr int TAPS = 8;
 constexpr int NP = 6;            // polynomial degree 5
 struct FarrowCoef {
