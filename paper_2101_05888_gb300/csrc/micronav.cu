@@ -46,35 +46,61 @@ __device__ __forceinline__ float2 echo_at<__nv_bfloat162>(const __nv_bfloat162* 
 
 // One warp per measurement m = ((i (C - shift) + c) K + k); lane l holds the
 // lag tau = l - L.  e1 = ping i, receiver c + shift; e2 = ping i + 1, receiver c.
+// The window is walked in chunks of DPC_CH samples: the warp stages e2[n ..
+// n + CH) and e1[n - L .. n + CH + L) in shared memory with coalesced loads
+// (zero outside the rows), then every lane reads e2 (broadcast) and its
+// shifted e1 (consecutive lanes, consecutive words) from there.
+constexpr int DPC_CH = 256;
+constexpr int DPC_MAXL = 15;
 template <typename ET>
 __global__ void __launch_bounds__(32 * DPC_WARPS)
     dpc_delay_kernel(const ET* __restrict__ echo, const float* __restrict__ scale, int C, int Ns, int shift,
-                     const int* __restrict__ centres, int K, int W, int L, long long M, double fs, double fc,
-                     double* __restrict__ coarse, double* __restrict__ fine, double* __restrict__ rho) {
+                     const int* __restrict__ centres, int K, int W, int L, long long M, float inv_fs,
+                     float inv_wfc, double* __restrict__ coarse, double* __restrict__ fine,
+                     double* __restrict__ rho) {
+    __shared__ float2 stage[DPC_WARPS][2 * DPC_CH + 2 * DPC_MAXL];
     const long long m = (long long)blockIdx.x * DPC_WARPS + (threadIdx.x >> 5);
     if (m >= M) return;   // whole warps
     const int lane = threadIdx.x & 31;
+    float2* s2 = stage[threadIdx.x >> 5];          // [DPC_CH] e2
+    float2* s1 = s2 + DPC_CH;                      // [DPC_CH + 2L] e1 from n - L
     const int nc = C - shift;
     const int k = (int)(m % K);
     const long long pr = m / K;
     const int c = (int)(pr % nc);
     const long long i = pr / nc;
     const size_t r1 = (size_t)i * C + c + shift, r2 = (size_t)(i + 1) * C + c;
-    const float s1 = scale ? scale[r1] : 1.f, s2 = scale ? scale[r2] : 1.f;
+    const float sc1 = scale ? scale[r1] : 1.f, sc2 = scale ? scale[r2] : 1.f;
     const ET* e1 = echo + r1 * (size_t)Ns;
     const ET* e2 = echo + r2 * (size_t)Ns;
     const int n0 = centres[k] - W / 2;
     const int tau = lane - L;
     const bool lag = lane <= 2 * L;
     float ar = 0.f, ai = 0.f, p1 = 0.f, p2 = 0.f;   // R(tau); sum |e1[n - tau]|^2; sum |e2[n]|^2
-    for (int n = n0; n < n0 + W; ++n) {
-        const float2 b2 = (n >= 0 && n < Ns) ? echo_at<ET>(e2, n, s2) : make_float2(0.f, 0.f);
-        const int n1 = n - tau;
-        const float2 b1 = (lag && n1 >= 0 && n1 < Ns) ? echo_at<ET>(e1, n1, s1) : make_float2(0.f, 0.f);
-        ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));       // e2 conj(e1)
-        ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
-        p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
-        p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
+    for (int nb = n0; nb < n0 + W; nb += DPC_CH) {
+        const int len = min(DPC_CH, n0 + W - nb);
+        __syncwarp();
+        for (int j = lane; j < len; j += 32) {
+            const int n = nb + j;
+            s2[j] = (n >= 0 && n < Ns) ? echo_at<ET>(e2, n, sc2) : make_float2(0.f, 0.f);
+        }
+        for (int j = lane; j < len + 2 * L; j += 32) {
+            const int n = nb - L + j;
+            s1[j] = (n >= 0 && n < Ns) ? echo_at<ET>(e1, n, sc1) : make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+        if (lag) {
+            // e1[n - tau] = s1[(n - nb) + L - tau]
+            const float2* a1 = s1 + (L - tau);
+#pragma unroll 4
+            for (int j = 0; j < len; ++j) {
+                const float2 b2 = s2[j], b1 = a1[j];
+                ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));       // e2 conj(e1)
+                ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
+                p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
+                p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
+            }
+        }
     }
     const float mag = lag ? sqrtf(fmaf(ar, ar, ai * ai)) : -1.f;
     // largest |R|, the lowest lag on ties
@@ -103,11 +129,13 @@ __global__ void __launch_bounds__(32 * DPC_WARPS)
             Rr = rr0 + 0.5f * d * (rrp - rrm) + 0.5f * d * d * (rrp - 2.f * rr0 + rrm);
             Ri = ri0 + 0.5f * d * (rip - rim) + 0.5f * d * d * (rip - 2.f * ri0 + rim);
         }
-        if (coarse) coarse[m] = ((double)(bl - L) + (double)d) / fs;
-        if (fine) fine[m] = -(double)atan2f(Ri, Rr) / (2.0 * M_PI * fc);
+        // FP32 epilogue (FP64 arithmetic is slow on this part; the outputs
+        // carry FP32 accuracy anyway), widened on the store
+        if (coarse) coarse[m] = (double)(((float)(bl - L) + d) * inv_fs);
+        if (fine) fine[m] = (double)(-atan2f(Ri, Rr) * inv_wfc);
         if (rho) {
-            const double den = sqrt((double)p2 * (double)q1);
-            rho[m] = den > 0.0 ? (double)best / den : 0.0;
+            const float den2 = p2 * q1;
+            rho[m] = den2 > 0.f ? (double)(best * rsqrtf(den2)) : 0.0;
         }
     }
 }
@@ -445,42 +473,60 @@ __global__ void dpc_regular_kernel(Prob pb, const double* q, double* band, doubl
 }
 
 // Damped banded Cholesky solve of (N + mu diag N) delta = -g and the trial
-// nodes q + delta (one thread; the system is small and banded).  acc[1] = 1
-// when the factorisation fails; acc[2] = max |delta|.
-__global__ void dpc_solve_kernel(int n, const double* band, const double* grad, double mu, double* work,
-                                 const double* q, double* q_try, double* acc) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double* U = work;            // [n][BROW]: U(j, j + d), A = U^T U
-    double* y = work + (size_t)n * BROW;
-    acc[1] = 0.0;
+// nodes q + delta, by one warp: row j of U (A = U^T U) has its BROW entries
+// computed by lanes 0 .. BANDW from the previous BANDW rows, held in a ring in
+// shared memory; the forward substitution U^T y = -g follows row by row; the
+// back substitution runs on one lane.  acc[1] = 1 when the factorisation
+// fails; acc[2] = max |delta|.
+__global__ void __launch_bounds__(32) dpc_solve_kernel(int n, const double* band, const double* grad, double mu,
+                                                       double* work, const double* q, double* q_try, double* acc) {
+    __shared__ double ring[BROW][BROW];   // ring[r % BROW][d] = U(r, r + d) for the last rows r
+    __shared__ double yr[BROW];           // y_r for the last rows r
+    const int d = threadIdx.x;
+    double* U = work;                     // [n][BROW], diagonal stored inverted
+    double* y = work + (size_t)n * BROW;  // [n]
+    if (d == 0) acc[1] = 0.0;
     for (int j = 0; j < n; ++j) {
-        for (int d = 0; d <= BANDW && j + d < n; ++d) {
-            double s = band[bidx(j, j + d)];
+        double s = 0.0;
+        if (d <= BANDW && j + d < n) {
+            s = band[bidx(j, j + d)];
             if (d == 0) s += mu * (band[bidx(j, j)] + 1e-12);   // Marquardt's scaling, Levenberg's floor
-            for (int k = max(0, j + d - BANDW); k < j; ++k) s -= U[(size_t)k * BROW + (j - k)] * U[(size_t)k * BROW + (j + d - k)];
-            if (d == 0) {
-                if (!(s > 0.0)) {
-                    acc[1] = 1.0;
-                    return;
-                }
-                U[(size_t)j * BROW] = sqrt(s);
-            } else {
-                U[(size_t)j * BROW + d] = s / U[(size_t)j * BROW];
-            }
+            for (int k = max(0, j + d - BANDW); k < j; ++k) s -= ring[k % BROW][j - k] * ring[k % BROW][j + d - k];
         }
+        // forward substitution term of row j: -g_j - sum_k U(k, j) y_k (lane 0)
+        double t = 0.0;
+        if (d == 0) {
+            t = -grad[j];
+            for (int k = max(0, j - BANDW); k < j; ++k) t -= ring[k % BROW][j - k] * yr[k % BROW];
+        }
+        const double djj = __shfl_sync(FULL, s, 0);
+        if (!(djj > 0.0)) {
+            if (d == 0) acc[1] = 1.0;
+            return;
+        }
+        // one FP64 reciprocal square root per row (FP64 square roots and
+        // divisions are long sequences on this part); U(j, j) = djj / sqrt(djj)
+        const double inv = rsqrt(djj);
+        __syncwarp();   // every read of the ring slot of row j - BROW is done
+        if (d <= BANDW && j + d < n) {
+            const double u = d == 0 ? djj * inv : s * inv;
+            ring[j % BROW][d] = u;
+            U[(size_t)j * BROW + d] = d == 0 ? inv : u;   // the diagonal kept as 1 / U(j, j)
+        }
+        if (d == 0) {
+            const double yj = t * inv;
+            yr[j % BROW] = yj;
+            y[j] = yj;
+        }
+        __syncwarp();
     }
-    // U^T y = -g
-    for (int j = 0; j < n; ++j) {
-        double s = -grad[j];
-        for (int k = max(0, j - BANDW); k < j; ++k) s -= U[(size_t)k * BROW + (j - k)] * y[k];
-        y[j] = s / U[(size_t)j * BROW];
-    }
+    if (d != 0) return;
     // U delta = y
     double dmax = 0.0;
     for (int j = n - 1; j >= 0; --j) {
         double s = y[j];
-        for (int d = 1; d <= BANDW && j + d < n; ++d) s -= U[(size_t)j * BROW + d] * y[j + d];
-        y[j] = s / U[(size_t)j * BROW];
+        for (int e = 1; e <= BANDW && j + e < n; ++e) s -= U[(size_t)j * BROW + e] * y[j + e];
+        y[j] = s * U[(size_t)j * BROW];
         dmax = fmax(dmax, fabs(y[j]));
         q_try[j] = q[j] + y[j];
     }
@@ -560,7 +606,7 @@ using namespace sas;
 
 extern "C" int sas_dpc_delays(sas_geometry_t h, int32_t shift, const int32_t* d_centres, int32_t K, int32_t W,
                               int32_t max_lag, double* d_coarse, double* d_fine, double* d_rho, void* stream) {
-    if (!h || !d_centres || K < 1 || W < 1 || W > 4096 || max_lag < 0 || max_lag > 15 || shift < 0 ||
+    if (!h || !d_centres || K < 1 || W < 1 || W > 4096 || max_lag < 0 || max_lag > DPC_MAXL || shift < 0 ||
         shift >= h->C || h->P < 2) {
         set_error("sas_dpc_delays: bad argument");
         return SAS_ERR_ARG;
@@ -572,21 +618,21 @@ extern "C" int sas_dpc_delays(sas_geometry_t h, int32_t shift, const int32_t* d_
     const long long M = (long long)(h->P - 1) * (h->C - shift) * K;
     cudaStream_t st = (cudaStream_t)stream;
     const int grid = blocks_for(M, DPC_WARPS);
-    const double fs = h->sig.fs, fc = h->sig.fc;
+    const float inv_fs = (float)(1.0 / h->sig.fs), inv_wfc = (float)(1.0 / (2.0 * M_PI * h->sig.fc));
     switch (h->echo_dtype) {
         case SAS_ECHO_C64:
             dpc_delay_kernel<float2><<<grid, 32 * DPC_WARPS, 0, st>>>((const float2*)h->d_echo, nullptr, h->C, h->Ns,
-                                                                      shift, d_centres, K, W, max_lag, M, fs, fc,
+                                                                      shift, d_centres, K, W, max_lag, M, inv_fs, inv_wfc,
                                                                       d_coarse, d_fine, d_rho);
             break;
         case SAS_ECHO_C32_F16:
             dpc_delay_kernel<__half2><<<grid, 32 * DPC_WARPS, 0, st>>>((const __half2*)h->d_echo, h->d_scale, h->C,
-                                                                       h->Ns, shift, d_centres, K, W, max_lag, M, fs,
-                                                                       fc, d_coarse, d_fine, d_rho);
+                                                                       h->Ns, shift, d_centres, K, W, max_lag, M, inv_fs,
+                                                                       inv_wfc, d_coarse, d_fine, d_rho);
             break;
         default:
             dpc_delay_kernel<__nv_bfloat162><<<grid, 32 * DPC_WARPS, 0, st>>>(
-                (const __nv_bfloat162*)h->d_echo, h->d_scale, h->C, h->Ns, shift, d_centres, K, W, max_lag, M, fs, fc,
+                (const __nv_bfloat162*)h->d_echo, h->d_scale, h->C, h->Ns, shift, d_centres, K, W, max_lag, M, inv_fs, inv_wfc,
                 d_coarse, d_fine, d_rho);
             break;
     }
@@ -702,7 +748,7 @@ extern "C" int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_
         bool accepted = false, stalled = false;
         double trial = cost;
         for (int tries = 0; tries < 40 && rc == SAS_OK; ++tries) {
-            dpc_solve_kernel<<<1, 1, 0, st>>>(n, band, grad, mu, work, S.q, q_try, acc);
+            dpc_solve_kernel<<<1, 32, 0, st>>>(n, band, grad, mu, work, S.q, q_try, acc);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -152,6 +152,14 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
     return *reinterpret_cast<float2*>(&rd);
 }
+// The value of x, opaque to the compiler: it cannot be recomputed at its uses
+// from the (FP64) expression that produced it, so it stays in a register.
+__device__ __forceinline__ float opaque(float x) {
+    float y;
+    asm volatile("mov.b32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // elementwise max / min of pairs (two scalar operations)
 __device__ __forceinline__ float2 fmax2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 __device__ __forceinline__ float2 fmin2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }

@@ -545,19 +545,24 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // seabed refraction: the slots (pixel layers in 3D; all of them in 2D)
     // strictly below the interface, and the depth Zr of the reference point
     // x_r = (x0, y0, Zr): the centre if it is below, else the deepest layer
-    unsigned bmask = 0u;
-    double Zr = Zc;
-    if constexpr (REFRACT) {
+    // (one thread derives them in FP64 and hands them to the block through
+    // shared memory: recomputing FP64 terms at their uses would load the
+    // slow FP64 pipe)
+    __shared__ unsigned s_bmask;
+    __shared__ double s_zr;
+    if (REFRACT && tid == 0) {
+        unsigned bm = 0u;
         double zdeep = -1.0e300;
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < PX; ++s) {
             const double zs = DIM3 ? layer_z(p, tz0 + s) : p.z0;
             if (zs > p.z_int) {
-                bmask |= 1u << s;
+                bm |= 1u << s;
                 zdeep = fmax(zdeep, zs);
             }
         }
-        if (!(Zc > p.z_int)) Zr = zdeep;
+        s_bmask = bm;
+        s_zr = Zc > p.z_int ? Zc : zdeep;
     }
 
     if (tid == 0) {
@@ -572,6 +577,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     }
     if (tid < TAPS * NP) coef_s[tid] = (&p.coef->c[0][0])[tid];
     __syncthreads();
+    const unsigned bmask = REFRACT ? s_bmask : 0u;
+    const double Zr = REFRACT ? s_zr : Zc;
 
     if (warp == 0) {
         // ================= producer =================
@@ -807,10 +814,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     {
         int lx, ly, lz;
         T::pixel(ct, 0, lx, ly, lz);
-        dxv = (float)((tx0 + lx - cx) * p.dx);
-        dyv_c = (float)((ty0 + ly - cy) * p.dy);
-        dv0 = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : dyv_c;
-        dvstep = DIM3 ? (float)p.dz : (float)(4.0 * p.dy);
+        // formed in FP64, kept opaque so that they are not re-derived in FP64 at their uses
+        dxv = opaque((float)((tx0 + lx - cx) * p.dx));
+        dyv_c = opaque((float)((ty0 + ly - cy) * p.dy));
+        dv0 = DIM3 ? opaque((float)((tz0 + lz - cz) * p.dz)) : dyv_c;
+        dvstep = DIM3 ? opaque((float)p.dz) : opaque((float)(4.0 * p.dy));
         const float d2c = fixed_d2<DIM3>(dxv, dyv_c);
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
@@ -833,12 +841,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     uint32_t tmask = 0xffu;                         // pixels the current ping's transmitter sees
     // seabed refraction: x_r's depth below the interface and offset from the
     // tile centre; |d_h|^2 of this thread's column (3D)
-    float r_br = 0.f, r_zoff = 0.f, r_d2h = 0.f;
-    if constexpr (REFRACT) {
-        r_br = (float)(Zr - p.z_int);
-        r_zoff = (float)(Zr - Zc);
-        r_d2h = fixed_d2<true>(dxv, dyv_c);
+    __shared__ float s_rf[2];
+    if (REFRACT && ct == 0) {
+        s_rf[0] = (float)(Zr - p.z_int);
+        s_rf[1] = (float)(Zr - Zc);
     }
+    if (REFRACT) named_bar_sync(BAR_CONS, NCONS);
+    const float r_br = REFRACT ? s_rf[0] : 0.f, r_zoff = REFRACT ? s_rf[1] : 0.f;
+    const float r_d2h = REFRACT ? fixed_d2<true>(dxv, dyv_c) : 0.f;
     // depth below the interface of slot s, and its offset from x_r's depth
     auto slot_depth = [&](int s, float& b, float& db) {
         db = DIM3 ? PXS(dvp, s) - r_zoff : 0.f;
