@@ -90,16 +90,34 @@ __global__ void __launch_bounds__(32 * DPC_WARPS)
         }
         __syncwarp();
         if (lag) {
-            // e1[n - tau] = s1[(n - nb) + L - tau]
+            // e1[n - tau] = s1[(n - nb) + L - tau]; two interleaved partial sums
+            // (even and odd samples) halve the FMA dependency chains
             const float2* a1 = s1 + (L - tau);
-#pragma unroll 4
-            for (int j = 0; j < len; ++j) {
-                const float2 b2 = s2[j], b1 = a1[j];
+            float br_ = 0.f, bi_ = 0.f, q1_ = 0.f, q2_ = 0.f;
+            int j = 0;
+#pragma unroll 2
+            for (; j + 1 < len; j += 2) {
+                const float2 b2 = s2[j], b1 = a1[j], c2 = s2[j + 1], c1 = a1[j + 1];
                 ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));       // e2 conj(e1)
                 ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
                 p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
                 p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
+                br_ = fmaf(c2.x, c1.x, fmaf(c2.y, c1.y, br_));
+                bi_ = fmaf(c2.y, c1.x, fmaf(-c2.x, c1.y, bi_));
+                q1_ = fmaf(c1.x, c1.x, fmaf(c1.y, c1.y, q1_));
+                q2_ = fmaf(c2.x, c2.x, fmaf(c2.y, c2.y, q2_));
             }
+            if (j < len) {
+                const float2 b2 = s2[j], b1 = a1[j];
+                ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));
+                ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
+                p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
+                p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
+            }
+            ar += br_;
+            ai += bi_;
+            p1 += q1_;
+            p2 += q2_;
         }
     }
     const float mag = lag ? sqrtf(fmaf(ar, ar, ai * ai)) : -1.f;
