@@ -491,59 +491,82 @@ __global__ void dpc_regular_kernel(Prob pb, const double* q, double* band, doubl
 }
 
 // Damped banded Cholesky solve of (N + mu diag N) delta = -g and the trial
-// nodes q + delta, by one warp: row j of U (A = U^T U) has its BROW entries
-// computed by lanes 0 .. BANDW from the previous BANDW rows, held in a ring in
-// shared memory; the forward substitution U^T y = -g follows row by row; the
-// back substitution runs on one lane.  acc[1] = 1 when the factorisation
-// fails; acc[2] = max |delta|.
+// nodes q + delta, by one warp, right-looking: the pending entries of the next
+// BANDW + 1 rows sit in a ring in shared memory; row j's factor U(j, j + d) is
+// one multiplication by 1 / sqrt(pending diagonal) per lane, and its rank-1
+// update of the trailing 7 x 7 triangle is one FMA on each of 28 lanes, so the
+// critical path per row is one reciprocal square root and a few FP64
+// operations (no sequential dot products).  The forward substitution
+// U^T y = -g rides along (its right-hand side updated the same way); the back
+// substitution runs on one lane.  acc[1] = 1 when the factorisation fails;
+// acc[2] = max |delta|.
 __global__ void __launch_bounds__(32) dpc_solve_kernel(int n, const double* band, const double* grad, double mu,
                                                        double* work, const double* q, double* q_try, double* acc) {
-    __shared__ double ring[BROW][BROW];   // ring[r % BROW][d] = U(r, r + d) for the last rows r
-    __shared__ double yr[BROW];           // y_r for the last rows r
-    const int d = threadIdx.x;
-    double* U = work;                     // [n][BROW], diagonal stored inverted
-    double* y = work + (size_t)n * BROW;  // [n]
-    if (d == 0) acc[1] = 0.0;
+    __shared__ double Pm[BROW][BROW];   // Pm[r % BROW][d] = pending A(r, r + d), rows j .. j + BANDW
+    __shared__ double tv[BROW];         // pending right-hand side of those rows
+    const int lane = threadIdx.x;
+    double* U = work;                   // [n][BROW], the diagonal stored inverted
+    double* y = work + (size_t)n * BROW;
+    // lane -> entry (j + ta, j + tb) of the trailing triangle, 1 <= ta <= tb <= BANDW
+    int ta = 1, e = lane;
+    while (ta <= BANDW && e >= BANDW - ta + 1) {
+        e -= BANDW - ta + 1;
+        ++ta;
+    }
+    const int tb = ta + e;
+    const bool upd = lane < BANDW * (BANDW + 1) / 2;
+    // row r of the damped matrix and of -g (lanes 0 .. BANDW; zero past the end)
+    auto fetch = [&](int r, double& a, double& t) {
+        a = 0.0;
+        t = 0.0;
+        if (lane <= BANDW && r < n && r + lane < n) {
+            a = band[bidx(r, r + lane)];
+            if (lane == 0) {
+                a += mu * (a + 1e-12);   // Marquardt's scaling, Levenberg's floor
+                t = -grad[r];
+            }
+        }
+    };
+    if (lane == 0) acc[1] = 0.0;
+    for (int r = 0; r < BROW; ++r) {
+        double a, t;
+        fetch(r, a, t);
+        if (lane <= BANDW) Pm[r][lane] = a;
+        if (lane == 0) tv[r] = t;
+    }
+    __syncwarp();
     for (int j = 0; j < n; ++j) {
-        double s = 0.0;
-        if (d <= BANDW && j + d < n) {
-            s = band[bidx(j, j + d)];
-            if (d == 0) s += mu * (band[bidx(j, j)] + 1e-12);   // Marquardt's scaling, Levenberg's floor
-            for (int k = max(0, j + d - BANDW); k < j; ++k) s -= ring[k % BROW][j - k] * ring[k % BROW][j + d - k];
-        }
-        // forward substitution term of row j: -g_j - sum_k U(k, j) y_k (lane 0)
-        double t = 0.0;
-        if (d == 0) {
-            t = -grad[j];
-            for (int k = max(0, j - BANDW); k < j; ++k) t -= ring[k % BROW][j - k] * yr[k % BROW];
-        }
-        const double djj = __shfl_sync(FULL, s, 0);
+        double an, tn;
+        fetch(j + BROW, an, tn);        // issued early: lands during the square root
+        const int sj = j % BROW;
+        const double djj = Pm[sj][0];
         if (!(djj > 0.0)) {
-            if (d == 0) acc[1] = 1.0;
+            if (lane == 0) acc[1] = 1.0;
             return;
         }
-        // one FP64 reciprocal square root per row (FP64 square roots and
-        // divisions are long sequences on this part); U(j, j) = djj / sqrt(djj)
         const double inv = rsqrt(djj);
-        __syncwarp();   // every read of the ring slot of row j - BROW is done
-        if (d <= BANDW && j + d < n) {
-            const double u = d == 0 ? djj * inv : s * inv;
-            ring[j % BROW][d] = u;
-            U[(size_t)j * BROW + d] = d == 0 ? inv : u;   // the diagonal kept as 1 / U(j, j)
+        double u = 0.0;
+        if (lane <= BANDW && j + lane < n) {
+            u = lane == 0 ? djj * inv : Pm[sj][lane] * inv;
+            U[(size_t)j * BROW + lane] = lane == 0 ? inv : u;
         }
-        if (d == 0) {
-            const double yj = t * inv;
-            yr[j % BROW] = yj;
-            y[j] = yj;
-        }
+        const double yj = tv[sj] * inv;
+        if (lane == 0) y[j] = yj;
+        const double ua = __shfl_sync(FULL, u, ta & 31), ub = __shfl_sync(FULL, u, tb & 31);
+        __syncwarp();
+        if (upd && j + tb < n) Pm[(j + ta) % BROW][tb - ta] -= ua * ub;
+        if (lane >= 1 && lane <= BANDW && j + lane < n) tv[(j + lane) % BROW] -= u * yj;
+        // row j's slot takes row j + BROW (untouched by rows <= j: it lies beyond their band)
+        if (lane <= BANDW) Pm[sj][lane] = an;
+        if (lane == 0) tv[sj] = tn;
         __syncwarp();
     }
-    if (d != 0) return;
+    if (lane != 0) return;
     // U delta = y
     double dmax = 0.0;
     for (int j = n - 1; j >= 0; --j) {
         double s = y[j];
-        for (int e = 1; e <= BANDW && j + e < n; ++e) s -= U[(size_t)j * BROW + e] * y[j + e];
+        for (int d = 1; d <= BANDW && j + d < n; ++d) s -= U[(size_t)j * BROW + d] * y[j + d];
         y[j] = s * U[(size_t)j * BROW];
         dmax = fmax(dmax, fabs(y[j]));
         q_try[j] = q[j] + y[j];

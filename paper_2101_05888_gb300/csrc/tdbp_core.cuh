@@ -203,9 +203,10 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
 //  * otherwise: E0..E5 FP32 pairs.
 //  * TAIL16 (off): E0..E3 FP32 pairs (32 B), then E4, E5 as BF16 pairs (8 B),
 //    so that a pixel reads 40 B: 15 % fewer shared-memory wavefronts, 15 %
-//    more instructions (the BF16 unpacking) and 3 % slower on the stripmap
-//    workload, where the issue rate binds as much as the shared pipe.  (BF16
-//    for E4, E5 changes the interpolated value by 3e-6 rms relative.)
+//    more instructions (the BF16 unpacking) and 1.3 % slower on the stripmap
+//    workload (641.9 against 650.0 G updates/s), where the issue rate binds as
+//    much as the shared pipe.  (BF16 for E4, E5 changes the interpolated
+//    value by 3e-6 rms relative.)
 
 
 // FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
