@@ -207,6 +207,12 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
 //    workload (641.9 against 650.0 G updates/s), where the issue rate binds as
 //    much as the shared pipe.  (BF16 for E4, E5 changes the interpolated
 //    value by 3e-6 rms relative.)
+//  (Also measured and dropped: each sample interval in two halves with a
+//  degree-3 polynomial on each, one 32-B row per half-sample position: 8
+//  instead of 12 wavefronts and two fewer FMAs per pixel, 3.6e-5 rms
+//  interpolation error, but 514 G updates/s: rows 4 half-samples apart share
+//  their banks, so neighbouring pixels' loads conflict (1.5e10 conflicts per
+//  64-ping launch against 1.6e7).)
 
 
 // FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
