@@ -43,7 +43,7 @@ UPDATES_PER_CLK_PER_SM = 4.0
 # ncu capture of the same kernel on 64 pings of the stripmap workload: reads
 # 128.3 MB (scaled by 2048 / 64 pings: each ping's rows are read once) plus the
 # 114.5 MB image write.  Only the configurations captured are listed.
-TRAFFIC_BYTES = {("stripmap_2d", "c64"): 128.3e6 * 2048 / 64 + 114.5e6}
+TRAFFIC_BYTES = {("stripmap_2d", "c64"): 129.5e6 * 2048 / 64 + 114.6e6}
 
 
 def parse():
