@@ -447,6 +447,71 @@ __device__ __forceinline__ float refr_leg_diff(const KParams& p, const float4 r0
     return fmaf(fmaf(Nw, Ds, Ns * Dw), rcp_sfu(Dw * Ds), r2.z);
 }
 
+// The same for two pixels at once (slots 2k, 2k+1), packed FP32x2: two
+// Newton steps for both, further steps only while some lane of the warp has
+// not converged (callers are warp-uniform here); the last step's q is kept
+// for the slower leg's run (the crossing moves by less than the tolerance in
+// that step, and the length is stationary in it).
+__device__ __forceinline__ float2 refr_leg_diff2(const KParams& p, const float4 r0, const float4 r1,
+                                                 const float4 r2, float2 rho, float2 drho, float2 b, float2 db,
+                                                 float br) {
+    const float a = r0.x;
+    const bool fsed = p.refr_fast_sed;
+    const float2 a2 = make_float2(a, a);
+    const float2 A = fsed ? b : a2, B = fsed ? a2 : b;
+    const float2 zero = make_float2(0.f, 0.f);
+    const float2 isM = make_float2(p.refr_isM, p.refr_isM), M2 = make_float2(p.refr_M, p.refr_M);
+    const float2 r22 = make_float2(p.refr_r2, p.refr_r2);
+    const float2 flo = fmax2(ffma2(make_float2(-B.x, -B.y), isM, rho), zero);
+    float2 f = ffma2(make_float2(r2.x, r2.x), drho, ffma2(make_float2(r2.y, r2.y), db, make_float2(r1.w, r1.w)));
+    f = fmin2(fmax2(f, flo), rho);
+    const float2 iA = make_float2(rcp_sfu(A.x), rcp_sfu(A.y));
+    const float2 vlo = fmul2(flo, iA);
+    float2 v = fmul2(f, iA), q = zero, Sd = zero, dv = zero;
+    const float2 Br2 = fmul2(B, r22);
+    auto step = [&]() {
+        const float2 t = ffma2(M2, fmul2(v, v), r22);
+        q = make_float2(rsqrt_sfu(t.x), rsqrt_sfu(t.y));
+        const float2 F = ffma2(A, v, ffma2(fmul2(B, v), q, make_float2(-rho.x, -rho.y)));
+        Sd = fmul2(Br2, fmul2(q, fmul2(q, q)));
+        const float2 den = fadd2(Sd, A);
+        dv = fmul2(F, make_float2(rcp_sfu(den.x), rcp_sfu(den.y)));
+        v = fmax2(fsub2(v, dv), vlo);
+    };
+    auto converged = [&]() {
+        return fabsf(dv.x) * fminf(A.x, Sd.x) < p.refr_tol && fabsf(dv.y) * fminf(A.y, Sd.y) < p.refr_tol;
+    };
+    step();
+    step();
+    for (int it = 2; it < 16 && __any_sync(__activemask(), !converged()); ++it) step();
+    const float2 fast = fmul2(A, v), slow = fmul2(fmul2(B, v), q);
+    float2 dxi, dsig;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const bool use_fast = (j ? A.y < Sd.y : A.x < Sd.x);
+        const float fj = j ? fast.y : fast.x, sj = j ? slow.y : slow.x, dr = j ? drho.y : drho.x;
+        float& dx = j ? dxi.y : dxi.x;
+        float& ds = j ? dsig.y : dsig.x;
+        if (fsed) {
+            ds = use_fast ? fj - r1.x : dr - (sj - r0.w);
+            dx = dr - ds;
+        } else {
+            dx = use_fast ? fj - r0.w : dr - (sj - r1.x);
+            ds = dr - dx;
+        }
+    }
+    const float2 xi = fadd2(make_float2(r0.w, r0.w), dxi), sg = fadd2(make_float2(r1.x, r1.x), dsig);
+    const float2 W2 = ffma2(xi, xi, make_float2(a * a, a * a)), V2 = ffma2(sg, sg, fmul2(b, b));
+    const float2 Dw = ffma2(W2, make_float2(rsqrt_sfu(W2.x), rsqrt_sfu(W2.y)), make_float2(r1.y, r1.y));
+    const float2 Ds = ffma2(V2, make_float2(rsqrt_sfu(V2.x), rsqrt_sfu(V2.y)), make_float2(r1.z, r1.z));
+    const float2 two = make_float2(2.f, 2.f);
+    const float2 Nw = fmul2(dxi, ffma2(two, make_float2(r0.w, r0.w), dxi));
+    const float2 Ns = fmul2(make_float2(p.refr_nf, p.refr_nf),
+                            ffma2(dsig, ffma2(two, make_float2(r1.x, r1.x), dsig), fmul2(db, fadd2(make_float2(br, br), b))));
+    const float2 num = ffma2(Nw, Ds, fmul2(Ns, Dw)), den = fmul2(Dw, Ds);
+    return ffma2(num, make_float2(rcp_sfu(den.x), rcp_sfu(den.y)), make_float2(r2.z, r2.z));
+}
+
 // Horizontal distance of a pixel from a sensor, rho = rho_r + drho, from
 // qh = 2 h_r.d_h + |d_h|^2 (h_r: horizontal part of x_r - s; d_h the
 // pixel's horizontal offset from x_r).
@@ -977,18 +1042,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             }
             if constexpr (REFRACT) {
                 if (rrefr) {
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int s = 2 * k + j;
-                        float& Dj = j ? D.y : D.x;
-                        if ((bmask >> s) & 1u) {
-                            if (!DIM3) refr_rho(rr0, j ? a.y : a.x, rhoR, drhoR);
-                            float b, db;
-                            slot_depth(s, b, db);
-                            Dj = refr_leg_diff(p, rr0, rr1, rr2, rhoR, drhoR, b, db, r_br) + PXS(dTp, s);
-                        } else {
-                            Dj += rr2.w;
+                    const unsigned bk = (bmask >> (2 * k)) & 3u;   // which of the two slots are below
+                    if (bk) {
+                        float2 rho2 = make_float2(rhoR, rhoR), drho2 = make_float2(drhoR, drhoR);
+                        if (!DIM3) {
+                            refr_rho(rr0, a.x, rho2.x, drho2.x);
+                            refr_rho(rr0, a.y, rho2.y, drho2.y);
                         }
+                        float2 b2, db2;
+                        slot_depth(2 * k, b2.x, db2.x);
+                        slot_depth(2 * k + 1, b2.y, db2.y);
+                        const float2 Dr = fadd2(refr_leg_diff2(p, rr0, rr1, rr2, rho2, drho2, b2, db2, r_br), dTp[k]);
+                        D.x = (bk & 1u) ? Dr.x : D.x + rr2.w;
+                        D.y = (bk & 2u) ? Dr.y : D.y + rr2.w;
+                    } else {
+                        D = fadd2(D, make_float2(rr2.w, rr2.w));
                     }
                 }
             }
