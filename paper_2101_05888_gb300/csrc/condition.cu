@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(1024) mf_replica_kernel(const float2* __restri
 }
 
 // One CTA per (row, block of M outputs): circular correlation of NF inputs.
+// R4 = 1 for NF <= 4096 (NF / 4 threads, one butterfly each per stage).
+template <int R4>
 __global__ void __launch_bounds__(1024) mf_block_kernel(const float2* __restrict__ raw, int n, int NF, int M, int nblk,
                                 const float2* __restrict__ Pc, float2* __restrict__ out) {
     extern __shared__ float2 buf[];
@@ -68,10 +70,10 @@ __global__ void __launch_bounds__(1024) mf_block_kernel(const float2* __restrict
         buf[j] = k < n ? src[k] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_smem(buf, tw, NF, -1.f);
+    fft_smem<R4>(buf, tw, NF, -1.f);
     for (int j = threadIdx.x; j < NF; j += blockDim.x) buf[j] = fftdev::cmul(buf[j], Pc[j]);
     __syncthreads();
-    fft_smem(buf, tw, NF, 1.f);
+    fft_smem<R4>(buf, tw, NF, 1.f);
     float2* dst = out + row * (long long)n;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const long long k = k0 + j;
@@ -394,13 +396,13 @@ extern "C" int sas_matched_filter(const void* d_raw, int64_t rows, int32_t n, co
     const int nt = fft_threads(NF);
     const size_t sm = sizeof(float2) * (NF + NF / 2);       // row + twiddles
     int rc = SAS_OK;
+    // one radix-4 butterfly per thread when NF / 4 threads fit in a block
+    auto blk = NF <= 4096 ? mf_block_kernel<1> : mf_block_kernel<fftdev::R4_PER_THREAD>;
     cudaError_t e = cudaFuncSetAttribute(mf_replica_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mf_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) {
         mf_replica_kernel<<<1, nt, sm, st>>>((const float2*)d_replica, L, NF, Pc);
-        mf_block_kernel<<<(unsigned)(rows * nblk), nt, sm, st>>>((const float2*)d_raw, n, NF, M, nblk, Pc,
-                                                                 (float2*)d_out);
+        blk<<<(unsigned)(rows * nblk), nt, sm, st>>>((const float2*)d_raw, n, NF, M, nblk, Pc, (float2*)d_out);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "matched filter");

@@ -16,7 +16,6 @@ namespace fftdev {
 
 constexpr int MAX_N = 16384;
 constexpr int R4_PER_THREAD = 4;     // radix-4 butterflies per thread per stage: blockDim.x >= N / 16
-constexpr int R2_PER_THREAD = 8;     // radix-2 butterflies per thread: blockDim.x >= N / 16
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -32,16 +31,21 @@ __device__ void fft_twiddles(float2* tw, int N) {
     __syncthreads();
 }
 
-// sign = -1 forward, +1 inverse.  Requires blockDim.x >= N / 16 (so every
-// butterfly of a stage is held in registers by the loops below).
+// sign = -1 forward, +1 inverse.  R4: radix-4 butterflies a thread holds per
+// stage (2 R4 radix-2 ones); requires blockDim.x >= N / (4 R4), so that every
+// butterfly of a stage is held in registers by the loops below.  R4 = 1 for
+// blockDim.x = N / 4 keeps the register footprint (and so the occupancy) of
+// small transforms low.
+template <int R4 = R4_PER_THREAD>
 __device__ void fft_smem(float2* buf, const float2* tw, int N, float sign) {
+    constexpr int R2 = 2 * R4;
     const int nt = blockDim.x, tid = threadIdx.x;
     const int N4 = N >> 2;
     int L = 1;
     while (4 * L <= N) {
-        float2 y[4 * R4_PER_THREAD];
+        float2 y[4 * R4];
 #pragma unroll
-        for (int c = 0; c < R4_PER_THREAD; ++c) {
+        for (int c = 0; c < R4; ++c) {
             const int j = tid + c * nt;
             if (j < N4) {
                 const int k = j & (L - 1);
@@ -61,7 +65,7 @@ __device__ void fft_smem(float2* buf, const float2* tw, int N, float sign) {
         }
         __syncthreads();
 #pragma unroll
-        for (int c = 0; c < R4_PER_THREAD; ++c) {
+        for (int c = 0; c < R4; ++c) {
             const int j = tid + c * nt;
             if (j < N4) {
                 const int k = j & (L - 1), i = j - k;
@@ -74,9 +78,9 @@ __device__ void fft_smem(float2* buf, const float2* tw, int N, float sign) {
     }
     if (L < N) {   // one radix-2 stage
         const int N2 = N >> 1;
-        float2 y[2 * R2_PER_THREAD];
+        float2 y[2 * R2];
 #pragma unroll
-        for (int c = 0; c < R2_PER_THREAD; ++c) {
+        for (int c = 0; c < R2; ++c) {
             const int j = tid + c * nt;
             if (j < N2) {
                 const int k = j & (L - 1);
@@ -88,7 +92,7 @@ __device__ void fft_smem(float2* buf, const float2* tw, int N, float sign) {
         }
         __syncthreads();
 #pragma unroll
-        for (int c = 0; c < R2_PER_THREAD; ++c) {
+        for (int c = 0; c < R2; ++c) {
             const int j = tid + c * nt;
             if (j < N2) {
                 const int k = j & (L - 1), i = j - k;
