@@ -271,105 +271,227 @@ __global__ void scale_columns_kernel(const float2* __restrict__ in, float2* __re
 }
 
 // ----------------------------------------------------------------------------
-// DRC: magnitude, maximum, global radix select, map
+// DRC: magnitude, maximum and the two middle order statistics of |I| by a
+// three-level radix select on the FP32 bit patterns (non-negative floats order
+// like their bits): level 1 the top 12 bits (sign, exponent and 3 mantissa
+// bits: 1/8-octave bins, so the magnitudes of a speckled image spread over many
+// bins), level 2 the next 10 bits of the pixels in the two chosen level-1
+// bins, level 3 the last 10 bits of those matching the chosen 22-bit
+// prefixes.  Both ranks (npix - 1) / 2 and npix / 2 are selected together.
+
+constexpr int DRC_NB1 = 2048;   // bits >> 20 of a non-negative float
+constexpr int DRC_NB = 1024;    // levels 2 and 3
+constexpr int DRC_T = 256;      // threads of the magnitude, level and map kernels
 
 struct DrcState {
-    unsigned maxbits;       // max |I| (FP32 bits)
-    unsigned prefix, rank;  // selection of rank klo
-    unsigned cnt_le, min_gt;
-    unsigned hist[256];
+    unsigned maxbits;        // max |I| (FP32 bits)
+    unsigned done[3];        // blocks finished, per level
+    unsigned rank[2];        // rank still to find within the chosen prefix
+    unsigned prefix[2];      // bits chosen so far, per middle rank
+    unsigned hist1[DRC_NB1];
+    unsigned hist2[2][DRC_NB];
+    unsigned hist3[2][DRC_NB];
 };
 
-__global__ void drc_mag_kernel(const float2* __restrict__ img, long long npix, float* __restrict__ mag,
-                               DrcState* st) {
+__global__ void __launch_bounds__(1024) drc_init_kernel(DrcState* st, long long npix) {
+    unsigned* w = reinterpret_cast<unsigned*>(st);
+    for (int i = threadIdx.x; i < (int)(sizeof(DrcState) / sizeof(unsigned)); i += blockDim.x) w[i] = 0u;
+    if (threadIdx.x == 0) {
+        st->rank[0] = (unsigned)((npix - 1) / 2);
+        st->rank[1] = (unsigned)(npix / 2);
+    }
+}
+
+// For each middle rank r, the bin of `hist` (this level's histogram for r)
+// that holds its residual rank: the bin is appended to the prefix (shifted by
+// `shift`) and the rank within the bin is kept.  Run by the last block of a
+// level kernel (DRC_T threads) once every block's counts are in; the counts
+// other blocks added are read from L2.
+template <int NB>
+__device__ void drc_pick(DrcState* st, const unsigned* hist0, const unsigned* hist1, int shift) {
+    constexpr int PER = NB / DRC_T, NW = DRC_T / 32;
+    __shared__ unsigned wsum[NW];
+    __shared__ unsigned pick_bin[2], pick_below[2];
+    if (threadIdx.x < 2) pick_bin[threadIdx.x] = pick_below[threadIdx.x] = 0u;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r = 0; r < 2; ++r) {
+        const unsigned* hist = r ? hist1 : hist0;
+        const unsigned rk = __ldcg(&st->rank[r]);
+        unsigned c[PER], tot = 0u;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            c[k] = __ldcg(&hist[threadIdx.x * PER + k]);
+            tot += c[k];
+        }
+        unsigned x = tot;                                   // inclusive scan over the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        unsigned below = x - tot;                           // pixels in the bins before this thread's
+        for (int w = 0; w < wid; ++w) below += wsum[w];
+        if (rk >= below && rk - below < tot) {              // exactly one thread
+#pragma unroll
+            for (int k = 0; k < PER; ++k) {
+                if (rk - below < c[k]) {
+                    pick_bin[r] = threadIdx.x * PER + k;
+                    pick_below[r] = below;
+                    break;
+                }
+                below += c[k];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) {
+        const int r = threadIdx.x;
+        st->rank[r] = __ldcg(&st->rank[r]) - pick_below[r];
+        st->prefix[r] = __ldcg(&st->prefix[r]) | (pick_bin[r] << shift);
+    }
+}
+
+// Adds a block's shared histogram (n bins) to the global one; returns true in
+// the last block of the grid to finish, after which every block's counts are
+// visible to it.
+__device__ bool drc_flush(const unsigned* h, unsigned* g, int n, unsigned* done) {
+    __shared__ bool last;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+        if (h[t]) atomicAdd(&g[t], h[t]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Level 1: |I| (correctly rounded), its maximum and the histogram of the top
+// 12 bits; the last block picks the level-1 bins.  A NaN with the sign bit set
+// (only a NaN can have it) is stored as the largest positive NaN, so that
+// every bit pattern the levels see is below 2^31.
+__device__ __forceinline__ float drc_magnitude(float2 v) {
+    return __uint_as_float(min(__float_as_uint(__fsqrt_rn(power_f32(v))), 0x7fffffffu));
+}
+
+__global__ void __launch_bounds__(DRC_T) drc_mag_kernel(const float2* __restrict__ img, long long npix,
+                                                        float* __restrict__ mag, DrcState* st) {
+    __shared__ unsigned h[DRC_NB1];
+    for (int t = threadIdx.x; t < DRC_NB1; t += blockDim.x) h[t] = 0u;
+    __syncthreads();
     unsigned mx = 0u;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float m = __fsqrt_rn(power_f32(img[i]));
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < npix; i += 4 * stride) {     // four independent loads in flight
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = img[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float m = drc_magnitude(v[u]);
+            mag[i + u * stride] = m;
+            const unsigned bits = __float_as_uint(m);
+            mx = max(mx, bits);
+            atomicAdd(&h[bits >> 20], 1u);
+        }
+    }
+    for (; i < npix; i += stride) {
+        const float m = drc_magnitude(img[i]);
         mag[i] = m;
-        mx = max(mx, __float_as_uint(m));
+        const unsigned bits = __float_as_uint(m);
+        mx = max(mx, bits);
+        atomicAdd(&h[bits >> 20], 1u);
     }
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(&st->maxbits, mx);
+    if (drc_flush(h, st->hist1, DRC_NB1, &st->done[0])) drc_pick<DRC_NB1>(st, st->hist1, st->hist1, 20);
 }
 
-__global__ void drc_hist_kernel(const float* __restrict__ mag, long long npix, int pass, DrcState* st) {
-    __shared__ unsigned h[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0u;
+// Levels 2 and 3: the pixels whose top bits match a rank's chosen prefix
+// (level 2: bits >> 20, level 3: bits >> 10) are histogrammed on the next 10
+// bits, one histogram per middle rank; the last block picks the bins, and at
+// level 3, where the two order statistics are complete, derives q (Eq. 12)
+// from their mean: stats = {q, median of I_n, max |I|}.
+template <int LEVEL>
+__global__ void __launch_bounds__(DRC_T) drc_level_kernel(const float* __restrict__ mag, long long npix,
+                                                          DrcState* st, double b, double* __restrict__ stats) {
+    constexpr int SH = LEVEL == 2 ? 20 : 10;
+    __shared__ unsigned h[2][DRC_NB];
+    for (int t = threadIdx.x; t < 2 * DRC_NB; t += blockDim.x) (&h[0][0])[t] = 0u;
     __syncthreads();
-    const int shift = 24 - 8 * pass;
-    const unsigned himask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
-    const unsigned pre = st->prefix;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned bits = __float_as_uint(mag[i]);
-        if ((bits & himask) == pre) atomicAdd(&h[(bits >> shift) & 255u], 1u);
+    const unsigned p0 = st->prefix[0] >> SH, p1 = st->prefix[1] >> SH;
+    auto add = [&](unsigned bits) {
+        const unsigned k = (bits >> (SH - 10)) & (DRC_NB - 1);
+        if ((bits >> SH) == p0) atomicAdd(&h[0][k], 1u);
+        if ((bits >> SH) == p1) atomicAdd(&h[1][k], 1u);
+    };
+    // mag is the 256-byte aligned scratch: quads of pixels, two in flight
+    const float4* m4 = reinterpret_cast<const float4*>(mag);
+    const long long n4 = npix >> 2, stride = (long long)gridDim.x * blockDim.x;
+    long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; j + stride < n4; j += 2 * stride) {
+        const float4 v = m4[j], w = m4[j + stride];
+        add(__float_as_uint(v.x)); add(__float_as_uint(v.y)); add(__float_as_uint(v.z)); add(__float_as_uint(v.w));
+        add(__float_as_uint(w.x)); add(__float_as_uint(w.y)); add(__float_as_uint(w.z)); add(__float_as_uint(w.w));
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 256; t += blockDim.x)
-        if (h[t]) atomicAdd(&st->hist[t], h[t]);
-}
-
-__global__ void drc_pick_kernel(int pass, DrcState* st) {
-    const int shift = 24 - 8 * pass;
-    unsigned rk = st->rank, acc = 0u;
-    int bsel = 255;
-    for (int bb = 0; bb < 256; ++bb) {
-        const unsigned h = st->hist[bb];
-        if (acc + h > rk) {
-            bsel = bb;
-            break;
+    if (j < n4) {
+        const float4 v = m4[j];
+        add(__float_as_uint(v.x)); add(__float_as_uint(v.y)); add(__float_as_uint(v.z)); add(__float_as_uint(v.w));
+    }
+    for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix; i += stride)
+        add(__float_as_uint(mag[i]));
+    unsigned* g = LEVEL == 2 ? &st->hist2[0][0] : &st->hist3[0][0];
+    if (!drc_flush(&h[0][0], g, 2 * DRC_NB, &st->done[LEVEL - 1])) return;
+    drc_pick<DRC_NB>(st, g, g + DRC_NB, SH - 10);
+    if (LEVEL == 3) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const float M = __uint_as_float(__ldcg(&st->maxbits));
+            const float lo = __uint_as_float(__ldcg(&st->prefix[0])), hi = __uint_as_float(__ldcg(&st->prefix[1]));
+            const double med = 0.5 * ((double)__fdiv_rn(lo, M) + (double)__fdiv_rn(hi, M));
+            // Eq. 12 has no value at a median of 1 (all pixels at the maximum:
+            // identity map) or 0 (q -> infinity: every non-zero pixel maps to 1)
+            stats[0] = med >= 1.0 ? 1.0 : (med <= 0.0 ? (1.0 / 0.0) : (b - b * med) / (med - b * med));
+            stats[1] = med;
+            stats[2] = (double)M;
         }
-        acc += h;
-    }
-    st->rank = rk - acc;
-    st->prefix |= (unsigned)bsel << shift;
-    for (int bb = 0; bb < 256; ++bb) st->hist[bb] = 0u;
-}
-
-__global__ void drc_second_kernel(const float* __restrict__ mag, long long npix, DrcState* st) {
-    const unsigned vlo = st->prefix;
-    unsigned le = 0u, mg = 0xffffffffu;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix;
-         i += (long long)gridDim.x * blockDim.x) {
-        const unsigned bits = __float_as_uint(mag[i]);
-        if (bits <= vlo) ++le;
-        else mg = min(mg, bits);
-    }
-    for (int o = 16; o; o >>= 1) {
-        le += __shfl_xor_sync(0xffffffffu, le, o);
-        mg = min(mg, __shfl_xor_sync(0xffffffffu, mg, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&st->cnt_le, le);
-        atomicMin(&st->min_gt, mg);
     }
 }
 
-// q from Eq. 12 on the median of I_n = |I| / max |I|; stats = {q, median, max}
-__global__ void drc_q_kernel(long long npix, double b, DrcState* st, double* __restrict__ stats) {
-    const unsigned long long khi = (unsigned long long)(npix / 2);
-    const float M = __uint_as_float(st->maxbits);
-    const float lo = __uint_as_float(st->prefix);
-    const float hi = (st->cnt_le > khi) ? lo : __uint_as_float(st->min_gt);
-    const double med = 0.5 * ((double)__fdiv_rn(lo, M) + (double)__fdiv_rn(hi, M));
-    // Eq. 12 has no value at a median of 1 (all pixels at the maximum: identity
-    // map) or 0 (q -> infinity: every non-zero pixel maps to 1)
-    stats[0] = med >= 1.0 ? 1.0 : (med <= 0.0 ? (1.0 / 0.0) : (b - b * med) / (med - b * med));
-    stats[1] = med;
-    stats[2] = (double)M;
-}
-
-__global__ void drc_map_kernel(const float* __restrict__ mag, long long npix, const DrcState* st,
-                               const double* __restrict__ stats, float* __restrict__ out) {
+// Eq. 11 map: I_n = |I| / max |I|, out = q I_n / ((q - 1) I_n + 1).  vec: the
+// output is 16-byte aligned (quads of pixels, two in flight).
+__global__ void __launch_bounds__(DRC_T) drc_map_kernel(const float* __restrict__ mag, long long npix,
+                                                        const DrcState* st, const double* __restrict__ stats,
+                                                        float* __restrict__ out, int vec) {
     const float M = __uint_as_float(st->maxbits);
     const float q = (float)stats[0];
     const bool qinf = isinf(stats[0]);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float In = __fdiv_rn(mag[i], M);
-        out[i] = qinf ? (In > 0.f ? 1.f : 0.f) : __fdiv_rn(q * In, fmaf(q - 1.f, In, 1.f));
+    auto map = [&](float m) {
+        const float In = __fdiv_rn(m, M);
+        return qinf ? (In > 0.f ? 1.f : 0.f) : __fdiv_rn(q * In, fmaf(q - 1.f, In, 1.f));
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long i = t0;
+    if (vec) {
+        const float4* m4 = reinterpret_cast<const float4*>(mag);
+        float4* o4 = reinterpret_cast<float4*>(out);
+        const long long n4 = npix >> 2;
+        long long j = t0;
+        for (; j + stride < n4; j += 2 * stride) {
+            const float4 v = m4[j], w = m4[j + stride];
+            o4[j] = make_float4(map(v.x), map(v.y), map(v.z), map(v.w));
+            o4[j + stride] = make_float4(map(w.x), map(w.y), map(w.z), map(w.w));
+        }
+        if (j < n4) {
+            const float4 v = m4[j];
+            o4[j] = make_float4(map(v.x), map(v.y), map(v.z), map(v.w));
+        }
+        i = 4 * n4 + t0;
     }
+    for (; i < npix; i += stride) out[i] = map(mag[i]);
 }
 
 bool pow2_in(long long n, long long lo, long long hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
@@ -497,26 +619,14 @@ extern "C" int sas_drc(const void* d_image, int64_t npix, double b, float* d_out
     float* mag = reinterpret_cast<float*>(scratch);
     DrcState* ds = reinterpret_cast<DrcState*>(scratch + off_ds);
     double* stats = d_stats ? d_stats : reinterpret_cast<double*>(scratch + off_st);
-    cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(DrcState), st);
-    if (e == cudaSuccess) {
-        const unsigned klo = (unsigned)((npix - 1) / 2);
-        e = cudaMemcpyAsync(&ds->rank, &klo, sizeof(unsigned), cudaMemcpyHostToDevice, st);
-        const unsigned ones = 0xffffffffu;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&ds->min_gt, &ones, sizeof(unsigned), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the two host values are stack variables
-    }
-    if (e == cudaSuccess) {
-        const unsigned grid = (unsigned)std::min<long long>((npix + 255) / 256, 8LL * sm_count());
-        drc_mag_kernel<<<grid, 256, 0, st>>>((const float2*)d_image, npix, mag, ds);
-        for (int pass = 0; pass < 4; ++pass) {
-            drc_hist_kernel<<<grid, 256, 0, st>>>(mag, npix, pass, ds);
-            drc_pick_kernel<<<1, 1, 0, st>>>(pass, ds);
-        }
-        drc_second_kernel<<<grid, 256, 0, st>>>(mag, npix, ds);
-        drc_q_kernel<<<1, 1, 0, st>>>(npix, b, ds, stats);
-        drc_map_kernel<<<grid, 256, 0, st>>>(mag, npix, ds, stats, d_out);
-        e = cudaGetLastError();
-    }
+    const unsigned grid = (unsigned)std::min<long long>((npix + DRC_T - 1) / DRC_T, 8LL * sm_count());
+    const int vec = ((uintptr_t)d_out & 15) == 0;
+    drc_init_kernel<<<1, 1024, 0, st>>>(ds, npix);
+    drc_mag_kernel<<<grid, DRC_T, 0, st>>>((const float2*)d_image, npix, mag, ds);
+    drc_level_kernel<2><<<grid, DRC_T, 0, st>>>(mag, npix, ds, b, stats);
+    drc_level_kernel<3><<<grid, DRC_T, 0, st>>>(mag, npix, ds, b, stats);
+    drc_map_kernel<<<grid, DRC_T, 0, st>>>(mag, npix, ds, stats, d_out, vec);
+    const cudaError_t e = cudaGetLastError();
     cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return cuda_fail(e, "drc");
     return SAS_OK;

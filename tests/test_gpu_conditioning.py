@@ -117,3 +117,33 @@ def test_drc_without_stats_output():
     torch.cuda.synchronize()
     ref, _, _ = cond.drc(img, 0.3)
     assert np.abs(out.cpu().numpy() - ref.reshape(-1)).max() < 1e-6
+
+
+@pytest.mark.parametrize("kind", ["constant", "mostly_dark", "speckle_2M", "half_dark_even"])
+def test_drc_selection_edge_cases(kind):
+    """The radix selection on the degenerate medians (all pixels at the
+    maximum: the identity map; a dark median: every lit pixel to 1), on an even
+    count whose two middle values differ, and on a 2M-pixel speckle image that
+    spans many blocks and 1/8-octave bins: median and maximum exact, map to
+    1e-6."""
+    rng = np.random.default_rng(len(kind))
+    if kind == "constant":
+        img = np.full(1000, 0.3 - 0.4j, np.complex64)
+    elif kind == "mostly_dark":
+        img = np.zeros(4097, np.complex64)
+        img[::3] = (rng.standard_normal(1366) + 1j).astype(np.complex64)
+    elif kind == "half_dark_even":
+        img = np.zeros(2 * 33333, np.complex64)
+        img[33333:] = (1.0 + rng.standard_exponential(33333)).astype(np.complex64)
+    else:
+        n = 1 << 21
+        img = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    out = torch.empty(img.size, dtype=torch.float32, device="cuda")
+    stats = torch.empty(3, dtype=torch.float64, device="cuda")
+    sas.sas_drc(torch.from_numpy(img).cuda(), img.size, 0.3, out, stats)
+    torch.cuda.synchronize()
+    ref, q, med = cond.drc(img, 0.3)
+    st = stats.cpu().numpy()
+    assert st[1] == med and st[2] == float(cond.magnitude_f32(img).max())
+    assert st[0] == q or abs(st[0] - q) <= 1e-12 * abs(q)
+    assert np.abs(out.cpu().numpy() - ref.reshape(-1)).max() < 1e-6
