@@ -16,6 +16,7 @@
 //    map of Eq. 11.
 // Medians of an even count are the FP64 mean of the two middle values.
 #include "fft.cuh"
+#include "fftreg.cuh"
 #include "sas_common.cuh"
 
 #include <algorithm>
@@ -53,32 +54,65 @@ __global__ void __launch_bounds__(1024) mf_replica_kernel(const float2* __restri
     for (int j = threadIdx.x; j < NF; j += blockDim.x) Pc[j] = make_float2(buf[j].x * s, -buf[j].y * s);
 }
 
-// One CTA per (row, block of M outputs): circular correlation of NF inputs.
-// R4 = 1 for NF <= 4096 (NF / 4 threads, one butterfly each per stage).
-template <int R4>
-__global__ void __launch_bounds__(1024) mf_block_kernel(const float2* __restrict__ raw, int n, int NF, int M, int nblk,
-                                const float2* __restrict__ Pc, float2* __restrict__ out) {
-    extern __shared__ float2 buf[];
-    float2* tw = buf + NF;
+// Register-FFT kernels: a CTA of G groups of T = N / (16 B) threads, one row
+// (or row block) per group, G = 256 / T up to N = 4096, else 1.
+template <int N>
+struct RegPlan {
+    static constexpr int B = fftreg::points_b<N>(), P = 16 * B, T = N / P;
+    static constexpr int G = T >= 256 ? 1 : 256 / T, THREADS = T * G;
+    static constexpr int MINB = THREADS <= 256 ? 2 : 1;     // at most 128 registers a thread
+    static constexpr size_t SMEM = sizeof(float2) * ((size_t)G * fftreg::padded(N) + N / 2);
+};
+
+// One group per (row, block of M outputs): circular correlation of NF inputs
+// (the segment raw[k0 .. k0 + NF), zero past the row end) with the replica,
+// through the spectra: IFFT(FFT(x) Pc); the first M outputs are the linear
+// correlation.
+template <int NF>
+__global__ void __launch_bounds__(RegPlan<NF>::THREADS, RegPlan<NF>::MINB) mf_reg_kernel(const float2* __restrict__ raw, int n, int M,
+                                                                      int nblk, long long items,
+                                                                      const float2* __restrict__ Pc,
+                                                                      float2* __restrict__ out) {
+    using RP = RegPlan<NF>;
+    extern __shared__ float2 sm[];
+    float2* tw = sm + RP::G * fftreg::padded(NF);
     fftdev::fft_twiddles(tw, NF);
-    const long long row = blockIdx.x / nblk;
-    const int b = blockIdx.x % nblk;
-    const long long k0 = (long long)b * M;
+    const int g = threadIdx.x / RP::T, tid = threadIdx.x % RP::T;
+    const long long item = (long long)blockIdx.x * RP::G + g;
+    const bool live = item < items;
+    const long long row = live ? item / nblk : 0;
+    const long long k0 = live ? (long long)(item % nblk) * M : 0;
     const float2* src = raw + row * (long long)n;
-    for (int j = threadIdx.x; j < NF; j += blockDim.x) {
-        const long long k = k0 + j;
-        buf[j] = k < n ? src[k] : make_float2(0.f, 0.f);
+    float2 x[RP::P];
+#pragma unroll
+    for (int m = 0; m < RP::P; ++m) {
+        const long long k = k0 + tid + RP::T * m;
+        x[m] = live && k < n ? src[k] : make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    fft_smem<R4>(buf, tw, NF, -1.f);
-    for (int j = threadIdx.x; j < NF; j += blockDim.x) buf[j] = fftdev::cmul(buf[j], Pc[j]);
-    __syncthreads();
-    fft_smem<R4>(buf, tw, NF, 1.f);
+    float2* rowbuf = sm + g * fftreg::padded(NF);
+    fftreg::fft<NF, RP::B, true>(x, rowbuf, tw, tid);
+#pragma unroll
+    for (int m = 0; m < RP::P; ++m) x[m] = fftreg::cmul(x[m], Pc[tid + RP::T * m]);
+    fftreg::fft<NF, RP::B, false>(x, rowbuf, tw, tid);
     float2* dst = out + row * (long long)n;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+#pragma unroll
+    for (int m = 0; m < RP::P; ++m) {
+        const int j = tid + RP::T * m;
         const long long k = k0 + j;
-        if (k < n) dst[k] = buf[j];
+        if (live && j < M && k < n) dst[k] = x[m];
     }
+}
+
+template <int NF>
+cudaError_t mf_reg_launch(const float2* raw, long long rows, int n, int M, int nblk, const float2* Pc, float2* out,
+                          cudaStream_t st) {
+    using RP = RegPlan<NF>;
+    cudaError_t e = cudaFuncSetAttribute(mf_reg_kernel<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RP::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long items = rows * nblk;
+    mf_reg_kernel<NF><<<(unsigned)((items + RP::G - 1) / RP::G), RP::THREADS, RP::SMEM, st>>>(raw, n, M, nblk, items,
+                                                                                             Pc, out);
+    return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
@@ -162,6 +196,107 @@ __global__ void __launch_bounds__(1024) whiten_apply_kernel(float2* __restrict__
         fft_smem(buf, tw, n, 1.f);
         for (int j = threadIdx.x; j < n; j += blockDim.x) out[r * n + j] = make_float2(buf[j].x * inv, buf[j].y * inv);
         __syncthreads();
+    }
+}
+
+// Register-FFT forms of the two whitening passes for n >= 256: groups of
+// threads hold a row in registers (see RegPlan); the CTAs stride over groups
+// of G rows.  Pass 1 writes the spectra; pass 2 reads them, applies the gain
+// and writes IFFT / n.
+template <int N>
+__global__ void __launch_bounds__(RegPlan<N>::THREADS, RegPlan<N>::MINB) whiten_spectra_reg_kernel(const float2* __restrict__ in,
+                                                                                 float2* __restrict__ out,
+                                                                                 long long rows) {
+    using RP = RegPlan<N>;
+    extern __shared__ float2 sm[];
+    float2* tw = sm + RP::G * fftreg::padded(N);
+    fftdev::fft_twiddles(tw, N);
+    const int g = threadIdx.x / RP::T, tid = threadIdx.x % RP::T;
+    float2* rowbuf = sm + g * fftreg::padded(N);
+    for (long long r0 = (long long)blockIdx.x * RP::G; r0 < rows; r0 += (long long)gridDim.x * RP::G) {
+        const long long r = r0 + g;
+        const bool live = r < rows;
+        const float2* src = in + (live ? r : 0) * N;
+        float2 x[RP::P];
+#pragma unroll
+        for (int m = 0; m < RP::P; ++m) x[m] = src[tid + RP::T * m];
+        fftreg::fft<N, RP::B, true>(x, rowbuf, tw, tid);
+        if (live) {
+#pragma unroll
+            for (int m = 0; m < RP::P; ++m) out[r * N + tid + RP::T * m] = x[m];
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(RegPlan<N>::THREADS, RegPlan<N>::MINB) whiten_apply_reg_kernel(float2* __restrict__ out,
+                                                                               long long rows,
+                                                                               const float* __restrict__ gain) {
+    using RP = RegPlan<N>;
+    extern __shared__ float2 sm[];
+    float2* tw = sm + RP::G * fftreg::padded(N);
+    fftdev::fft_twiddles(tw, N);
+    const int g = threadIdx.x / RP::T, tid = threadIdx.x % RP::T;
+    float2* rowbuf = sm + g * fftreg::padded(N);
+    const float inv = 1.f / (float)N;
+    for (long long r0 = (long long)blockIdx.x * RP::G; r0 < rows; r0 += (long long)gridDim.x * RP::G) {
+        const long long r = r0 + g;
+        const bool live = r < rows;
+        float2* row = out + (live ? r : 0) * N;
+        float2 x[RP::P];
+#pragma unroll
+        for (int m = 0; m < RP::P; ++m) {
+            const float2 v = row[tid + RP::T * m];
+            const float gg = gain[tid + RP::T * m];
+            x[m] = make_float2(v.x * gg, v.y * gg);
+        }
+        fftreg::fft<N, RP::B, false>(x, rowbuf, tw, tid);
+        if (live) {
+#pragma unroll
+            for (int m = 0; m < RP::P; ++m) row[tid + RP::T * m] = make_float2(x[m].x * inv, x[m].y * inv);
+        }
+    }
+}
+
+template <int N>
+cudaError_t whiten_reg_launch(bool apply, const float2* in, float2* out, long long rows, const float* gain,
+                              cudaStream_t st) {
+    using RP = RegPlan<N>;
+    const long long groups = (rows + RP::G - 1) / RP::G;
+    if (!apply) {
+        cudaError_t e = cudaFuncSetAttribute(whiten_spectra_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)RP::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, whiten_spectra_reg_kernel<N>, RP::THREADS, RP::SMEM);
+        if (e != cudaSuccess) return e;
+        const long long grid = std::min<long long>(groups, (long long)std::max(per_sm, 1) * sm_count());
+        whiten_spectra_reg_kernel<N><<<(unsigned)grid, RP::THREADS, RP::SMEM, st>>>(in, out, rows);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(whiten_apply_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)RP::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, whiten_apply_reg_kernel<N>, RP::THREADS, RP::SMEM);
+        if (e != cudaSuccess) return e;
+        const long long grid = std::min<long long>(groups, (long long)std::max(per_sm, 1) * sm_count());
+        whiten_apply_reg_kernel<N><<<(unsigned)grid, RP::THREADS, RP::SMEM, st>>>(out, rows, gain);
+    }
+    return cudaGetLastError();
+}
+
+// the register path for n in [256, 16384] (false: n outside it)
+bool whiten_reg_dispatch(int n, bool apply, const float2* in, float2* out, long long rows, const float* gain,
+                         cudaStream_t st, cudaError_t* err) {
+    switch (n) {
+        case 256: *err = whiten_reg_launch<256>(apply, in, out, rows, gain, st); return true;
+        case 512: *err = whiten_reg_launch<512>(apply, in, out, rows, gain, st); return true;
+        case 1024: *err = whiten_reg_launch<1024>(apply, in, out, rows, gain, st); return true;
+        case 2048: *err = whiten_reg_launch<2048>(apply, in, out, rows, gain, st); return true;
+        case 4096: *err = whiten_reg_launch<4096>(apply, in, out, rows, gain, st); return true;
+        case 8192: *err = whiten_reg_launch<8192>(apply, in, out, rows, gain, st); return true;
+        case 16384: *err = whiten_reg_launch<16384>(apply, in, out, rows, gain, st); return true;
+        default: return false;
     }
 }
 
@@ -518,14 +653,23 @@ extern "C" int sas_matched_filter(const void* d_raw, int64_t rows, int32_t n, co
     const int nt = fft_threads(NF);
     const size_t sm = sizeof(float2) * (NF + NF / 2);       // row + twiddles
     int rc = SAS_OK;
-    // one radix-4 butterfly per thread when NF / 4 threads fit in a block
-    auto blk = NF <= 4096 ? mf_block_kernel<1> : mf_block_kernel<fftdev::R4_PER_THREAD>;
     cudaError_t e = cudaFuncSetAttribute(mf_replica_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) {
         mf_replica_kernel<<<1, nt, sm, st>>>((const float2*)d_replica, L, NF, Pc);
-        blk<<<(unsigned)(rows * nblk), nt, sm, st>>>((const float2*)d_raw, n, NF, M, nblk, Pc, (float2*)d_out);
         e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const float2* raw = (const float2*)d_raw;
+        float2* o = (float2*)d_out;
+        switch (NF) {
+            case 256: e = mf_reg_launch<256>(raw, rows, n, M, nblk, Pc, o, st); break;
+            case 512: e = mf_reg_launch<512>(raw, rows, n, M, nblk, Pc, o, st); break;
+            case 1024: e = mf_reg_launch<1024>(raw, rows, n, M, nblk, Pc, o, st); break;
+            case 2048: e = mf_reg_launch<2048>(raw, rows, n, M, nblk, Pc, o, st); break;
+            case 4096: e = mf_reg_launch<4096>(raw, rows, n, M, nblk, Pc, o, st); break;
+            case 8192: e = mf_reg_launch<8192>(raw, rows, n, M, nblk, Pc, o, st); break;
+            default: e = mf_reg_launch<16384>(raw, rows, n, M, nblk, Pc, o, st); break;
+        }
     }
     if (e != cudaSuccess) rc = cuda_fail(e, "matched filter");
     cudaFreeAsync(Pc, st);
@@ -560,13 +704,20 @@ extern "C" int sas_whiten(const void* d_in, void* d_out, int64_t rows, int32_t n
     cudaError_t e = cudaFuncSetAttribute(whiten_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(whiten_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess &&
+        !whiten_reg_dispatch(n, false, (const float2*)d_in, (float2*)d_out, rows, gain, st, &e)) {
         whiten_spectra_kernel<<<(unsigned)std::min<long long>(rows, 8LL * sm_count()), nt, sm, st>>>(
             (const float2*)d_in, (float2*)d_out, rows, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
         whiten_power_kernel<<<dim3((n + 255) / 256, nparts), 256, 0, st>>>((const float2*)d_out, rows, n, nparts,
                                                                            part);
         whiten_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(part, nparts, n, rows, P);
         whiten_gain_kernel<<<1, 1024, 0, st>>>(P, n, gamma, gain);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !whiten_reg_dispatch(n, true, nullptr, (float2*)d_out, rows, gain, st, &e)) {
         whiten_apply_kernel<<<(unsigned)std::min<long long>(rows, 8LL * sm_count()), nt, sm, st>>>(
             (float2*)d_out, rows, n, gain);
         e = cudaGetLastError();
