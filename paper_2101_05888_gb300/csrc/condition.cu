@@ -133,21 +133,54 @@ __global__ void __launch_bounds__(1024) whiten_spectra_kernel(const float2* __re
     }
 }
 
-// FP64 sum of |S(f)|^2 over the rows of chunk blockIdx.y: part[chunk][f]
-__global__ void whiten_power_kernel(const float2* __restrict__ S, long long rows, int n, int nchunks,
-                                    double* __restrict__ part) {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= n) return;
-    const long long r0 = rows * blockIdx.y / nchunks, r1 = rows * (blockIdx.y + 1) / nchunks;
-    double acc = 0.0;
-    for (long long r = r0; r < r1; ++r) {
-        const float2 v = S[r * n + f];
-        acc += (double)v.x * v.x + (double)v.y * v.y;
-    }
-    part[(size_t)blockIdx.y * n + f] = acc;
+// Sum of |S(f)|^2 over the rows of chunk blockIdx.y: part[chunk][f].  Two
+// bins a thread (16-byte loads, eight rows in flight); |S|^2 in FP32, summed
+// in FP32 over runs of 32 rows, the runs added in FP64 (FP64 arithmetic is a
+// small fraction of the FP32 rate on this part).  n even; VEC: S 16-byte
+// aligned (else the two bins are read as two 8-byte loads).
+constexpr int WP_RUN = 32;
+template <bool VEC>
+__device__ __forceinline__ float4 load_bins2(const float2* S, long long i) {
+    if constexpr (VEC) return reinterpret_cast<const float4*>(S)[i];
+    const float2 a = S[2 * i], b = S[2 * i + 1];
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// P(f) = sum over CTAs in order / rows; then (one CTA) the gain sqrt(G / max G)
+template <bool VEC>
+__global__ void __launch_bounds__(256) whiten_power_kernel(const float2* __restrict__ S, long long rows, int n,
+                                                           int nchunks, double* __restrict__ part) {
+    const int f2 = blockIdx.x * blockDim.x + threadIdx.x;     // bins 2 f2, 2 f2 + 1
+    if (2 * f2 >= n) return;
+    const long long r0 = rows * blockIdx.y / nchunks, r1 = rows * (blockIdx.y + 1) / nchunks;
+    const long long n2 = n / 2;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (long long ra = r0; ra < r1; ra += WP_RUN) {
+        const long long rb = ra + WP_RUN < r1 ? ra + WP_RUN : r1;
+        float s0 = 0.f, s1 = 0.f;
+        long long r = ra;
+        for (; r + 8 <= rb; r += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = load_bins2<VEC>(S, (r + u) * n2 + f2);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s0 = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, s0));
+                s1 = fmaf(v[u].z, v[u].z, fmaf(v[u].w, v[u].w, s1));
+            }
+        }
+        for (; r < rb; ++r) {
+            const float4 v = load_bins2<VEC>(S, r * n2 + f2);
+            s0 = fmaf(v.x, v.x, fmaf(v.y, v.y, s0));
+            s1 = fmaf(v.z, v.z, fmaf(v.w, v.w, s1));
+        }
+        acc0 += (double)s0;
+        acc1 += (double)s1;
+    }
+    part[(size_t)blockIdx.y * n + 2 * f2] = acc0;
+    part[(size_t)blockIdx.y * n + 2 * f2 + 1] = acc1;
+}
+
+// P(f) = sum over the chunks in order / rows
 __global__ void whiten_reduce_kernel(const double* __restrict__ part, int nparts, int n, long long rows,
                                      double* __restrict__ P) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,27 +190,41 @@ __global__ void whiten_reduce_kernel(const double* __restrict__ part, int nparts
     P[f] = s / (double)rows;
 }
 
-__global__ void whiten_gain_kernel(const double* __restrict__ P, int n, double gamma, float* __restrict__ gain) {
-    __shared__ double red[1024];
-    __shared__ double pmin_s[1024];
+// one CTA: stats = {gamma mean_f P + min_f P} (the numerator of G / max G)
+__global__ void __launch_bounds__(1024) whiten_stats_kernel(const double* __restrict__ P, int n, double gamma,
+                                                            double* __restrict__ stats) {
+    __shared__ double red[32], mn[32];
     double s = 0.0, pmin = 1.0 / 0.0;
     for (int f = threadIdx.x; f < n; f += blockDim.x) {
         s += P[f];
         pmin = fmin(pmin, P[f]);
     }
-    red[threadIdx.x] = s;
-    pmin_s[threadIdx.x] = pmin;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-        if ((int)threadIdx.x < o) {
-            red[threadIdx.x] += red[threadIdx.x + o];
-            pmin_s[threadIdx.x] = fmin(pmin_s[threadIdx.x], pmin_s[threadIdx.x + o]);
-        }
-        __syncthreads();
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        pmin = fmin(pmin, __shfl_xor_sync(0xffffffffu, pmin, o));
     }
-    const double pbar = red[0] / (double)n;
-    const double gmax = 1.0 / (gamma * pbar + pmin_s[0]);
-    for (int f = threadIdx.x; f < n; f += blockDim.x) gain[f] = (float)sqrt((1.0 / (gamma * pbar + P[f])) / gmax);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s;
+        mn[threadIdx.x >> 5] = pmin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0, m = 1.0 / 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += red[w];
+            m = fmin(m, mn[w]);
+        }
+        stats[0] = gamma * (t / (double)n);
+        stats[1] = stats[0] + m;
+    }
+}
+
+// gain(f) = sqrt(G(f) / max G) = sqrt((gamma Pbar + Pmin) / (gamma Pbar + P(f)))
+__global__ void whiten_gain_kernel(const double* __restrict__ P, int n, const double* __restrict__ stats,
+                                   float* __restrict__ gain) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    gain[f] = (float)sqrt(stats[1] / (stats[0] + P[f]));
 }
 
 // pass 2: out[r] = IFFT(out[r] * gain) (the spectra from pass 1)
@@ -687,8 +734,9 @@ extern "C" int sas_whiten(const void* d_in, void* d_out, int64_t rows, int32_t n
     double* part = nullptr;
     double* P = nullptr;
     float* gain = d_gain;
-    SAS_CUDA(cudaMallocAsync((void**)&part, sizeof(double) * ((size_t)nparts * n + n), st));
+    SAS_CUDA(cudaMallocAsync((void**)&part, sizeof(double) * ((size_t)nparts * n + n + 2), st));
     P = part + (size_t)nparts * n;
+    double* wstats = P + n;
     float* own_gain = nullptr;
     int rc = SAS_OK;
     if (!gain) {
@@ -711,10 +759,14 @@ extern "C" int sas_whiten(const void* d_in, void* d_out, int64_t rows, int32_t n
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        whiten_power_kernel<<<dim3((n + 255) / 256, nparts), 256, 0, st>>>((const float2*)d_out, rows, n, nparts,
-                                                                           part);
+        const dim3 pgrid((n / 2 + 255) / 256, nparts);
+        if (((uintptr_t)d_out & 15) == 0)
+            whiten_power_kernel<true><<<pgrid, 256, 0, st>>>((const float2*)d_out, rows, n, nparts, part);
+        else
+            whiten_power_kernel<false><<<pgrid, 256, 0, st>>>((const float2*)d_out, rows, n, nparts, part);
         whiten_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(part, nparts, n, rows, P);
-        whiten_gain_kernel<<<1, 1024, 0, st>>>(P, n, gamma, gain);
+        whiten_stats_kernel<<<1, 1024, 0, st>>>(P, n, gamma, wstats);
+        whiten_gain_kernel<<<(n + 255) / 256, 256, 0, st>>>(P, n, wstats, gain);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && !whiten_reg_dispatch(n, true, nullptr, (float2*)d_out, rows, gain, st, &e)) {

@@ -78,6 +78,20 @@ def test_whitening_matches_oracle(rows, n, gamma):
     assert oracle.rel_l2(d_in.cpu().numpy(), ref) < 1e-5
 
 
+def test_whitening_output_not_16_byte_aligned():
+    """An output that starts 8 bytes past a 16-byte boundary (a complex64 view
+    one element in) takes the 8-byte-load path of the power sums."""
+    rows, n, gamma = 6, 2048, 0.1
+    e = _colored(rows, n, 77)
+    store = torch.empty(rows * n + 1, dtype=torch.complex64, device="cuda")
+    out = store[1:].view(rows, n)
+    assert out.data_ptr() % 16 == 8
+    sas.sas_whiten(torch.from_numpy(e).cuda(), out, rows, n, gamma)
+    torch.cuda.synchronize()
+    ref, _ = cond.whiten(e, gamma)
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5
+
+
 @pytest.mark.parametrize("rows,n,alpha", [(41, 300, 0.0), (64, 333, 0.25), (1, 40, 0.1), (2, 65, 0.0)])
 def test_tvg_matches_oracle(rows, n, alpha):
     rng = np.random.default_rng(rows * n)
