@@ -61,7 +61,9 @@ struct RegPlan {
     static constexpr int B = fftreg::points_b<N>(), P = 16 * B, T = N / P;
     static constexpr int G = T >= 256 ? 1 : 256 / T, THREADS = T * G;
     static constexpr int MINB = THREADS <= 256 ? 2 : 1;     // at most 128 registers a thread
-    static constexpr size_t SMEM = sizeof(float2) * ((size_t)G * fftreg::padded(N) + N / 2);
+    // the matched filter's 16-point rows fit 80 registers without spills: three CTAs an SM
+    static constexpr int MINB_MF = B == 1 ? 3 : MINB;
+    static constexpr size_t SMEM = sizeof(float2) * ((size_t)G * fftreg::padded(N) + fftreg::tpad_size(N / 2));
 };
 
 // One group per (row, block of M outputs): circular correlation of NF inputs
@@ -69,14 +71,14 @@ struct RegPlan {
 // through the spectra: IFFT(FFT(x) Pc); the first M outputs are the linear
 // correlation.
 template <int NF>
-__global__ void __launch_bounds__(RegPlan<NF>::THREADS, RegPlan<NF>::MINB) mf_reg_kernel(const float2* __restrict__ raw, int n, int M,
+__global__ void __launch_bounds__(RegPlan<NF>::THREADS, RegPlan<NF>::MINB_MF) mf_reg_kernel(const float2* __restrict__ raw, int n, int M,
                                                                       int nblk, long long items,
                                                                       const float2* __restrict__ Pc,
                                                                       float2* __restrict__ out) {
     using RP = RegPlan<NF>;
     extern __shared__ float2 sm[];
     float2* tw = sm + RP::G * fftreg::padded(NF);
-    fftdev::fft_twiddles(tw, NF);
+    fftreg::twiddles(tw, NF);
     const int g = threadIdx.x / RP::T, tid = threadIdx.x % RP::T;
     const long long item = (long long)blockIdx.x * RP::G + g;
     const bool live = item < items;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(RegPlan<N>::THREADS, RegPlan<N>::MINB) whiten_
     using RP = RegPlan<N>;
     extern __shared__ float2 sm[];
     float2* tw = sm + RP::G * fftreg::padded(N);
-    fftdev::fft_twiddles(tw, N);
+    fftreg::twiddles(tw, N);
     const int g = threadIdx.x / RP::T, tid = threadIdx.x % RP::T;
     float2* rowbuf = sm + g * fftreg::padded(N);
     for (long long r0 = (long long)blockIdx.x * RP::G; r0 < rows; r0 += (long long)gridDim.x * RP::G) {
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(RegPlan<N>::THREADS, RegPlan<N>::MINB) whiten_
     using RP = RegPlan<N>;
     extern __shared__ float2 sm[];
     float2* tw = sm + RP::G * fftreg::padded(N);
-    fftdev::fft_twiddles(tw, N);
+    fftreg::twiddles(tw, N);
     const int g = threadIdx.x / RP::T, tid = threadIdx.x % RP::T;
     float2* rowbuf = sm + g * fftreg::padded(N);
     const float inv = 1.f / (float)N;

@@ -15,10 +15,12 @@
 // and leaves its output in registers, with one shared-memory exchange between
 // consecutive stages (3 for N = 16384; the radix-4 form in fft.cuh makes 7
 // passes).  Forward (s = -1): X[f] = sum_n x[n] exp(-2 pi i f n / N); inverse
-// (s = +1): +i and no 1/N.  Twiddles from the half table tw[j] =
-// exp(-2 pi i j / N), j < N / 2, that fft_twiddles fills (exp(-2 pi i j / N)
-// = -tw[j - N/2] above it): w, w^2, w^3, w^4, w^8, w^12 looked up, the other
-// powers one product of two of them.
+// (s = +1): +i and no 1/N.  Twiddles from the half table exp(-2 pi i j / N),
+// j < N / 2 (exp(-2 pi i j / N) = -tw(j - N/2) above it), stored at
+// tpad(j) = j + j/16 + j/256: a stage reads w^h at h k N / (R L) for the lanes'
+// consecutive k, power-of-two strides that the skew spreads over the banks
+// (about 1.5 wavefronts a request instead of 4 to 10 unskewed): w, w^2, w^3,
+// w^4, w^8, w^12 looked up, the other powers one product of two of them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,6 +43,20 @@ __device__ __forceinline__ float2 mul_si(float2 a) {
 // shared-memory index of row position i: one pad point every 16
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded(int n) { return n + n / 16; }
+
+// twiddle table: entry j at tpad(j); tpad_size(n2) entries hold j < n2
+__device__ __forceinline__ int tpad(int j) { return j + (j >> 4) + (j >> 8); }
+__host__ __device__ constexpr int tpad_size(int n2) { return n2 + n2 / 16 + n2 / 256 + 1; }
+
+// tw(j) = exp(-2 pi i j / N), j < N / 2, filled by the block
+__device__ void twiddles(float2* tw, int N) {
+    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
+        float s, c;
+        sincospif(-2.f * (float)j / (float)N, &s, &c);
+        tw[tpad(j)] = make_float2(c, s);
+    }
+    __syncthreads();
+}
 
 template <bool FWD>
 __device__ __forceinline__ void dft2(float2& a0, float2& a1) {
@@ -125,7 +141,7 @@ __device__ __forceinline__ void dft(float2 (&a)[R]) {
 // exp(s 2 pi i t / N) from the half table
 template <int N, bool FWD>
 __device__ __forceinline__ float2 twiddle(const float2* tw, int t) {
-    float2 v = t < N / 2 ? tw[t] : tw[t - N / 2];
+    float2 v = t < N / 2 ? tw[tpad(t)] : tw[tpad(t - N / 2)];
     if (t >= N / 2) v = make_float2(-v.x, -v.y);
     return FWD ? v : make_float2(v.x, -v.y);
 }
@@ -192,7 +208,7 @@ __device__ __forceinline__ void stages(float2 (&x)[16 * B], float2* row, const f
 
 // The transform of the row whose natural slots thread tid (< N / (16 B)) of
 // its group holds in x; row: the group's padded shared buffer (padded(N)
-// points); tw: the N/2-point table.  Every thread of the block calls it (the
+// points); tw: the table that twiddles() fills (tpad_size(N / 2) points).  Every thread of the block calls it (the
 // exchanges synchronise the block).
 template <int N, int B, bool FWD>
 __device__ __forceinline__ void fft(float2 (&x)[16 * B], float2* row, const float2* tw, int tid) {
