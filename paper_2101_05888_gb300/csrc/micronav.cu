@@ -20,7 +20,6 @@ namespace sas {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int DPC_WARPS = 8;      // delay windows per block
 constexpr int BANDW = 7;          // half-bandwidth of the normal matrix
 constexpr int BROW = BANDW + 1;   // stored diagonals per row
 
@@ -29,10 +28,6 @@ constexpr int BROW = BANDW + 1;   // stored diagonals per row
 
 template <typename ET>
 __device__ __forceinline__ float2 echo_at(const ET* row, int n, float sc);
-template <>
-__device__ __forceinline__ float2 echo_at<float2>(const float2* row, int n, float) {
-    return row[n];
-}
 template <>
 __device__ __forceinline__ float2 echo_at<__half2>(const __half2* row, int n, float sc) {
     const float2 v = __half22float2(row[n]);
@@ -44,118 +39,227 @@ __device__ __forceinline__ float2 echo_at<__nv_bfloat162>(const __nv_bfloat162* 
     return make_float2(v.x * sc, v.y * sc);
 }
 
-// One warp per measurement m = ((i (C - shift) + c) K + k); lane l holds the
-// lag tau = l - L.  e1 = ping i, receiver c + shift; e2 = ping i + 1, receiver c.
-// The window is walked in chunks of DPC_CH samples: the warp stages e2[n ..
-// n + CH) and e1[n - L .. n + CH + L) in shared memory with coalesced loads
-// (zero outside the rows), then every lane reads e2 (broadcast) and its
-// shifted e1 (consecutive lanes, consecutive words) from there.
-constexpr int DPC_CH = 256;
+// One thread per measurement m = ((i (C - shift) + c) K + k), 32 consecutive
+// m to a warp: e1 = ping i, receiver c + shift; e2 = ping i + 1, receiver c;
+// R(tau) = sum_n e2[n] conj(e1[n - tau]) over the window, tau = -L .. L, all
+// 2L + 1 lags accumulated in the thread's registers: with e2 = (bx, by),
+// R += (bx, by) (ax, ax) + (by, -bx) (ay, ay), two packed FP32x2 FMAs.  The
+// window is walked in chunks of DPC_CH samples: per chunk the warp stages,
+// for each of its 32 windows in turn, e2[nb .. nb + CH) and e1[nb - L .. nb +
+// CH + L) in shared memory (coalesced row runs, zero outside the rows and, for
+// e2, past the window); e1 is stored as (ax, ax, ay, ay) so that one 16-byte
+// load gives both operand pairs.  Rows have odd strides, so the 32 threads,
+// each reading its own window, hit distinct banks.  Energies: sum |e2|^2 over
+// the window, and for e1 the total over [n0 - L, n0 + W + L) with its first
+// 2L terms kept; the energy under the peak lag is that total less the head
+// before and the tail after the shifted window.
+constexpr int DPC_TW = 2;         // warps per block
+constexpr int DPC_CH = 32;        // samples per window and chunk
 constexpr int DPC_MAXL = 15;
-template <typename ET>
-__global__ void __launch_bounds__(32 * DPC_WARPS)
-    dpc_delay_kernel(const ET* __restrict__ echo, const float* __restrict__ scale, int C, int Ns, int shift,
-                     const int* __restrict__ centres, int K, int W, int L, long long M, float inv_fs,
+
+template <int L>
+struct DpcShape {
+    static constexpr int NL = 2 * L + 1;
+    static constexpr int S2 = DPC_CH + 1;            // odd row strides
+    static constexpr int S1 = DPC_CH + 2 * L + 1;
+    static constexpr int NH = L > 0 ? 2 * L : 1;     // head energies kept per window
+    static constexpr int U = L <= 8 ? 8 : 4;         // samples per register block
+    static constexpr size_t PAR = 32 * 32;           // window table: 32 B a window
+    static constexpr size_t WARP_BYTES =
+        PAR + sizeof(float4) * 32 * S1 + sizeof(float2) * 32 * S2 + sizeof(float) * 32 * NH;
+    static constexpr size_t SMEM = DPC_TW * WARP_BYTES;
+};
+
+struct DpcWin {
+    long long e1, e2;   // element offsets of the rows of e1 and e2
+    int n0, live;
+    float sc1, sc2;
+};
+
+__device__ __forceinline__ float2 dpc_load(const void* echo, int dtype, long long idx, float sc) {
+    if (dtype == SAS_ECHO_C64) return static_cast<const float2*>(echo)[idx];
+    if (dtype == SAS_ECHO_C32_F16) return echo_at<__half2>(static_cast<const __half2*>(echo) + idx, 0, sc);
+    return echo_at<__nv_bfloat162>(static_cast<const __nv_bfloat162*>(echo) + idx, 0, sc);
+}
+
+template <int L>
+__global__ void __launch_bounds__(32 * DPC_TW)
+    dpc_delay_kernel(const void* __restrict__ echo, int dtype, const float* __restrict__ scale, int C, int Ns,
+                     int shift, const int* __restrict__ centres, int K, int W, long long M, float inv_fs,
                      float inv_wfc, double* __restrict__ coarse, double* __restrict__ fine,
                      double* __restrict__ rho) {
-    __shared__ float2 stage[DPC_WARPS][2 * DPC_CH + 2 * DPC_MAXL];
-    const long long m = (long long)blockIdx.x * DPC_WARPS + (threadIdx.x >> 5);
-    if (m >= M) return;   // whole warps
-    const int lane = threadIdx.x & 31;
-    float2* s2 = stage[threadIdx.x >> 5];          // [DPC_CH] e2
-    float2* s1 = s2 + DPC_CH;                      // [DPC_CH + 2L] e1 from n - L
-    const int nc = C - shift;
-    const int k = (int)(m % K);
-    const long long pr = m / K;
-    const int c = (int)(pr % nc);
-    const long long i = pr / nc;
-    const size_t r1 = (size_t)i * C + c + shift, r2 = (size_t)(i + 1) * C + c;
-    const float sc1 = scale ? scale[r1] : 1.f, sc2 = scale ? scale[r2] : 1.f;
-    const ET* e1 = echo + r1 * (size_t)Ns;
-    const ET* e2 = echo + r2 * (size_t)Ns;
-    const int n0 = centres[k] - W / 2;
-    const int tau = lane - L;
-    const bool lag = lane <= 2 * L;
-    float ar = 0.f, ai = 0.f, p1 = 0.f, p2 = 0.f;   // R(tau); sum |e1[n - tau]|^2; sum |e2[n]|^2
-    for (int nb = n0; nb < n0 + W; nb += DPC_CH) {
-        const int len = min(DPC_CH, n0 + W - nb);
-        __syncwarp();
-        for (int j = lane; j < len; j += 32) {
-            const int n = nb + j;
-            s2[j] = (n >= 0 && n < Ns) ? echo_at<ET>(e2, n, sc2) : make_float2(0.f, 0.f);
-        }
-        for (int j = lane; j < len + 2 * L; j += 32) {
-            const int n = nb - L + j;
-            s1[j] = (n >= 0 && n < Ns) ? echo_at<ET>(e1, n, sc1) : make_float2(0.f, 0.f);
-        }
-        __syncwarp();
-        if (lag) {
-            // e1[n - tau] = s1[(n - nb) + L - tau]; two interleaved partial sums
-            // (even and odd samples) halve the FMA dependency chains
-            const float2* a1 = s1 + (L - tau);
-            float br_ = 0.f, bi_ = 0.f, q1_ = 0.f, q2_ = 0.f;
-            int j = 0;
-#pragma unroll 2
-            for (; j + 1 < len; j += 2) {
-                const float2 b2 = s2[j], b1 = a1[j], c2 = s2[j + 1], c1 = a1[j + 1];
-                ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));       // e2 conj(e1)
-                ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
-                p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
-                p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
-                br_ = fmaf(c2.x, c1.x, fmaf(c2.y, c1.y, br_));
-                bi_ = fmaf(c2.y, c1.x, fmaf(-c2.x, c1.y, bi_));
-                q1_ = fmaf(c1.x, c1.x, fmaf(c1.y, c1.y, q1_));
-                q2_ = fmaf(c2.x, c2.x, fmaf(c2.y, c2.y, q2_));
+    using S = DpcShape<L>;
+    constexpr int NL = S::NL, U = S::U;
+    extern __shared__ __align__(16) unsigned char dpc_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* base = dpc_smem + warp * S::WARP_BYTES;
+    DpcWin* win = reinterpret_cast<DpcWin*>(base);                            // [32]
+    float4* s1 = reinterpret_cast<float4*>(base + S::PAR);                    // [32][S1] (ax, ax, ay, ay)
+    float2* s2 = reinterpret_cast<float2*>(s1 + 32 * S::S1);                  // [32][S2]
+    float* eh = reinterpret_cast<float*>(s2 + 32 * S::S2);                    // [32][NH]
+    const long long m0 = ((long long)blockIdx.x * DPC_TW + warp) * 32;
+    if (m0 >= M) return;   // whole warps
+    const long long m = m0 + lane;
+    const bool live = m < M;
+    {
+        DpcWin wn = {0, 0, 0, 0, 1.f, 1.f};
+        if (live) {
+            const int nc = C - shift;
+            const int k = (int)(m % K);
+            const long long pr = m / K;
+            const int c = (int)(pr % nc);
+            const long long i = pr / nc;
+            const long long r1 = i * C + c + shift, r2 = (i + 1) * C + c;
+            wn.e1 = r1 * Ns;
+            wn.e2 = r2 * Ns;
+            wn.n0 = centres[k] - W / 2;
+            wn.live = 1;
+            if (scale) {
+                wn.sc1 = scale[r1];
+                wn.sc2 = scale[r2];
             }
-            if (j < len) {
-                const float2 b2 = s2[j], b1 = a1[j];
-                ar = fmaf(b2.x, b1.x, fmaf(b2.y, b1.y, ar));
-                ai = fmaf(b2.y, b1.x, fmaf(-b2.x, b1.y, ai));
-                p1 = fmaf(b1.x, b1.x, fmaf(b1.y, b1.y, p1));
-                p2 = fmaf(b2.x, b2.x, fmaf(b2.y, b2.y, p2));
-            }
-            ar += br_;
-            ai += bi_;
-            p1 += q1_;
-            p2 += q2_;
         }
+        win[lane] = wn;
     }
-    const float mag = lag ? sqrtf(fmaf(ar, ar, ai * ai)) : -1.f;
-    // largest |R|, the lowest lag on ties
-    float best = mag;
-    int bl = lane;
+    float2 acc[NL];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float ob = __shfl_xor_sync(FULL, best, o);
-        const int ol = __shfl_xor_sync(FULL, bl, o);
-        if (ob > best || (ob == best && ol < bl)) {
-            best = ob;
-            bl = ol;
+    for (int t = 0; t < NL; ++t) acc[t] = make_float2(0.f, 0.f);
+    float2 p2v = make_float2(0.f, 0.f);   // sum |e2|^2 (two partial sums)
+    float etot = 0.f;                     // sum |e1|^2 over [n0 - L, n0 + W + L)
+    const float4* a1 = s1 + lane * S::S1;
+    const float2* b2s = s2 + lane * S::S2;
+    int len = 0;
+    for (int off = 0; off < W; off += DPC_CH) {
+        len = min(DPC_CH, W - off);
+        __syncwarp();
+        // eight windows at a time: all their loads issued before the stores
+        constexpr int SW = 8, J1 = (DPC_CH + 2 * L + 31) / 32;   // e1 loads a lane makes per window
+        for (int w0 = 0; w0 < 32; w0 += SW) {
+            float2 v2[SW], v1[SW][J1];
+#pragma unroll
+            for (int u = 0; u < SW; ++u) {
+                const DpcWin wn = win[w0 + u];
+                const int nb = wn.n0 + off;
+                const int n = nb + lane;
+                v2[u] = make_float2(0.f, 0.f);
+                if (wn.live && lane < len && n >= 0 && n < Ns) v2[u] = dpc_load(echo, dtype, wn.e2 + n, wn.sc2);
+#pragma unroll
+                for (int h = 0; h < J1; ++h) {
+                    const int j = lane + 32 * h, n1 = nb - L + j;
+                    v1[u][h] = make_float2(0.f, 0.f);
+                    if (wn.live && j < DPC_CH + 2 * L && n1 >= 0 && n1 < Ns)
+                        v1[u][h] = dpc_load(echo, dtype, wn.e1 + n1, wn.sc1);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SW; ++u) {
+                s2[(w0 + u) * S::S2 + lane] = v2[u];
+#pragma unroll
+                for (int h = 0; h < J1; ++h) {
+                    const int j = lane + 32 * h;
+                    if (j < DPC_CH + 2 * L) s1[(w0 + u) * S::S1 + j] = make_float4(v1[u][h].x, v1[u][h].x, v1[u][h].y, v1[u][h].y);
+                }
+            }
+        }
+        __syncwarp();
+        // e1 energy: the staged samples [nb + L, nb + L + len); in the first
+        // chunk also [n0 - L, n0 + L), kept for the head sums
+        if (off == 0) {
+#pragma unroll
+            for (int q = 0; q < 2 * L; ++q) {
+                const float4 v = a1[q];
+                const float e = fmaf(v.x, v.x, v.z * v.z);
+                eh[lane * S::NH + q] = e;
+                etot += e;
+            }
+        }
+        for (int q = 0; q < len; ++q) {
+            const float4 v = a1[2 * L + q];
+            etot = fmaf(v.x, v.x, fmaf(v.z, v.z, etot));
+        }
+        // R(tau) over the chunk (e2 is zero past the window)
+#pragma unroll 1
+        for (int j0 = 0; j0 < DPC_CH; j0 += U) {
+            float2 bv[U], bs[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                bv[u] = b2s[j0 + u];
+                bs[u] = make_float2(bv[u].y, -bv[u].x);
+                p2v = ffma2(bv[u], bv[u], p2v);
+            }
+            // e1 staged at j0 + q serves sample j0 + u at lag t = u + 2L - q
+#pragma unroll
+            for (int q = 0; q < U + 2 * L; ++q) {
+                const float4 a = a1[j0 + q];
+                const float2 ax = make_float2(a.x, a.y), ay = make_float2(a.z, a.w);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = u + 2 * L - q;
+                    if (t >= 0 && t < NL) {
+                        acc[t] = ffma2(bv[u], ax, acc[t]);
+                        acc[t] = ffma2(bs[u], ay, acc[t]);
+                    }
+                }
+            }
         }
     }
-    const int lm = max(bl - 1, 0), lp = min(bl + 1, 31);
-    const float mm = __shfl_sync(FULL, mag, lm), mp = __shfl_sync(FULL, mag, lp);
-    const float rr0 = __shfl_sync(FULL, ar, bl), ri0 = __shfl_sync(FULL, ai, bl);
-    const float rrm = __shfl_sync(FULL, ar, lm), rim = __shfl_sync(FULL, ai, lm);
-    const float rrp = __shfl_sync(FULL, ar, lp), rip = __shfl_sync(FULL, ai, lp);
-    const float q1 = __shfl_sync(FULL, p1, bl);
-    if (lane == 0) {
-        float d = 0.f, Rr = rr0, Ri = ri0;
-        if (bl > 0 && bl < 2 * L) {
-            const float den = mm - 2.f * best + mp;
-            d = den != 0.f ? 0.5f * (mm - mp) / den : 0.f;
-            Rr = rr0 + 0.5f * d * (rrp - rrm) + 0.5f * d * d * (rrp - 2.f * rr0 + rrm);
-            Ri = ri0 + 0.5f * d * (rip - rim) + 0.5f * d * d * (rip - 2.f * ri0 + rim);
-        }
-        // FP32 epilogue (FP64 arithmetic is slow on this part; the outputs
-        // carry FP32 accuracy anyway), widened on the store
-        if (coarse) coarse[m] = (double)(((float)(bl - L) + d) * inv_fs);
-        if (fine) fine[m] = (double)(-atan2f(Ri, Rr) * inv_wfc);
-        if (rho) {
-            const float den2 = p2 * q1;
-            rho[m] = den2 > 0.f ? (double)(best * rsqrtf(den2)) : 0.0;
+    if (!live) return;
+    // largest |R|, the lowest lag on ties
+    float best2 = -1.f;
+    int bl = 0;
+#pragma unroll
+    for (int t = 0; t < NL; ++t) {
+        const float q = fmaf(acc[t].x, acc[t].x, acc[t].y * acc[t].y);
+        if (q > best2) {
+            best2 = q;
+            bl = t;
         }
     }
+    float2 R0 = acc[0], Rm = acc[0], Rp = acc[0];
+#pragma unroll
+    for (int t = 0; t < NL; ++t) {
+        if (t == bl) R0 = acc[t];
+        if (t == bl - 1) Rm = acc[t];
+        if (t == bl + 1) Rp = acc[t];
+    }
+    const float best = sqrtf(best2);
+    float d = 0.f, Rr = R0.x, Ri = R0.y;
+    if (bl > 0 && bl < 2 * L) {
+        const float mm = sqrtf(fmaf(Rm.x, Rm.x, Rm.y * Rm.y)), mp = sqrtf(fmaf(Rp.x, Rp.x, Rp.y * Rp.y));
+        const float den = mm - 2.f * best + mp;
+        d = den != 0.f ? 0.5f * (mm - mp) / den : 0.f;
+        Rr = R0.x + 0.5f * d * (Rp.x - Rm.x) + 0.5f * d * d * (Rp.x - 2.f * R0.x + Rm.x);
+        Ri = R0.y + 0.5f * d * (Rp.y - Rm.y) + 0.5f * d * d * (Rp.y - 2.f * R0.y + Rm.y);
+    }
+    // FP32 epilogue (FP64 arithmetic is slow on this part; the outputs carry
+    // FP32 accuracy anyway), widened on the store
+    if (coarse) coarse[m] = (double)(((float)(bl - L) + d) * inv_fs);
+    if (fine) fine[m] = (double)(-atan2f(Ri, Rr) * inv_wfc);
+    if (rho) {
+        // e1 energy under the peak lag tau = bl - L: the window [n0 - tau, n0 - tau + W)
+        // is the extended range less its first 2L - bl and its last bl terms
+        float head = 0.f, tail = 0.f;
+        for (int q = 0; q < 2 * L - bl; ++q) head += eh[lane * S::NH + q];
+        for (int q = 0; q < bl; ++q) {
+            const float4 v = a1[len + 2 * L - 1 - q];
+            tail = fmaf(v.x, v.x, fmaf(v.z, v.z, tail));
+        }
+        const float q1 = etot - head - tail, den2 = (p2v.x + p2v.y) * q1;
+        rho[m] = den2 > 0.f ? (double)(best * rsqrtf(den2)) : 0.0;
+    }
+}
+
+template <int L>
+cudaError_t dpc_delay_launch(const void* echo, int dtype, const float* scale, int C, int Ns, int shift,
+                             const int* centres, int K, int W, long long M, float inv_fs, float inv_wfc,
+                             double* coarse, double* fine, double* rho, cudaStream_t st) {
+    using S = DpcShape<L>;
+    cudaError_t e = cudaFuncSetAttribute(dpc_delay_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long warps = (M + 31) / 32;
+    dpc_delay_kernel<L><<<(unsigned)((warps + DPC_TW - 1) / DPC_TW), 32 * DPC_TW, S::SMEM, st>>>(
+        echo, dtype, scale, C, Ns, shift, centres, K, W, M, inv_fs, inv_wfc, coarse, fine, rho);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -658,25 +762,20 @@ extern "C" int sas_dpc_delays(sas_geometry_t h, int32_t shift, const int32_t* d_
     }
     const long long M = (long long)(h->P - 1) * (h->C - shift) * K;
     cudaStream_t st = (cudaStream_t)stream;
-    const int grid = blocks_for(M, DPC_WARPS);
     const float inv_fs = (float)(1.0 / h->sig.fs), inv_wfc = (float)(1.0 / (2.0 * M_PI * h->sig.fc));
-    switch (h->echo_dtype) {
-        case SAS_ECHO_C64:
-            dpc_delay_kernel<float2><<<grid, 32 * DPC_WARPS, 0, st>>>((const float2*)h->d_echo, nullptr, h->C, h->Ns,
-                                                                      shift, d_centres, K, W, max_lag, M, inv_fs, inv_wfc,
-                                                                      d_coarse, d_fine, d_rho);
-            break;
-        case SAS_ECHO_C32_F16:
-            dpc_delay_kernel<__half2><<<grid, 32 * DPC_WARPS, 0, st>>>((const __half2*)h->d_echo, h->d_scale, h->C,
-                                                                       h->Ns, shift, d_centres, K, W, max_lag, M, inv_fs,
-                                                                       inv_wfc, d_coarse, d_fine, d_rho);
-            break;
-        default:
-            dpc_delay_kernel<__nv_bfloat162><<<grid, 32 * DPC_WARPS, 0, st>>>(
-                (const __nv_bfloat162*)h->d_echo, h->d_scale, h->C, h->Ns, shift, d_centres, K, W, max_lag, M, inv_fs, inv_wfc,
-                d_coarse, d_fine, d_rho);
-            break;
+    const float* sc = h->echo_dtype == SAS_ECHO_C64 ? nullptr : h->d_scale;
+    cudaError_t e = cudaSuccess;
+#define SAS_DPC_L(LL)                                                                                             \
+    case LL:                                                                                                      \
+        e = dpc_delay_launch<LL>(h->d_echo, h->echo_dtype, sc, h->C, h->Ns, shift, d_centres, K, W, M, inv_fs,    \
+                                 inv_wfc, d_coarse, d_fine, d_rho, st);                                           \
+        break;
+    switch (max_lag) {
+        SAS_DPC_L(0) SAS_DPC_L(1) SAS_DPC_L(2) SAS_DPC_L(3) SAS_DPC_L(4) SAS_DPC_L(5) SAS_DPC_L(6) SAS_DPC_L(7)
+        SAS_DPC_L(8) SAS_DPC_L(9) SAS_DPC_L(10) SAS_DPC_L(11) SAS_DPC_L(12) SAS_DPC_L(13) SAS_DPC_L(14) SAS_DPC_L(15)
     }
+#undef SAS_DPC_L
+    SAS_CUDA(e);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }

@@ -137,6 +137,57 @@ def test_delays_match_oracle():
     geom.close()
 
 
+@pytest.mark.parametrize("W,L,edge", [(100, 3, False), (128, 15, False), (37, 0, False), (64, 8, True),
+                                      (130, 8, True)])
+def test_delay_shapes_match_oracle(W, L, edge):
+    """Window lengths that are not a multiple of the 32-sample staging chunk,
+    no lag search (L = 0) and the widest one (L = 15), windows that run past
+    either end of the rows (zero there), and a last warp of measurements only
+    partly filled (M = 5 x 6 x 10 = 300): rows where ping i + 1, receiver c
+    repeats ping i, receiver c + 2, three samples later, under noise."""
+    pl, vy, vz, _ = _scene(P=6, K=10)
+    P, C, Ns, shift, K = 6, 8, 1024, 2, 10
+    rng = np.random.default_rng(W + 10 * L)
+    noise = lambda: rng.normal(size=Ns) + 1j * rng.normal(size=Ns)
+    echo = np.zeros((P, C, Ns), complex)
+    for c in range(C):
+        echo[0, c] = noise()
+    for i in range(1, P):
+        for c in range(C):
+            echo[i, c] = np.roll(echo[i - 1, c + shift], 3) * 0.9 + 0.3 * noise() if c + shift < C else noise()
+    if edge:
+        centres = np.concatenate([[5, Ns - 3], np.linspace(100, Ns - 100, K - 2)])
+    else:
+        centres = np.linspace(80, Ns - 80, K)
+    centres = np.round(centres).astype(np.int32)
+    p = mn.positions(pl, vy, vz)
+    geom = sas.Geometry(p, pl.att, pl.tx_lever, pl.rx_lever, sas.make_signal(FC, FS, C_SOUND, 0.0, Ns))
+    geom.upload_echo(echo.astype(np.complex64))
+    nc = C - shift
+    M = (P - 1) * nc * K
+    co, fi, rh = (torch.empty(M, dtype=torch.float64, device="cuda") for _ in range(3))
+    sas.sas_dpc_delays(geom.h, shift, _dev(centres, torch.int32), K, W, L, co, fi, rh)
+    torch.cuda.synchronize()
+    co, fi, rh = co.cpu().numpy(), fi.cpu().numpy(), rh.cpu().numpy()
+    e32 = echo.astype(np.complex64).astype(np.complex128)
+    checked = 0
+    for m in range(M):
+        i, c, k = m // (nc * K), (m // K) % nc, m % K
+        R = np.abs(mn.correlate(e32[i, c + shift], e32[i + 1, c], int(centres[k]), W, L))
+        top = np.sort(R)[-2:]
+        if L > 0 and top[1] < top[0] * (1 + 1e-4):
+            continue                                    # near-tie of the peak lag: FP32 and FP64 may differ
+        rc, rf, rr = mn.estimate_delay(e32[i, c + shift], e32[i + 1, c], int(centres[k]), W, L, FS, FC)
+        assert abs(co[m] - rc) < 1e-4 / FS
+        assert abs(((fi[m] - rf) * FC + 0.5) % 1.0 - 0.5) < 1e-4
+        assert abs(rh[m] - rr) < 1e-5
+        checked += 1
+    assert checked > 0.9 * M
+    if L >= 3:
+        assert np.median(co) == pytest.approx(3 / FS, abs=0.5 / FS)    # the planted three-sample delay
+    geom.close()
+
+
 def test_end_to_end_recovers_sway_and_heave():
     """Simulated speckle echoes -> GPU delays -> coarse solve -> unwrapped fine
     delays -> fine solve: the sway and heave velocities come back to a few
