@@ -54,7 +54,7 @@ __device__ __forceinline__ float2 echo_at<__nv_bfloat162>(const __nv_bfloat162* 
 // 2L terms kept; the energy under the peak lag is that total less the head
 // before and the tail after the shifted window.
 constexpr int DPC_TW = 2;         // warps per block
-constexpr int DPC_CH = 32;        // samples per window and chunk
+constexpr int DPC_CH = 16;        // samples per window and chunk
 constexpr int DPC_MAXL = 15;
 
 template <int L>
@@ -62,11 +62,10 @@ struct DpcShape {
     static constexpr int NL = 2 * L + 1;
     static constexpr int S2 = DPC_CH + 1;            // odd row strides
     static constexpr int S1 = DPC_CH + 2 * L + 1;
-    static constexpr int NH = L > 0 ? 2 * L : 1;     // head energies kept per window
+    static constexpr int NH = L > 0 ? 2 * L : 1;     // head energies kept per window (registers)
     static constexpr int U = L <= 8 ? 8 : 4;         // samples per register block
     static constexpr size_t PAR = 32 * 32;           // window table: 32 B a window
-    static constexpr size_t WARP_BYTES =
-        PAR + sizeof(float4) * 32 * S1 + sizeof(float2) * 32 * S2 + sizeof(float) * 32 * NH;
+    static constexpr size_t WARP_BYTES = PAR + sizeof(float4) * 32 * S1 + sizeof(float2) * 32 * S2;
     static constexpr size_t SMEM = DPC_TW * WARP_BYTES;
 };
 
@@ -96,7 +95,6 @@ __global__ void __launch_bounds__(32 * DPC_TW)
     DpcWin* win = reinterpret_cast<DpcWin*>(base);                            // [32]
     float4* s1 = reinterpret_cast<float4*>(base + S::PAR);                    // [32][S1] (ax, ax, ay, ay)
     float2* s2 = reinterpret_cast<float2*>(s1 + 32 * S::S1);                  // [32][S2]
-    float* eh = reinterpret_cast<float*>(s2 + 32 * S::S2);                    // [32][NH]
     const long long m0 = ((long long)blockIdx.x * DPC_TW + warp) * 32;
     if (m0 >= M) return;   // whole warps
     const long long m = m0 + lane;
@@ -126,14 +124,18 @@ __global__ void __launch_bounds__(32 * DPC_TW)
     for (int t = 0; t < NL; ++t) acc[t] = make_float2(0.f, 0.f);
     float2 p2v = make_float2(0.f, 0.f);   // sum |e2|^2 (two partial sums)
     float etot = 0.f;                     // sum |e1|^2 over [n0 - L, n0 + W + L)
+    float eh[S::NH];                      // its first 2L terms
+#pragma unroll
+    for (int q = 0; q < S::NH; ++q) eh[q] = 0.f;
     const float4* a1 = s1 + lane * S::S1;
     const float2* b2s = s2 + lane * S::S2;
     int len = 0;
     for (int off = 0; off < W; off += DPC_CH) {
         len = min(DPC_CH, W - off);
         __syncwarp();
-        // eight windows at a time: all their loads issued before the stores
-        constexpr int SW = 8, J1 = (DPC_CH + 2 * L + 31) / 32;   // e1 loads a lane makes per window
+        // SW windows at a time: all their loads issued before the stores
+        constexpr int J1 = (DPC_CH + 2 * L + 31) / 32;           // e1 loads a lane makes per window
+        constexpr int SW = J1 == 1 ? 16 : 8;
         for (int w0 = 0; w0 < 32; w0 += SW) {
             float2 v2[SW], v1[SW][J1];
 #pragma unroll
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(32 * DPC_TW)
             }
 #pragma unroll
             for (int u = 0; u < SW; ++u) {
-                s2[(w0 + u) * S::S2 + lane] = v2[u];
+                if (lane < DPC_CH) s2[(w0 + u) * S::S2 + lane] = v2[u];
 #pragma unroll
                 for (int h = 0; h < J1; ++h) {
                     const int j = lane + 32 * h;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(32 * DPC_TW)
             for (int q = 0; q < 2 * L; ++q) {
                 const float4 v = a1[q];
                 const float e = fmaf(v.x, v.x, v.z * v.z);
-                eh[lane * S::NH + q] = e;
+                eh[q] = e;
                 etot += e;
             }
         }
@@ -239,7 +241,9 @@ __global__ void __launch_bounds__(32 * DPC_TW)
         // e1 energy under the peak lag tau = bl - L: the window [n0 - tau, n0 - tau + W)
         // is the extended range less its first 2L - bl and its last bl terms
         float head = 0.f, tail = 0.f;
-        for (int q = 0; q < 2 * L - bl; ++q) head += eh[lane * S::NH + q];
+#pragma unroll
+        for (int q = 0; q < 2 * L; ++q)
+            if (q < 2 * L - bl) head += eh[q];
         for (int q = 0; q < bl; ++q) {
             const float4 v = a1[len + 2 * L - 1 - q];
             tail = fmaf(v.x, v.x, fmaf(v.z, v.z, tail));
