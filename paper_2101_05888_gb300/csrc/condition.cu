@@ -350,80 +350,134 @@ bool whiten_reg_dispatch(int n, bool apply, const float2* in, float2* out, long 
 }
 
 // ----------------------------------------------------------------------------
-// exact selection of order statistics of non-negative FP32 values (their bit
-// patterns order like the values): ranks klo <= khi, returns both values
+// TVG: both middle order statistics of the FP32 power of every column of
+// e [rows][n], by a three-level radix select on the bit patterns (as for DRC
+// below): level 1 on the top 12 bits (1/8-octave bins), levels 2 and 3 on the
+// next 10 bits of the values matching each rank's chosen prefix: three reads
+// of the echo.  One CTA per strip of TVG_COLS columns, its histograms (2048
+// bins a column at level 1, 2 x 1024 at levels 2 and 3) in shared memory;
+// thread t reads column t mod TVG_COLS of rows t / TVG_COLS + k TVG_RPI, eight
+// rows in flight.
+constexpr int TVG_COLS = 8;
+constexpr int TVG_THREADS = 256;
+constexpr int TVG_RPI = TVG_THREADS / TVG_COLS;   // rows an iteration reads
+constexpr size_t TVG_SMEM = sizeof(unsigned) * TVG_COLS * 2048;
 
-// TVG: one CTA per strip of 32 columns of e [rows][n]; value = FP32 power.
-constexpr int SEL_COLS = 32;
-constexpr int SEL_THREADS = 256;
+__device__ __forceinline__ unsigned tvg_bits(float2 v) {
+    return min(__float_as_uint(power_f32(v)), 0x7fffffffu);   // a NaN with the sign bit: the largest NaN
+}
 
-__global__ void __launch_bounds__(SEL_THREADS) tvg_median_kernel(const float2* __restrict__ e, long long rows, int n,
-                                                                 double* __restrict__ med) {
-    __shared__ unsigned hist[256][SEL_COLS];
-    __shared__ unsigned prefix[SEL_COLS], rank_s[SEL_COLS];
-    __shared__ unsigned cnt_le[SEL_COLS], min_gt[SEL_COLS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SEL_THREADS / 32;
-    const int col = blockIdx.x * SEL_COLS + lane;
-    const bool colok = col < n;
-    const unsigned klo = (unsigned)((rows - 1) / 2), khi = (unsigned)(rows / 2);
-    if (threadIdx.x < SEL_COLS) {
-        prefix[threadIdx.x] = 0u;
-        rank_s[threadIdx.x] = klo;
+// One level over the strip: every value of column c whose bits >> PSH equal
+// that rank's prefix >> PSH adds to bin (bits >> BSH) & (NB - 1) of h[r][c].
+template <int LEVEL>
+__device__ __forceinline__ void tvg_level(const float2* __restrict__ e, long long rows, int n, int col, bool colok,
+                                          unsigned* h, const unsigned* prefix) {
+    constexpr int NB = LEVEL == 1 ? 2048 : 1024, BSH = LEVEL == 1 ? 20 : (LEVEL == 2 ? 10 : 0);
+    constexpr int PSH = LEVEL == 2 ? 20 : 10;
+    const int c = threadIdx.x % TVG_COLS;
+    unsigned p0 = 0u, p1 = 0u;
+    if (LEVEL > 1) {
+        p0 = prefix[2 * c] >> PSH;
+        p1 = prefix[2 * c + 1] >> PSH;
     }
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        for (int t = threadIdx.x; t < 256 * SEL_COLS; t += SEL_THREADS) (&hist[0][0])[t] = 0u;
-        __syncthreads();
-        const unsigned pre = prefix[lane];
-        const unsigned himask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
-        if (colok) {
-            for (long long r = warp; r < rows; r += nw) {
-                const unsigned bits = __float_as_uint(power_f32(e[r * n + col]));
-                if ((bits & himask) == pre) atomicAdd(&hist[(bits >> shift) & 255u][lane], 1u);
-            }
+    unsigned* h0 = h + (LEVEL == 1 ? c * NB : (2 * c) * NB);
+    unsigned* h1 = h0 + NB;
+    auto add = [&](unsigned bits) {
+        const unsigned k = (bits >> BSH) & (NB - 1);
+        if (LEVEL == 1) {
+            atomicAdd(&h0[k], 1u);
+        } else {
+            if ((bits >> PSH) == p0) atomicAdd(&h0[k], 1u);
+            if ((bits >> PSH) == p1) atomicAdd(&h1[k], 1u);
         }
-        __syncthreads();
-        if (threadIdx.x < SEL_COLS) {
-            const int c = threadIdx.x;
-            unsigned rk = rank_s[c], acc = 0u;
-            int bsel = 255;
-            for (int bb = 0; bb < 256; ++bb) {
-                const unsigned h = hist[bb][c];
-                if (acc + h > rk) {
-                    bsel = bb;
+    };
+    if (!colok) return;
+    const long long r0 = threadIdx.x / TVG_COLS;
+    long long r = r0;
+    for (; r + 7 * TVG_RPI < rows; r += 8 * TVG_RPI) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = e[(r + u * TVG_RPI) * n + col];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) add(tvg_bits(v[u]));
+    }
+    for (; r < rows; r += TVG_RPI) add(tvg_bits(e[r * n + col]));
+}
+
+// The bins of every (column, rank) holding the rank's residual: one warp per
+// (column, rank) pair, the lanes summing 32-bin slices and scanning.
+template <int LEVEL>
+__device__ __forceinline__ void tvg_pick(const unsigned* h, unsigned* prefix, unsigned* rank) {
+    constexpr int NB = LEVEL == 1 ? 2048 : 1024, PER = NB / 32, SH = LEVEL == 1 ? 20 : (LEVEL == 2 ? 10 : 0);
+    const int lane = threadIdx.x & 31;
+    for (int pr = threadIdx.x >> 5; pr < 2 * TVG_COLS; pr += TVG_THREADS / 32) {
+        const int c = pr >> 1;
+        const unsigned* hh = h + (LEVEL == 1 ? c * NB : pr * NB);   // level 1: one histogram a column
+        const unsigned rk = rank[pr];
+        unsigned tot = 0u;
+        for (int k = 0; k < PER; ++k) tot += hh[lane * PER + k];
+        unsigned x = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        unsigned below = x - tot;
+        const bool mine = rk >= below && rk - below < tot;
+        unsigned bin = 0u, before = 0u;
+        if (mine) {
+            for (int k = 0; k < PER; ++k) {
+                const unsigned hk = hh[lane * PER + k];
+                if (rk - below < hk) {
+                    bin = lane * PER + k;
+                    before = below;
                     break;
                 }
-                acc += h;
+                below += hk;
             }
-            rank_s[c] = rk - acc;
-            prefix[c] |= (unsigned)bsel << shift;
         }
-        __syncthreads();
-    }
-    // the second middle value: equal to the first if enough values tie with
-    // it, otherwise the smallest value above it
-    if (threadIdx.x < SEL_COLS) {
-        cnt_le[threadIdx.x] = 0u;
-        min_gt[threadIdx.x] = 0xffffffffu;
-    }
-    __syncthreads();
-    const unsigned vlo = prefix[lane];
-    if (colok) {
-        unsigned le = 0u, mg = 0xffffffffu;
-        for (long long r = warp; r < rows; r += nw) {
-            const unsigned bits = __float_as_uint(power_f32(e[r * n + col]));
-            if (bits <= vlo) ++le;
-            else mg = min(mg, bits);
+        const unsigned who = __ballot_sync(0xffffffffu, mine);
+        const int src = who ? __ffs(who) - 1 : 0;
+        bin = __shfl_sync(0xffffffffu, bin, src);
+        before = __shfl_sync(0xffffffffu, before, src);
+        if (lane == 0) {
+            rank[pr] = rk - before;
+            prefix[pr] |= bin << SH;
         }
-        atomicAdd(&cnt_le[lane], le);
-        atomicMin(&min_gt[lane], mg);
     }
+}
+
+__global__ void __launch_bounds__(TVG_THREADS, 2) tvg_median_kernel(const float2* __restrict__ e, long long rows, int n,
+                                                                 double* __restrict__ med) {
+    extern __shared__ unsigned tvg_h[];                       // TVG_COLS x 2048 counters
+    __shared__ unsigned prefix[2 * TVG_COLS], rank[2 * TVG_COLS];   // index 2 c + r
+    const int col = blockIdx.x * TVG_COLS + (int)(threadIdx.x % TVG_COLS);
+    const bool colok = col < n;
+    if (threadIdx.x < 2 * TVG_COLS) {
+        prefix[threadIdx.x] = 0u;
+        rank[threadIdx.x] = (threadIdx.x & 1) ? (unsigned)(rows / 2) : (unsigned)((rows - 1) / 2);
+    }
+    for (int t = threadIdx.x; t < TVG_COLS * 2048; t += TVG_THREADS) tvg_h[t] = 0u;
     __syncthreads();
-    if (threadIdx.x < SEL_COLS && blockIdx.x * SEL_COLS + (int)threadIdx.x < n) {
+    tvg_level<1>(e, rows, n, col, colok, tvg_h, prefix);
+    __syncthreads();
+    tvg_pick<1>(tvg_h, prefix, rank);
+    __syncthreads();
+    for (int t = threadIdx.x; t < TVG_COLS * 2048; t += TVG_THREADS) tvg_h[t] = 0u;
+    __syncthreads();
+    tvg_level<2>(e, rows, n, col, colok, tvg_h, prefix);
+    __syncthreads();
+    tvg_pick<2>(tvg_h, prefix, rank);
+    __syncthreads();
+    for (int t = threadIdx.x; t < TVG_COLS * 2048; t += TVG_THREADS) tvg_h[t] = 0u;
+    __syncthreads();
+    tvg_level<3>(e, rows, n, col, colok, tvg_h, prefix);
+    __syncthreads();
+    tvg_pick<3>(tvg_h, prefix, rank);
+    __syncthreads();
+    if (threadIdx.x < TVG_COLS && blockIdx.x * TVG_COLS + (int)threadIdx.x < n) {
         const int c = threadIdx.x;
-        const unsigned lo = prefix[c];
-        const unsigned hi = (cnt_le[c] > khi) ? lo : min_gt[c];
-        med[blockIdx.x * SEL_COLS + c] = 0.5 * ((double)__uint_as_float(lo) + (double)__uint_as_float(hi));
+        const float lo = __uint_as_float(prefix[2 * c]), hi = __uint_as_float(prefix[2 * c + 1]);
+        med[blockIdx.x * TVG_COLS + c] = 0.5 * ((double)lo + (double)hi);
     }
 }
 
@@ -444,13 +498,25 @@ __global__ void tvg_gain_kernel(const double* __restrict__ med, int n, double al
     }
 }
 
-__global__ void scale_columns_kernel(const float2* __restrict__ in, float2* __restrict__ out, long long total, int n,
+// out[r][c] = in[r][c] gain[c]: thread = column (its gain in a register),
+// rows blockIdx.y, blockIdx.y + gridDim.y, ..., four in flight
+__global__ void scale_columns_kernel(const float2* __restrict__ in, float2* __restrict__ out, long long rows, int n,
                                      const float* __restrict__ gain) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float g = gain[i % n];
-        const float2 v = in[i];
-        out[i] = make_float2(v.x * g, v.y * g);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const float g = gain[c];
+    const long long step = gridDim.y;
+    long long r = blockIdx.y;
+    for (; r + 3 * step < rows; r += 4 * step) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = in[(r + u * step) * n + c];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) out[(r + u * step) * n + c] = make_float2(v[u].x * g, v[u].y * g);
+    }
+    for (; r < rows; r += step) {
+        const float2 v = in[r * n + c];
+        out[r * n + c] = make_float2(v.x * g, v.y * g);
     }
 }
 
@@ -797,11 +863,16 @@ extern "C" int sas_tvg(const void* d_in, void* d_out, int64_t rows, int32_t n, d
         if (!med) med = own;
         if (!gain) gain = reinterpret_cast<float*>(own + n);
     }
-    tvg_median_kernel<<<(n + SEL_COLS - 1) / SEL_COLS, SEL_THREADS, 0, st>>>((const float2*)d_in, rows, n, med);
+    cudaError_t e0 = cudaFuncSetAttribute(tvg_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TVG_SMEM);
+    if (e0 != cudaSuccess) {
+        if (own) cudaFreeAsync(own, st);
+        return cuda_fail(e0, "tvg");
+    }
+    tvg_median_kernel<<<(n + TVG_COLS - 1) / TVG_COLS, TVG_THREADS, TVG_SMEM, st>>>((const float2*)d_in, rows, n, med);
     tvg_gain_kernel<<<1, 1024, 0, st>>>(med, n, alpha, gain);
-    const long long total = rows * (long long)n;
-    scale_columns_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 16LL * sm_count()), 256, 0, st>>>(
-        (const float2*)d_in, (float2*)d_out, total, n, gain);
+    const unsigned gx = (unsigned)((n + 255) / 256);
+    const unsigned gy = (unsigned)std::max<long long>(1, std::min<long long>(rows, (16LL * sm_count() + gx - 1) / gx));
+    scale_columns_kernel<<<dim3(gx, gy), 256, 0, st>>>((const float2*)d_in, (float2*)d_out, rows, n, gain);
     cudaError_t e = cudaGetLastError();
     if (own) cudaFreeAsync(own, st);
     if (e != cudaSuccess) return cuda_fail(e, "tvg");

@@ -92,7 +92,8 @@ def test_whitening_output_not_16_byte_aligned():
     assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5
 
 
-@pytest.mark.parametrize("rows,n,alpha", [(41, 300, 0.0), (64, 333, 0.25), (1, 40, 0.1), (2, 65, 0.0)])
+@pytest.mark.parametrize("rows,n,alpha", [(41, 300, 0.0), (64, 333, 0.25), (1, 40, 0.1), (2, 65, 0.0),
+                                            (700, 50, 0.2), (300, 17, 0.0)])
 def test_tvg_matches_oracle(rows, n, alpha):
     rng = np.random.default_rng(rows * n)
     env = np.exp(-np.linspace(0, 4, n))
