@@ -2,18 +2,21 @@
 // compression:
 //  * sas_matched_filter: correlation of raw echo rows with the transmitted
 //    replica, y[k] = sum_l e[k + l] conj(p[l]) / sum_l |p[l]|^2, by
-//    overlap-save with FP32 FFTs in shared memory (one CTA per block of
-//    outputs of a row);
-//  * sas_whiten (Eq. 9): P(f) = mean over rows of |FFT(e)|^2 (FP64 per-CTA
-//    partial sums, reduced in a fixed order), G(f) = 1 / (gamma mean P + P(f)),
-//    scaled so that max G = 1, applied as a power gain (rows times sqrt G);
+//    overlap-save with FP32 register-resident FFTs (fftreg.cuh; a group of
+//    threads per block of outputs of a row);
+//  * sas_whiten (Eq. 9): P(f) = mean over rows of |FFT(e)|^2 (FP32 sums over
+//    runs of rows added in FP64 per chunk of rows, the chunks reduced in a
+//    fixed order), G(f) = 1 / (gamma mean P + P(f)), scaled so that max G = 1,
+//    applied as a power gain (rows times sqrt G);
 //  * sas_tvg (Eq. 10): P(t) = median over rows of the FP32 power |e(t)|^2,
-//    exact selection by a 4-pass radix select on the FP32 bit patterns per
-//    32-column strip (one CTA per strip), G(t) = 1 / (alpha mean P + P(t)),
-//    applied as a power gain;
+//    exact selection of both middle values by a three-level radix select on
+//    the FP32 bit patterns per 8-column strip (one CTA per strip),
+//    G(t) = 1 / (alpha mean P + P(t)), applied as a power gain;
 //  * sas_drc (Eqs. 11-12): I_n = |I| / max |I| (FP32), the median of I_n by
-//    the same radix select over the whole image, q from Eq. 12, the rational
-//    map of Eq. 11.
+//    the same three-level select over the whole image, q from Eq. 12, the
+//    rational map of Eq. 11.
+// The radix-4 shared-memory FFT of fft.cuh serves the replica spectrum and
+// whitening rows shorter than 256 points.
 // Medians of an even count are the FP64 mean of the two middle values.
 #include "fft.cuh"
 #include "fftreg.cuh"

@@ -1,6 +1,6 @@
 // Displaced-phase-centre (DPC) micronavigation (Sec. II-D, Eqs. 3-8):
 //  * time-delay estimation between the overlapping receivers of consecutive
-//    pings (one warp per measurement window, one lane per lag);
+//    pings (one thread per measurement window, all lags in its registers);
 //  * Eq. 4 residuals and their derivatives in FP64, Eqs. 6-7 regularisers;
 //  * Levenberg-Marquardt on Eq. 8 with Gauss-Newton normal equations.  In the
 //    velocity variables of the paper the normal matrix is dense (a ping's
