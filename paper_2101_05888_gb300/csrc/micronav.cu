@@ -26,46 +26,35 @@ constexpr int BROW = BANDW + 1;   // stored diagonals per row
 // ---------------------------------------------------------------------------
 // Time-delay estimation
 
-template <typename ET>
-__device__ __forceinline__ float2 echo_at(const ET* row, int n, float sc);
-template <>
-__device__ __forceinline__ float2 echo_at<__half2>(const __half2* row, int n, float sc) {
-    const float2 v = __half22float2(row[n]);
-    return make_float2(v.x * sc, v.y * sc);
-}
-template <>
-__device__ __forceinline__ float2 echo_at<__nv_bfloat162>(const __nv_bfloat162* row, int n, float sc) {
-    const float2 v = __bfloat1622float2(row[n]);
-    return make_float2(v.x * sc, v.y * sc);
-}
-
 // One thread per measurement m = ((i (C - shift) + c) K + k), 32 consecutive
 // m to a warp: e1 = ping i, receiver c + shift; e2 = ping i + 1, receiver c;
 // R(tau) = sum_n e2[n] conj(e1[n - tau]) over the window, tau = -L .. L, all
-// 2L + 1 lags accumulated in the thread's registers: with e2 = (bx, by),
-// R += (bx, by) (ax, ax) + (by, -bx) (ay, ay), two packed FP32x2 FMAs.  The
-// window is walked in chunks of DPC_CH samples: per chunk the warp stages,
-// for each of its 32 windows in turn, e2[nb .. nb + CH) and e1[nb - L .. nb +
-// CH + L) in shared memory (coalesced row runs, zero outside the rows and, for
-// e2, past the window); e1 is stored as (ax, ax, ay, ay) so that one 16-byte
-// load gives both operand pairs.  Rows have odd strides, so the 32 threads,
-// each reading its own window, hit distinct banks.  Energies: sum |e2|^2 over
-// the window, and for e1 the total over [n0 - L, n0 + W + L) with its first
-// 2L terms kept; the energy under the peak lag is that total less the head
+// 2L + 1 lags accumulated in the thread's registers as conj(R): with
+// e2 = (bx, by) and e1 = (ax, ay), conj(R) += (bx, bx) (ax, ay) + (by, by)
+// (ay, -ax), two packed FP32x2 FMAs, the e2 pairs formed once per sample for
+// all lags.  The window is walked in chunks of DPC_CH samples, staged by
+// asynchronous copies into two buffers: while a chunk is correlated, the
+// warp's copies of the next one (for each of its 32 windows, e2[nb .. nb +
+// CH) and e1[nb - L .. nb + CH + L), zero outside the rows and, for e2, past
+// the window) are in flight.  Rows have odd strides, so the 32 threads, each
+// reading its own window, hit distinct banks.  Energies: sum |e2|^2 over the
+// window, and for e1 the total over [n0 - L, n0 + W + L) with its first 2L
+// terms kept; the energy under the peak lag is that total less the head
 // before and the tail after the shifted window.
 constexpr int DPC_TW = 2;         // warps per block
 constexpr int DPC_CH = 16;        // samples per window and chunk
 constexpr int DPC_MAXL = 15;
 
-template <int L>
+template <typename ET, int L>
 struct DpcShape {
     static constexpr int NL = 2 * L + 1;
-    static constexpr int S2 = DPC_CH + 1;            // odd row strides
+    static constexpr int S2 = DPC_CH + 1;            // odd row strides (elements)
     static constexpr int S1 = DPC_CH + 2 * L + 1;
     static constexpr int NH = L > 0 ? 2 * L : 1;     // head energies kept per window (registers)
     static constexpr int U = L <= 8 ? 8 : 4;         // samples per register block
     static constexpr size_t PAR = 32 * 32;           // window table: 32 B a window
-    static constexpr size_t WARP_BYTES = PAR + sizeof(float4) * 32 * S1 + sizeof(float2) * 32 * S2;
+    static constexpr size_t BUF = (sizeof(ET) * 32 * (S1 + S2) + 15) / 16 * 16;   // one chunk of the 32 windows
+    static constexpr size_t WARP_BYTES = PAR + 2 * BUF;
     static constexpr size_t SMEM = DPC_TW * WARP_BYTES;
 };
 
@@ -75,30 +64,53 @@ struct DpcWin {
     float sc1, sc2;
 };
 
-__device__ __forceinline__ float2 dpc_load(const void* echo, int dtype, long long idx, float sc) {
-    if (dtype == SAS_ECHO_C64) return static_cast<const float2*>(echo)[idx];
-    if (dtype == SAS_ECHO_C32_F16) return echo_at<__half2>(static_cast<const __half2*>(echo) + idx, 0, sc);
-    return echo_at<__nv_bfloat162>(static_cast<const __nv_bfloat162*>(echo) + idx, 0, sc);
+template <typename ET>
+__device__ __forceinline__ float2 dpc_value(ET v, float sc);
+template <>
+__device__ __forceinline__ float2 dpc_value<float2>(float2 v, float) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float2 dpc_value<__half2>(__half2 v, float sc) {
+    const float2 f = __half22float2(v);
+    return make_float2(f.x * sc, f.y * sc);
+}
+template <>
+__device__ __forceinline__ float2 dpc_value<__nv_bfloat162>(__nv_bfloat162 v, float sc) {
+    const float2 f = __bfloat1622float2(v);
+    return make_float2(f.x * sc, f.y * sc);
 }
 
-template <int L>
+// asynchronous copy of one element into shared memory; zero-filled (nothing
+// read) when !valid
+template <typename ET>
+__device__ __forceinline__ void dpc_copy(ET* dst, const ET* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? (int)sizeof(ET) : 0;
+    if constexpr (sizeof(ET) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+template <typename ET, int L>
 __global__ void __launch_bounds__(32 * DPC_TW)
-    dpc_delay_kernel(const void* __restrict__ echo, int dtype, const float* __restrict__ scale, int C, int Ns,
-                     int shift, const int* __restrict__ centres, int K, int W, long long M, float inv_fs,
-                     float inv_wfc, double* __restrict__ coarse, double* __restrict__ fine,
-                     double* __restrict__ rho) {
-    using S = DpcShape<L>;
+    dpc_delay_kernel(const ET* __restrict__ echo, const float* __restrict__ scale, int C, int Ns, int shift,
+                     const int* __restrict__ centres, int K, int W, long long M, float inv_fs, float inv_wfc,
+                     double* __restrict__ coarse, double* __restrict__ fine, double* __restrict__ rho) {
+    using S = DpcShape<ET, L>;
     constexpr int NL = S::NL, U = S::U;
+    constexpr size_t BUFE = S::BUF / sizeof(ET);
     extern __shared__ __align__(16) unsigned char dpc_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* base = dpc_smem + warp * S::WARP_BYTES;
     DpcWin* win = reinterpret_cast<DpcWin*>(base);                            // [32]
-    float4* s1 = reinterpret_cast<float4*>(base + S::PAR);                    // [32][S1] (ax, ax, ay, ay)
-    float2* s2 = reinterpret_cast<float2*>(s1 + 32 * S::S1);                  // [32][S2]
+    ET* buf0 = reinterpret_cast<ET*>(base + S::PAR);                          // [2] x ([32][S1] e1, [32][S2] e2)
     const long long m0 = ((long long)blockIdx.x * DPC_TW + warp) * 32;
     if (m0 >= M) return;   // whole warps
     const long long m = m0 + lane;
     const bool live = m < M;
+    float sc1 = 1.f, sc2 = 1.f;
     {
         DpcWin wn = {0, 0, 0, 0, 1.f, 1.f};
         if (live) {
@@ -117,9 +129,36 @@ __global__ void __launch_bounds__(32 * DPC_TW)
                 wn.sc2 = scale[r2];
             }
         }
+        sc1 = wn.sc1;
+        sc2 = wn.sc2;
         win[lane] = wn;
     }
-    float2 acc[NL];
+    __syncwarp();
+    // copies of the chunk at `off` of the 32 windows into buffer b
+    auto stage = [&](int off, int b) {
+        ET* s1 = buf0 + b * BUFE;
+        ET* s2 = s1 + 32 * S::S1;
+        const int lw = min(DPC_CH, W - off);
+        for (int w = 0; w < 32; ++w) {
+            const DpcWin wn = win[w];
+            const int nb = wn.n0 + off;
+            if (lane < DPC_CH) {
+                const int n = nb + lane;
+                const bool ok = wn.live && lane < lw && n >= 0 && n < Ns;
+                dpc_copy(s2 + w * S::S2 + lane, echo + wn.e2 + (ok ? n : 0), ok);
+            }
+#pragma unroll
+            for (int h = 0; h < (DPC_CH + 2 * L + 31) / 32; ++h) {
+                const int j = lane + 32 * h, n1 = nb - L + j;
+                if (j < DPC_CH + 2 * L) {
+                    const bool ok = wn.live && n1 >= 0 && n1 < Ns;
+                    dpc_copy(s1 + w * S::S1 + j, echo + wn.e1 + (ok ? n1 : 0), ok);
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float2 acc[NL];   // conj(R(tau)), tau = t - L
 #pragma unroll
     for (int t = 0; t < NL; ++t) acc[t] = make_float2(0.f, 0.f);
     float2 p2v = make_float2(0.f, 0.f);   // sum |e2|^2 (two partial sums)
@@ -127,83 +166,64 @@ __global__ void __launch_bounds__(32 * DPC_TW)
     float eh[S::NH];                      // its first 2L terms
 #pragma unroll
     for (int q = 0; q < S::NH; ++q) eh[q] = 0.f;
-    const float4* a1 = s1 + lane * S::S1;
-    const float2* b2s = s2 + lane * S::S2;
+    const int nch = (W + DPC_CH - 1) / DPC_CH;
     int len = 0;
-    for (int off = 0; off < W; off += DPC_CH) {
+    const ET* a1 = buf0;
+    stage(0, 0);
+    for (int ci = 0; ci < nch; ++ci) {
+        const int off = ci * DPC_CH;
         len = min(DPC_CH, W - off);
-        __syncwarp();
-        // SW windows at a time: all their loads issued before the stores
-        constexpr int J1 = (DPC_CH + 2 * L + 31) / 32;           // e1 loads a lane makes per window
-        constexpr int SW = J1 == 1 ? 16 : 8;
-        for (int w0 = 0; w0 < 32; w0 += SW) {
-            float2 v2[SW], v1[SW][J1];
-#pragma unroll
-            for (int u = 0; u < SW; ++u) {
-                const DpcWin wn = win[w0 + u];
-                const int nb = wn.n0 + off;
-                const int n = nb + lane;
-                v2[u] = make_float2(0.f, 0.f);
-                if (wn.live && lane < len && n >= 0 && n < Ns) v2[u] = dpc_load(echo, dtype, wn.e2 + n, wn.sc2);
-#pragma unroll
-                for (int h = 0; h < J1; ++h) {
-                    const int j = lane + 32 * h, n1 = nb - L + j;
-                    v1[u][h] = make_float2(0.f, 0.f);
-                    if (wn.live && j < DPC_CH + 2 * L && n1 >= 0 && n1 < Ns)
-                        v1[u][h] = dpc_load(echo, dtype, wn.e1 + n1, wn.sc1);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < SW; ++u) {
-                if (lane < DPC_CH) s2[(w0 + u) * S::S2 + lane] = v2[u];
-#pragma unroll
-                for (int h = 0; h < J1; ++h) {
-                    const int j = lane + 32 * h;
-                    if (j < DPC_CH + 2 * L) s1[(w0 + u) * S::S1 + j] = make_float4(v1[u][h].x, v1[u][h].x, v1[u][h].y, v1[u][h].y);
-                }
-            }
+        if (ci + 1 < nch) {
+            stage(off + DPC_CH, (ci + 1) & 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncwarp();
+        a1 = buf0 + (ci & 1) * BUFE + lane * S::S1;
+        const ET* b2s = buf0 + (ci & 1) * BUFE + 32 * S::S1 + lane * S::S2;
         // e1 energy: the staged samples [nb + L, nb + L + len); in the first
         // chunk also [n0 - L, n0 + L), kept for the head sums
-        if (off == 0) {
+        if (ci == 0) {
 #pragma unroll
             for (int q = 0; q < 2 * L; ++q) {
-                const float4 v = a1[q];
-                const float e = fmaf(v.x, v.x, v.z * v.z);
+                const float2 v = dpc_value(a1[q], sc1);
+                const float e = fmaf(v.x, v.x, v.y * v.y);
                 eh[q] = e;
                 etot += e;
             }
         }
         for (int q = 0; q < len; ++q) {
-            const float4 v = a1[2 * L + q];
-            etot = fmaf(v.x, v.x, fmaf(v.z, v.z, etot));
+            const float2 v = dpc_value(a1[2 * L + q], sc1);
+            etot = fmaf(v.x, v.x, fmaf(v.y, v.y, etot));
         }
-        // R(tau) over the chunk (e2 is zero past the window)
+        // conj(R(tau)) over the chunk (e2 is zero past the window)
 #pragma unroll 1
         for (int j0 = 0; j0 < DPC_CH; j0 += U) {
-            float2 bv[U], bs[U];
+            float2 bx[U], by[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                bv[u] = b2s[j0 + u];
-                bs[u] = make_float2(bv[u].y, -bv[u].x);
-                p2v = ffma2(bv[u], bv[u], p2v);
+                const float2 b = dpc_value(b2s[j0 + u], sc2);
+                p2v = ffma2(b, b, p2v);
+                bx[u] = make_float2(b.x, b.x);
+                by[u] = make_float2(b.y, b.y);
             }
             // e1 staged at j0 + q serves sample j0 + u at lag t = u + 2L - q
 #pragma unroll
             for (int q = 0; q < U + 2 * L; ++q) {
-                const float4 a = a1[j0 + q];
-                const float2 ax = make_float2(a.x, a.y), ay = make_float2(a.z, a.w);
+                const float2 a = dpc_value(a1[j0 + q], sc1);
+                const float2 am = make_float2(a.y, -a.x);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int t = u + 2 * L - q;
                     if (t >= 0 && t < NL) {
-                        acc[t] = ffma2(bv[u], ax, acc[t]);
-                        acc[t] = ffma2(bs[u], ay, acc[t]);
+                        acc[t] = ffma2(bx[u], a, acc[t]);
+                        acc[t] = ffma2(by[u], am, acc[t]);
                     }
                 }
             }
         }
+        __syncwarp();   // the buffer is refilled two chunks later
     }
     if (!live) return;
     // largest |R|, the lowest lag on ties
@@ -224,6 +244,9 @@ __global__ void __launch_bounds__(32 * DPC_TW)
         if (t == bl - 1) Rm = acc[t];
         if (t == bl + 1) Rp = acc[t];
     }
+    R0.y = -R0.y;   // R: the conjugates of the accumulated sums
+    Rm.y = -Rm.y;
+    Rp.y = -Rp.y;
     const float best = sqrtf(best2);
     float d = 0.f, Rr = R0.x, Ri = R0.y;
     if (bl > 0 && bl < 2 * L) {
@@ -245,25 +268,42 @@ __global__ void __launch_bounds__(32 * DPC_TW)
         for (int q = 0; q < 2 * L; ++q)
             if (q < 2 * L - bl) head += eh[q];
         for (int q = 0; q < bl; ++q) {
-            const float4 v = a1[len + 2 * L - 1 - q];
-            tail = fmaf(v.x, v.x, fmaf(v.z, v.z, tail));
+            const float2 v = dpc_value(a1[len + 2 * L - 1 - q], sc1);
+            tail = fmaf(v.x, v.x, fmaf(v.y, v.y, tail));
         }
         const float q1 = etot - head - tail, den2 = (p2v.x + p2v.y) * q1;
         rho[m] = den2 > 0.f ? (double)(best * rsqrtf(den2)) : 0.0;
     }
 }
 
-template <int L>
-cudaError_t dpc_delay_launch(const void* echo, int dtype, const float* scale, int C, int Ns, int shift,
-                             const int* centres, int K, int W, long long M, float inv_fs, float inv_wfc,
-                             double* coarse, double* fine, double* rho, cudaStream_t st) {
-    using S = DpcShape<L>;
-    cudaError_t e = cudaFuncSetAttribute(dpc_delay_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+template <typename ET, int L>
+cudaError_t dpc_delay_launch(const ET* echo, const float* scale, int C, int Ns, int shift, const int* centres, int K,
+                             int W, long long M, float inv_fs, float inv_wfc, double* coarse, double* fine,
+                             double* rho, cudaStream_t st) {
+    using S = DpcShape<ET, L>;
+    cudaError_t e =
+        cudaFuncSetAttribute(dpc_delay_kernel<ET, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (e != cudaSuccess) return e;
     const long long warps = (M + 31) / 32;
-    dpc_delay_kernel<L><<<(unsigned)((warps + DPC_TW - 1) / DPC_TW), 32 * DPC_TW, S::SMEM, st>>>(
-        echo, dtype, scale, C, Ns, shift, centres, K, W, M, inv_fs, inv_wfc, coarse, fine, rho);
+    dpc_delay_kernel<ET, L><<<(unsigned)((warps + DPC_TW - 1) / DPC_TW), 32 * DPC_TW, S::SMEM, st>>>(
+        echo, scale, C, Ns, shift, centres, K, W, M, inv_fs, inv_wfc, coarse, fine, rho);
     return cudaGetLastError();
+}
+
+template <typename ET>
+cudaError_t dpc_delay_dispatch(int L, const ET* echo, const float* scale, int C, int Ns, int shift,
+                               const int* centres, int K, int W, long long M, float inv_fs, float inv_wfc,
+                               double* coarse, double* fine, double* rho, cudaStream_t st) {
+#define SAS_DPC_L(LL)                                                                                             \
+    case LL:                                                                                                      \
+        return dpc_delay_launch<ET, LL>(echo, scale, C, Ns, shift, centres, K, W, M, inv_fs, inv_wfc, coarse,   \
+                                        fine, rho, st);
+    switch (L) {
+        SAS_DPC_L(0) SAS_DPC_L(1) SAS_DPC_L(2) SAS_DPC_L(3) SAS_DPC_L(4) SAS_DPC_L(5) SAS_DPC_L(6) SAS_DPC_L(7)
+        SAS_DPC_L(8) SAS_DPC_L(9) SAS_DPC_L(10) SAS_DPC_L(11) SAS_DPC_L(12) SAS_DPC_L(13) SAS_DPC_L(14) SAS_DPC_L(15)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SAS_DPC_L
 }
 
 // ---------------------------------------------------------------------------
@@ -767,18 +807,22 @@ extern "C" int sas_dpc_delays(sas_geometry_t h, int32_t shift, const int32_t* d_
     const long long M = (long long)(h->P - 1) * (h->C - shift) * K;
     cudaStream_t st = (cudaStream_t)stream;
     const float inv_fs = (float)(1.0 / h->sig.fs), inv_wfc = (float)(1.0 / (2.0 * M_PI * h->sig.fc));
-    const float* sc = h->echo_dtype == SAS_ECHO_C64 ? nullptr : h->d_scale;
-    cudaError_t e = cudaSuccess;
-#define SAS_DPC_L(LL)                                                                                             \
-    case LL:                                                                                                      \
-        e = dpc_delay_launch<LL>(h->d_echo, h->echo_dtype, sc, h->C, h->Ns, shift, d_centres, K, W, M, inv_fs,    \
-                                 inv_wfc, d_coarse, d_fine, d_rho, st);                                           \
-        break;
-    switch (max_lag) {
-        SAS_DPC_L(0) SAS_DPC_L(1) SAS_DPC_L(2) SAS_DPC_L(3) SAS_DPC_L(4) SAS_DPC_L(5) SAS_DPC_L(6) SAS_DPC_L(7)
-        SAS_DPC_L(8) SAS_DPC_L(9) SAS_DPC_L(10) SAS_DPC_L(11) SAS_DPC_L(12) SAS_DPC_L(13) SAS_DPC_L(14) SAS_DPC_L(15)
+    cudaError_t e;
+    switch (h->echo_dtype) {
+        case SAS_ECHO_C64:
+            e = dpc_delay_dispatch<float2>(max_lag, (const float2*)h->d_echo, nullptr, h->C, h->Ns, shift, d_centres, K,
+                                           W, M, inv_fs, inv_wfc, d_coarse, d_fine, d_rho, st);
+            break;
+        case SAS_ECHO_C32_F16:
+            e = dpc_delay_dispatch<__half2>(max_lag, (const __half2*)h->d_echo, h->d_scale, h->C, h->Ns, shift,
+                                            d_centres, K, W, M, inv_fs, inv_wfc, d_coarse, d_fine, d_rho, st);
+            break;
+        default:
+            e = dpc_delay_dispatch<__nv_bfloat162>(max_lag, (const __nv_bfloat162*)h->d_echo, h->d_scale, h->C, h->Ns,
+                                                   shift, d_centres, K, W, M, inv_fs, inv_wfc, d_coarse, d_fine, d_rho,
+                                                   st);
+            break;
     }
-#undef SAS_DPC_L
     SAS_CUDA(e);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
