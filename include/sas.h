@@ -451,6 +451,13 @@ int sas_dpc_model_delays(const sas_dpc_problem* pr, const double* d_vy, const do
 int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_vz, int32_t max_iter, double* h_loss,
                   int32_t* h_iters, void* cuda_stream);
 
+/* Test hook: the banded solve inside sas_dpc_solve streams its rows through
+ * shared memory in chunks of 512 rows; rows (a power of two in [8, 512]) sets
+ * a smaller chunk for the following calls of this process, so that small
+ * problems cross chunk boundaries; rows = 0 restores 512.  The result does
+ * not depend on it.  Errors: SAS_ERR_ARG. */
+int sas_debug_dpc_solve_chunk(int32_t rows);
+
 #ifdef __cplusplus
 }
 #endif

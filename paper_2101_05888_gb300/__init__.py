@@ -47,7 +47,7 @@ ENTRY_POINTS = [
     "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_cull_stats",
     "sas_matched_filter", "sas_whiten", "sas_tvg", "sas_drc",
     "sas_debug_starve_copies",
-    "sas_dpc_delays", "sas_dpc_footprints", "sas_dpc_model_delays", "sas_dpc_solve",
+    "sas_dpc_delays", "sas_dpc_footprints", "sas_dpc_model_delays", "sas_dpc_solve", "sas_debug_dpc_solve_chunk",
 ]
 
 
@@ -135,6 +135,7 @@ def lib():
                 "sas_tvg": ([V, V, I64, ctypes.c_int32, D, V, V, V], I),
                 "sas_drc": ([V, I64, D, V, V, V], I),
                 "sas_debug_starve_copies": ([V, I, ctypes.c_int32], I),
+                "sas_debug_dpc_solve_chunk": ([ctypes.c_int32], I),
                 "sas_dpc_delays": ([V, ctypes.c_int32, V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, V, V, V,
                                     V], I),
                 "sas_dpc_footprints": ([P(sas_dpc_problem), V, V, V, V], I),
@@ -340,6 +341,10 @@ def sas_dpc_solve(pr: sas_dpc_problem, d_vy, d_vz, max_iter: int = 100, stream=N
 
 def sas_debug_starve_copies(h, skip: int, wait_limit_ms: int):
     _check(lib().sas_debug_starve_copies(h, skip, wait_limit_ms))
+
+
+def sas_debug_dpc_solve_chunk(rows: int):
+    _check(lib().sas_debug_dpc_solve_chunk(int(rows)))
 
 
 # ---------------------------------------------------------------------------

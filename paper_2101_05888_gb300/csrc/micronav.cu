@@ -646,15 +646,48 @@ __global__ void dpc_regular_kernel(Prob pb, const double* q, double* band, doubl
 // critical path per row is one reciprocal square root and a few FP64
 // operations (no sequential dot products).  The forward substitution
 // U^T y = -g rides along (its right-hand side updated the same way); the back
-// substitution runs on one lane.  acc[1] = 1 when the factorisation fails;
-// acc[2] = max |delta|.
+// substitution runs on one lane.  The rows of the band and of g (forward),
+// and of U and y (backward, in reverse), stream through shared memory in
+// chunks of 2^rlog rows (at most SOL_R) by asynchronous copies, the next chunk
+// in flight while the current one is used, so no global-memory latency sits
+// on the chain.  acc[1] = 1 when the factorisation fails; acc[2] = max |delta|.
+constexpr int SOL_R = 512;
+int g_sol_rlog = 9;   // chunk rows 2^9 = SOL_R; smaller through sas_debug_dpc_solve_chunk
+static_assert(BANDW == 7, "the back substitution keeps seven deltas in registers");
+constexpr size_t SOL_SMEM = sizeof(double) * 2 * SOL_R * (BROW + 1);
+
+__device__ __forceinline__ void sol_copy8(double* dst, const double* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+// rows [c R, min(n, c R + R)) of a [n][w] array into buf [R][w]
+__device__ __forceinline__ void sol_stage(double* buf, const double* src, int n, int w, int c, int R, int lane) {
+    const int r0 = c * R, r1 = min(n, r0 + R);
+    for (int i = lane; i < (r1 - r0) * w; i += 32) sol_copy8(buf + i, src + (size_t)r0 * w + i);
+}
+
 __global__ void __launch_bounds__(32) dpc_solve_kernel(int n, const double* band, const double* grad, double mu,
-                                                       double* work, const double* q, double* q_try, double* acc) {
+                                                       double* work, const double* q, double* q_try, double* acc,
+                                                       int rlog) {
+    extern __shared__ __align__(16) double sol_sm[];
+    double* bbuf = sol_sm;                          // [2][SOL_R][BROW]: band rows, then U rows
+    double* gbuf = sol_sm + 2 * SOL_R * BROW;       // [2][SOL_R]: g, then y
     __shared__ double Pm[BROW][BROW];   // Pm[r % BROW][d] = pending A(r, r + d), rows j .. j + BANDW
     __shared__ double tv[BROW];         // pending right-hand side of those rows
     const int lane = threadIdx.x;
     double* U = work;                   // [n][BROW], the diagonal stored inverted
     double* y = work + (size_t)n * BROW;
+    const int R = 1 << rlog;            // chunk rows, 8 .. SOL_R; buffers keep the SOL_R stride
+    const int nch = (n + R - 1) / R;
+    auto commit = [] { asm volatile("cp.async.commit_group;" ::: "memory"); };
+    auto wait1 = [] { asm volatile("cp.async.wait_group 1;" ::: "memory"); };
+    auto wait0 = [] { asm volatile("cp.async.wait_group 0;" ::: "memory"); };
+    auto stage_fwd = [&](int c) {
+        sol_stage(bbuf + (c & 1) * SOL_R * BROW, band, n, BROW, c, R, lane);
+        sol_stage(gbuf + (c & 1) * SOL_R, grad, n, 1, c, R, lane);
+        commit();
+    };
     // lane -> entry (j + ta, j + tb) of the trailing triangle, 1 <= ta <= tb <= BANDW
     int ta = 1, e = lane;
     while (ta <= BANDW && e >= BANDW - ta + 1) {
@@ -663,19 +696,29 @@ __global__ void __launch_bounds__(32) dpc_solve_kernel(int n, const double* band
     }
     const int tb = ta + e;
     const bool upd = lane < BANDW * (BANDW + 1) / 2;
-    // row r of the damped matrix and of -g (lanes 0 .. BANDW; zero past the end)
+    // row r of the damped matrix and of -g (lanes 0 .. BANDW; zero past the end),
+    // from its staged chunk
     auto fetch = [&](int r, double& a, double& t) {
         a = 0.0;
         t = 0.0;
         if (lane <= BANDW && r < n && r + lane < n) {
-            a = band[bidx(r, r + lane)];
+            const int c = r >> rlog, i = r & (R - 1);
+            a = bbuf[((c & 1) * SOL_R + i) * BROW + lane];
             if (lane == 0) {
                 a += mu * (a + 1e-12);   // Marquardt's scaling, Levenberg's floor
-                t = -grad[r];
+                t = -gbuf[(c & 1) * SOL_R + i];
             }
         }
     };
     if (lane == 0) acc[1] = 0.0;
+    stage_fwd(0);
+    if (nch > 1) {
+        stage_fwd(1);
+        wait1();
+    } else {
+        wait0();
+    }
+    __syncwarp();
     for (int r = 0; r < BROW; ++r) {
         double a, t;
         fetch(r, a, t);
@@ -684,12 +727,27 @@ __global__ void __launch_bounds__(32) dpc_solve_kernel(int n, const double* band
     }
     __syncwarp();
     for (int j = 0; j < n; ++j) {
+        const int rn = j + BROW;
+        if (rn < n && (rn & (R - 1)) == 0) {
+            // the fetches move to chunk rn / R: chunk rn / R - 1 is done with,
+            // its buffer takes chunk rn / R + 1
+            const int c = rn >> rlog;
+            __syncwarp();
+            if (c + 1 < nch) {
+                stage_fwd(c + 1);
+                wait1();
+            } else {
+                wait0();
+            }
+            __syncwarp();
+        }
         double an, tn;
-        fetch(j + BROW, an, tn);        // issued early: lands during the square root
+        fetch(rn, an, tn);
         const int sj = j % BROW;
         const double djj = Pm[sj][0];
         if (!(djj > 0.0)) {
             if (lane == 0) acc[1] = 1.0;
+            wait0();
             return;
         }
         const double inv = rsqrt(djj);
@@ -709,17 +767,68 @@ __global__ void __launch_bounds__(32) dpc_solve_kernel(int n, const double* band
         if (lane == 0) tv[sj] = tn;
         __syncwarp();
     }
-    if (lane != 0) return;
-    // U delta = y
+    wait0();
+    // U delta = y, rows n - 1 .. 0, U and y streamed back in reverse chunks
+    __threadfence_block();
+    __syncwarp();
+    auto stage_bwd = [&](int c) {
+        sol_stage(bbuf + (c & 1) * SOL_R * BROW, U, n, BROW, c, R, lane);
+        sol_stage(gbuf + (c & 1) * SOL_R, y, n, 1, c, R, lane);
+        commit();
+    };
+    stage_bwd(nch - 1);
+    if (nch > 1) {
+        stage_bwd(nch - 2);
+        wait1();
+    } else {
+        wait0();
+    }
+    __syncwarp();
+    // delta of rows j + 1 .. j + 7 in registers; the terms of rows j + 2 ..
+    // j + 7 are summed before delta_{j+1} is known, so one FMA and one
+    // multiplication per row are on the dependent chain
+    double d1 = 0.0, d2 = 0.0, d3 = 0.0, d4 = 0.0, d5 = 0.0, d6 = 0.0, d7 = 0.0;
     double dmax = 0.0;
     for (int j = n - 1; j >= 0; --j) {
-        double s = y[j];
-        for (int d = 1; d <= BANDW && j + d < n; ++d) s -= U[(size_t)j * BROW + d] * y[j + d];
-        y[j] = s * U[(size_t)j * BROW];
-        dmax = fmax(dmax, fabs(y[j]));
-        q_try[j] = q[j] + y[j];
+        const int c = j >> rlog, i = j & (R - 1);
+        if (i == R - 1 && c < nch - 1) {
+            // entering chunk c from above: chunk c + 1 is done with, its buffer
+            // takes chunk c - 1
+            __syncwarp();
+            if (c >= 1) {
+                stage_bwd(c - 1);
+                wait1();
+            } else {
+                wait0();
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            // entries past row n - 1 were never written: only j + d < n is read
+            const double* Ur = bbuf + ((c & 1) * SOL_R + i) * BROW;
+            double s = gbuf[(c & 1) * SOL_R + i];
+            if (j + 7 < n) s -= Ur[7] * d7;
+            if (j + 6 < n) s -= Ur[6] * d6;
+            if (j + 5 < n) s -= Ur[5] * d5;
+            if (j + 4 < n) s -= Ur[4] * d4;
+            if (j + 3 < n) s -= Ur[3] * d3;
+            if (j + 2 < n) s -= Ur[2] * d2;
+            if (j + 1 < n) s -= Ur[1] * d1;
+            const double dj = s * Ur[0];
+            d7 = d6;
+            d6 = d5;
+            d5 = d4;
+            d4 = d3;
+            d3 = d2;
+            d2 = d1;
+            d1 = dj;
+            y[j] = dj;
+            dmax = fmax(dmax, fabs(dj));
+            q_try[j] = q[j] + dj;
+        }
     }
-    acc[2] = dmax;
+    wait0();
+    if (lane == 0) acc[2] = dmax;
 }
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -916,6 +1025,11 @@ extern "C" int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_
         return SAS_OK;
     };
     rc = setup(pb, S, d_vy, d_vz, st);
+    if (rc == SAS_OK) {
+        const cudaError_t ea =
+            cudaFuncSetAttribute(dpc_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SOL_SMEM);
+        if (ea != cudaSuccess) fail(ea, "dpc solve attribute");
+    }
     if (rc == SAS_OK) rc = loss_at(S.q, cost);
     double mu = 1e-3;
     for (int it = 0; rc == SAS_OK && it < max_iter; ++it) {
@@ -936,7 +1050,7 @@ extern "C" int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_
         bool accepted = false, stalled = false;
         double trial = cost;
         for (int tries = 0; tries < 40 && rc == SAS_OK; ++tries) {
-            dpc_solve_kernel<<<1, 32, 0, st>>>(n, band, grad, mu, work, S.q, q_try, acc);
+            dpc_solve_kernel<<<1, 32, SOL_SMEM, st>>>(n, band, grad, mu, work, S.q, q_try, acc, g_sol_rlog);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpyAsync(hacc, acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -977,4 +1091,16 @@ extern "C" int sas_dpc_solve(const sas_dpc_problem* pr, double* d_vy, double* d_
         if (h_iters) *h_iters = iters;
     }
     return rc;
+}
+
+extern "C" int sas_debug_dpc_solve_chunk(int32_t rows) {
+    if (rows == 0) rows = SOL_R;
+    int lg = 3;
+    while ((1 << lg) < rows && lg < 9) ++lg;
+    if (rows < 8 || rows > SOL_R || (1 << lg) != rows) {
+        set_error("sas_debug_dpc_solve_chunk: rows must be 0 or a power of two in [8, 512]");
+        return SAS_ERR_ARG;
+    }
+    g_sol_rlog = lg;
+    return SAS_OK;
 }

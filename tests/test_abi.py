@@ -59,3 +59,7 @@ def test_argument_errors_without_gpu(libsas):
     assert libsas.sas_backproject_2d(None, None, None, None, 0, None) == sas.SAS_ERR_ARG
     assert libsas.sas_sharpness(None, 0, None, None, None) == sas.SAS_ERR_ARG
     assert libsas.sas_debug_starve_copies(None, 1, 10) == sas.SAS_ERR_ARG
+    for rows in (7, 24, 1024, -8):
+        assert libsas.sas_debug_dpc_solve_chunk(rows) == sas.SAS_ERR_ARG
+    assert libsas.sas_debug_dpc_solve_chunk(16) == sas.SAS_OK
+    assert libsas.sas_debug_dpc_solve_chunk(0) == sas.SAS_OK

@@ -68,8 +68,10 @@ def test_footprints_and_model_delays_match_oracle():
     assert np.abs(ref).max() > 1e-6
 
 
-@pytest.mark.parametrize("huber", [0.0, 2e-4])
-def test_solve_matches_oracle(huber):
+@pytest.mark.parametrize("huber,chunk", [(0.0, 0), (2e-4, 0), (0.0, 8), (2e-4, 16)])
+def test_solve_matches_oracle(huber, chunk):
+    """chunk: rows of the banded solve's shared-memory chunks (0: 512, one
+    chunk here; 8 and 16: the 32 unknowns cross 3 and 1 chunk boundaries)."""
     pl, vy, vz, meas = _scene(P=16, K=6, seed=9)
     P = pl.P
     ps = mn.footprints(pl, np.zeros(P), np.zeros(P), meas, C_SOUND)
@@ -84,7 +86,11 @@ def test_solve_matches_oracle(huber):
     ry, rz, rloss = mn.solve(pl, np.zeros(P), np.zeros(P), meas, ps, C_SOUND, z_dvl, lam1, lam2, huber=huber)
     prob = _Problem(pl, meas, z_dvl, lam1, lam2, huber=huber, ps=ps)
     gy, gz = torch.zeros(P, dtype=torch.float64, device="cuda"), torch.zeros(P, dtype=torch.float64, device="cuda")
-    loss, iters = sas.sas_dpc_solve(prob.pr, gy, gz, 200)
+    sas.sas_debug_dpc_solve_chunk(chunk)
+    try:
+        loss, iters = sas.sas_dpc_solve(prob.pr, gy, gz, 200)
+    finally:
+        sas.sas_debug_dpc_solve_chunk(0)
     gy, gz = gy.cpu().numpy(), gz.cpu().numpy()
     assert iters > 0
     # the same minimum: loss to 1e-9 relative; velocities to 1e-6 m/s (of ~3e-2)
