@@ -79,6 +79,20 @@ def workload_of(args):
     return w
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest of the ranks' values: the slowest rank's time is the whole
+    job's.  Every rank calls it; the one-element tensor lives where the process
+    group's backend works (the current GPU for NCCL, the host for gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    dist = torch.distributed
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -282,9 +296,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms = t_all0.elapsed_time(t_all1)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, world)
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     value = world * w.updates * args.steps / (total_ms / 1e3) / 1e9
@@ -404,11 +416,7 @@ def run_stage(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t_.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     gbs = STAGE_BYTES[args.stage] * n_el / (ms / 1e3) / 1e9
     peaks = measured_peaks()
     peak = float(peaks.get("hbm_gbs") or 6800.0)
@@ -465,11 +473,7 @@ def run_dpc(args, rank, world, local_rank):
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t_ = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t_, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t_.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     seg_bytes = 2 * W * 8
     gbs = M * seg_bytes / (ms / 1e3) / 1e9
     # one solve of Eq. 8: delays predicted from a sway / heave trajectory plus noise
