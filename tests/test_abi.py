@@ -63,3 +63,24 @@ def test_argument_errors_without_gpu(libsas):
         assert libsas.sas_debug_dpc_solve_chunk(rows) == sas.SAS_ERR_ARG
     assert libsas.sas_debug_dpc_solve_chunk(16) == sas.SAS_OK
     assert libsas.sas_debug_dpc_solve_chunk(0) == sas.SAS_OK
+
+
+def test_conditioning_and_dpc_argument_errors_without_gpu(libsas):
+    """The host-side checks of the conditioning and micronavigation calls
+    refuse bad sizes before any CUDA call (the placeholder pointers are never
+    used)."""
+    fake = ctypes.c_void_p(0x1000)
+    assert libsas.sas_matched_filter(fake, 4, 100, fake, 0, fake, None) == sas.SAS_ERR_ARG       # L < 1
+    assert libsas.sas_matched_filter(fake, 4, 100, fake, 4097, fake, None) == sas.SAS_ERR_ARG    # L > 4096
+    assert libsas.sas_matched_filter(fake, 0, 100, fake, 8, fake, None) == sas.SAS_OK            # no rows
+    assert libsas.sas_whiten(fake, fake, 4, 300, 0.1, None, None) == sas.SAS_ERR_ARG             # n not 2^k
+    assert libsas.sas_whiten(fake, fake, 4, 32768, 0.1, None, None) == sas.SAS_ERR_ARG           # n > 16384
+    assert libsas.sas_whiten(fake, fake, 4, 256, -1.0, None, None) == sas.SAS_ERR_ARG            # gamma < 0
+    assert libsas.sas_tvg(fake, fake, 0, 16, 0.1, None, None, None) == sas.SAS_ERR_ARG           # no rows
+    assert libsas.sas_tvg(fake, fake, 4, 16, -0.5, None, None, None) == sas.SAS_ERR_ARG          # alpha < 0
+    assert libsas.sas_drc(fake, 100, 1.0, fake, None, None) == sas.SAS_ERR_ARG                  # b = 1
+    assert libsas.sas_drc(fake, 0, 0.3, fake, None, None) == sas.SAS_ERR_ARG                    # no pixels
+    assert libsas.sas_dpc_delays(None, 2, fake, 10, 128, 8, None, None, None, None) == sas.SAS_ERR_ARG
+    assert libsas.sas_dpc_footprints(None, fake, fake, fake, None) == sas.SAS_ERR_ARG
+    pr = sas.sas_dpc_problem(P=1, C=8, shift=2, K=4, side=1, c=1500.0)                          # P < 2
+    assert libsas.sas_dpc_solve(ctypes.byref(pr), fake, fake, 10, None, None, None) == sas.SAS_ERR_ARG
