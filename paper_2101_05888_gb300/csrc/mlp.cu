@@ -134,13 +134,11 @@ __global__ void __launch_bounds__(TPB) mlp_block_kernel(const float* __restrict_
             continue;
         }
         float rx = -tgt[s0 + s].x, ry = -tgt[s0 + s].y;
-        float t[NT];
         for (int m = 0; m < NT; ++m) {
             float v = W[O_B3 + m];
             const float* w3 = W + O_W3 + m * H;
             const float* a = A2 + s * H;
             for (int i = 0; i < H; ++i) v = fmaf(w3[i], a[i], v);
-            t[m] = v;
             const float2 wv = win[(s0 + s) * NT + m];
             rx = fmaf(v, wv.x, rx);
             ry = fmaf(v, wv.y, ry);

@@ -34,7 +34,7 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     const int npos_pad = (npos + RUN - 1) / RUN * RUN;
     // expansion runs read up to RUN + 7 samples past a run start: pad the slot
     const int slot_bytes = ((seglen + RUN + 8) * elem + 127) / 128 * 128;
-    const size_t smem = smem_bytes(slot_bytes, npos_pad, refract ? NREC_REFR : NREC);
+    const size_t smem = smem_bytes(slot_bytes, npos_pad, refract ? (int)NREC_REFR : (int)NREC);
     if (smem > 227 * 1024) {
         set_error("shared memory need %zu exceeds the per-block limit", smem);
         return SAS_ERR_UNSUPPORTED;
