@@ -33,10 +33,10 @@ def _json_lines(text):
     return [json.loads(l) for l in text.splitlines() if l.startswith("{")]
 
 
-def test_max_over_ranks_two_gloo_ranks():
-    r = _torchrun([os.path.join("tests", "_gloo_max.py")])
+def test_max_over_ranks_two_gloo_ranks(tmp_path):
+    r = _torchrun([os.path.join("tests", "_gloo_max.py"), str(tmp_path)])
     assert r.returncode == 0, r.stderr[-2000:]
-    got = sorted(_json_lines(r.stdout), key=lambda d: d["rank"])
+    got = [json.load(open(tmp_path / ("rank%d.json" % k))) for k in range(2)]
     assert [d["rank"] for d in got] == [0, 1] and all(d["world"] == 2 for d in got)
     assert all(d["max"] == 3.5 for d in got)          # 1.5 on rank 0, 3.5 on rank 1
 
