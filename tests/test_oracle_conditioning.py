@@ -1,6 +1,7 @@
 """Pins for the conditioning oracle (Sec. II-E, Eqs. 9-12) and the matched
 filter, against closed forms that follow from the equations themselves."""
 import numpy as np
+import pytest
 
 import oracle
 from oracle import conditioning as cond
@@ -135,3 +136,32 @@ def test_tvg_silent_median_leaves_samples():
     assert Pmed[0] == 0 and Pmed[1] == 0 and G[0] == 1.0 and G[1] == 1.0
     assert np.array_equal(out[:, :2], e[:, :2].astype(np.complex128))
     assert np.allclose(np.abs(out[:, 2:]) ** 2, 1.0)
+
+
+def _colored(rows, n, seed):
+    rng = np.random.default_rng(seed)
+    w = rng.normal(size=(rows, n + 4)) + 1j * rng.normal(size=(rows, n + 4))
+    h = np.array([1.0, 0.7 - 0.2j, 0.3, -0.1j, 0.05])
+    return np.stack([np.convolve(r, h, mode="valid") for r in w]).astype(np.complex64)
+
+
+@pytest.mark.parametrize("rows,n,gamma", [(40, 256, 0.0), (64, 1024, 0.1), (9, 16384, 0.05), (7, 2048, 0.1),
+                                          (3, 4096, 0.0), (5, 8192, 0.2), (17, 512, 0.3)])
+def test_whitening_gain_tolerance_holds_for_an_independent_fp32_fft(rows, n, gamma):
+    """The GPU whitening tests bound the gain error by
+    max(1e-6, 2^-23 sqrt(log2 n kappa)), kappa = mean P / (gamma mean P + min P):
+    the rounding of FP32 spectra amplified by the conditioning of Eq. 9.  An
+    independent single-precision FFT (scipy.fft on complex64) meets that
+    bound on the same inputs, so the bound asks no more than FP32 arithmetic
+    can give."""
+    sfft = pytest.importorskip("scipy.fft")
+    e = _colored(rows, n, n + rows)
+    _, Gh = cond.whiten(e, gamma)
+    S = sfft.fft(e, axis=-1)
+    assert S.dtype == np.complex64
+    P = np.mean(np.abs(S.astype(np.complex128)) ** 2, axis=0)
+    G = 1.0 / (gamma * P.mean() + P)
+    gain = np.sqrt(G / G.max()).astype(np.float32)
+    kappa = np.mean(1.0 / Gh) / (1.0 + gamma)
+    tol = max(1e-6, 2.0 ** -23 * np.sqrt(np.log2(n) * kappa))
+    assert np.abs(gain - np.sqrt(Gh)).max() < tol
