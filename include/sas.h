@@ -310,7 +310,11 @@ int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, float* d_tabl
                             void* cuda_stream);
 
 /* Waits for the stream, then reports and clears the handle's device status:
- * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check. */
+ * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check.
+ * After a timeout the results of the calls since the last check are invalid,
+ * and a kernel may have left while one of its own bulk copies was still in
+ * flight: treat the device state as suspect and recreate the handle (and
+ * re-upload the echo) before relying on further results. */
 int sas_sync_status(sas_geometry_t h, void* cuda_stream);
 
 /* ---- Data conditioning (Sec. II-E) and range compression ----------------

@@ -4,6 +4,7 @@ link uses the static CUDA runtime, so the library has no dependency beyond the
 driver."""
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -15,15 +16,16 @@ OUT = os.path.join(HERE, "libsas.so")
 BUILD_DIR = os.path.join(os.path.dirname(HERE), "_build")
 SOURCES = ["sas_api.cu", "tdbp_forward.cu", "tdbp_vjp.cu", "tdbp_adjoint.cu", "sharpness.cu", "sharpness_static.cu", "mlp.cu",
            "simulate.cu", "condition.cu", "micronav.cu"]
-HEADERS = ["sas_common.cuh", "tdbp_core.cuh", "fft.cuh"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 
 def _inputs():
-    inc = os.path.join(os.path.dirname(HERE), "include", "sas.h")
-    return [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [inc, __file__]
+    # every header in csrc/ and include/: an edit to any of them rebuilds the library
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+                     glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
+    return [os.path.join(CSRC, s) for s in SOURCES] + headers + [__file__]
 
 
 def up_to_date() -> bool:

@@ -855,8 +855,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             n_cur = n_next;
             last_cur = last_next;
         }
-        // copies issued for a stage that was never expanded must land before exit
-        for (int kk = kw; kk < kf; ++kk) mbar_wait_bounded(smem_u32(&full[kk % NSEG]), (kk / NSEG) & 1, p.wait_ns);
+        // copies issued for a stage that was never expanded must land before
+        // exit; if one does not land in time, the CTA leaves with a bulk copy
+        // possibly still writing its shared memory: recorded as a timeout
+        for (int kk = kw; kk < kf; ++kk) {
+            if (!mbar_wait_bounded(smem_u32(&full[kk % NSEG]), (kk / NSEG) & 1, p.wait_ns) && lane == 0)
+                atomicOr(p.status, DEV_TIMEOUT);
+        }
         if (p.cull) {
             n_cand = __reduce_add_sync(0xffffffffu, n_cand);
             n_act = __reduce_add_sync(0xffffffffu, n_act);

@@ -99,6 +99,9 @@ def test_tabulation_matches_oracle_mlp():
     assert np.abs(table - ref).max() < 1e-5
 
 
+KAISER_SWEEP = (4.0, 5.0, 6.0, 6.5, 7.0, 8.0)
+
+
 def test_learned_interpolator_gain():
     """Train on simulator echoes (the library's own simulator, small-2D
     geometry, 10^6 windows) against the 32-tap truth; tabulate at 4096
@@ -126,16 +129,26 @@ def test_learned_interpolator_gain():
     echo = point_echo(w, nav, scat).astype(np.complex64)
     geom = sas.Geometry.from_nav(nav, lib_signal(w))
     grid = sas.grid_from(w.grid)
-    geom.upload_echo(echo, sas.SAS_ECHO_C32_BF16)
-    img_l = geom.backproject(grid, learned.interp_from_table(table)).cpu().numpy()
-    geom.upload_echo(echo, sas.SAS_ECHO_C64)
-    img_k = geom.backproject(grid, sas.kaiser(4.0)).cpu().numpy()
-    geom.sync_status()
     tx, rx = oracle_positions(nav)
-    truth = oracle.backproject(tx, rx, oracle_signal(w), echo, 32, TRUTH_BETA, grid_pixels(w.grid)).reshape(img_l.shape)
-    err_l = oracle.rel_l2(img_l, truth)
-    err_k = oracle.rel_l2(img_k, truth)
-    print("vs 32-tap truth: learned BF16 %.3g, Kaiser(4) FP32 %.3g, gain %.2fx" % (err_l, err_k, err_k / err_l))
-    assert err_l < 3e-3
-    assert err_l < err_k
+    truth = oracle.backproject(tx, rx, oracle_signal(w), echo, 32, TRUTH_BETA, grid_pixels(w.grid))
+    lt = learned.interp_from_table(table)
+    errs = {}
+    for store, name in ((sas.SAS_ECHO_C64, "FP32"), (sas.SAS_ECHO_C32_BF16, "BF16")):
+        geom.upload_echo(echo, store)
+        errs[("learned", name)] = oracle.rel_l2(geom.backproject(grid, lt).cpu().numpy(), truth)
+        # the plain 8-tap Kaiser-sinc over the window shapes around its best
+        # (flat-band optimum near beta 6.5 at this band edge)
+        for beta in KAISER_SWEEP:
+            errs[(beta, name)] = oracle.rel_l2(geom.backproject(grid, sas.kaiser(beta)).cpu().numpy(), truth)
+    geom.sync_status()
     geom.close()
+    for name in ("FP32", "BF16"):
+        best = min(KAISER_SWEEP, key=lambda b: errs[(b, name)])
+        print("vs 32-tap truth, %s echo: learned %.3g; Kaiser-sinc %s; best beta %g: %.3g; learned gain over "
+              "beta 4 %.2fx, over the best Kaiser %.2fx" % (
+                  name, errs[("learned", name)], " ".join("b%g %.3g" % (b, errs[(b, name)]) for b in KAISER_SWEEP),
+                  best, errs[(best, name)], errs[(4.0, name)] / errs[("learned", name)],
+                  errs[(best, name)] / errs[("learned", name)]))
+    err_l = errs[("learned", "BF16")]
+    assert err_l < 3e-3
+    assert err_l < errs[(4.0, "FP32")]

@@ -67,10 +67,19 @@ def test_forward_3d_refraction_16bit_echo():
     tx, rx = oracle_positions(nav)
     with oracle.medium(0.013, 1650.0):
         ref = oracle.backproject(tx, rx, oracle_signal(w), echo, 8, BETA, grid_pixels(w.grid))
-    for dt, tol in ((sas.SAS_ECHO_C32_F16, 3e-3), (sas.SAS_ECHO_C32_BF16, 3e-2)):
+    # the reduced-precision budget for both: BF16 rounding of the echo rows
+    # (8 significant bits, about 1.5e-3 rms) dominates the BF16 total
+    for dt, tol in ((sas.SAS_ECHO_C32_F16, 3e-3), (sas.SAS_ECHO_C32_BF16, 3e-3)):
         geom.upload_echo(echo, dt)
         img = _image(geom, w)
-        assert oracle.rel_l2(img.reshape(-1), ref) < tol
+        stored = geom.download_echo().cpu().numpy()
+        with oracle.medium(0.013, 1650.0):
+            ref_q = oracle.backproject(tx, rx, oracle_signal(w), stored, 8, BETA, grid_pixels(w.grid))
+        e_total, e_kernel = oracle.rel_l2(img.reshape(-1), ref), oracle.rel_l2(img.reshape(-1), ref_q)
+        print("refraction, 16-bit echo %d: kernel on the stored echo %.3g, total %.3g, echo rounding %.3g" % (
+            dt, e_kernel, e_total, oracle.rel_l2(ref_q, ref)))
+        assert e_kernel < 1e-3
+        assert e_total < tol
     geom.close()
 
 
