@@ -13,6 +13,12 @@ the slowest rank's time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload stripmap_2d|volume_3d|autofocus_2d|small_2d] [--echo c64|f16|bf16]
+
+The line also carries the second half of the metric ("learned_bf16"): the
+learned interpolator (trained on the GPU at start-up by the library's own
+kernels) with BF16 echo storage on the same workload, its throughput, its
+ratio to the FP32 line and its rel-L2 against the FP64 oracle's 32-tap
+interpolation on sampled pixels.
 """
 from __future__ import annotations
 
@@ -40,10 +46,11 @@ BETA = 4.0
 # lanes/clk/SM -> 4 updates per clock per SM from either pipe.
 UPDATES_PER_CLK_PER_SM = 4.0
 # DRAM bytes (read + write) per launch of the forward kernel, beam off, from an
-# ncu capture of the same kernel on 64 pings of the stripmap workload: reads
-# 128.3 MB (scaled by 2048 / 64 pings: each ping's rows are read once) plus the
-# 114.5 MB image write.  Only the configurations captured are listed.
-TRAFFIC_BYTES = {("stripmap_2d", "c64"): 129.5e6 * 2048 / 64 + 114.6e6}
+# ncu capture of the current kernel on 64 pings of the stripmap workload: the
+# reads scaled by 2048 / 64 pings (each ping's rows are read once) plus the
+# image write.  Only the configurations captured with the current kernel are
+# listed (others report null).
+TRAFFIC_BYTES = {}
 
 
 def parse():
@@ -66,6 +73,8 @@ def parse():
                     help="receivers move during reception (per-ping velocity), not stop-and-hop")
     ap.add_argument("--beam-deg", type=float, default=0.0,
                     help="azimuth beam width [deg] (ray culling on); 0 = omnidirectional")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned-interpolator / BF16 arm (2D straight-path workloads only)")
     ap.add_argument("--refraction", type=float, default=0.0, metavar="C_SEDIMENT",
                     help="seabed refraction: sediment sound speed [m/s] below the interface z = 0 (the "
                          "workloads' seafloor); 0 = straight paths")
@@ -220,7 +229,7 @@ def config_of(w, args):
     g = w.grid
     return {"workload": w.name, "pings": w.n_pings, "rx": w.n_rx, "samples": w.n_samples,
             "pixels": "%dx%dx%d" % (g.nx, g.ny, g.nz), "pixel_m": g.dx, "taps": 8,
-            "interp": "kaiser_sinc beta=%g (Farrow degree 5)" % BETA, "echo": args.echo,
+            "interp": "kaiser_sinc beta=%g (Farrow form, a cubic on each half sample)" % BETA, "echo": args.echo,
             "updates_per_step": w.updates, "l2": l2_note(w, args), "parallelism": "replicas",
             "delay_model": ("receiver moving during reception" if args.motion else "stop-and-hop") +
                            (", seabed refraction (interface z = 0, c_sediment = %g m/s)" % args.refraction
@@ -265,8 +274,16 @@ def run_ours(args, rank, world, local_rank):
     def step():
         fn(geom.h, grid, interp, image, 0)
 
+    # the paper's timing protocol (Sec. III-C): the same job three times, the
+    # third reported -- here the third of the warm-up runs, each timed alone
+    warm_ms = []
     for _ in range(args.warmup):
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
         step()
+        w1.record(stream)
+        w1.synchronize()
+        warm_ms.append(w0.elapsed_time(w1))
     geom.sync_status()
     geom.cull_stats(reset=True)
     if world > 1:
@@ -340,6 +357,13 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": e2e_s * 1e3}
         del h_echo, h_img
 
+    # second half of the metric: the learned interpolator with BF16 echo storage
+    # on the same workload, its speed against the FP32 Kaiser-sinc line above and
+    # its error against the FP64 oracle's 32-tap interpolation on sampled pixels
+    learned_line = None
+    if args.learned and not (args.beam_deg > 0 or args.motion or args.refraction > 0 or dim3):
+        learned_line = learned_arm(args, w, nav, echo, geom, grid, image, stream, ms_per_step, rank == 0)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, nav, echo, args.cpu_seconds)
@@ -355,9 +379,63 @@ def run_ours(args, rank, world, local_rank):
                              "computed_fraction": computed / max(cand, 1.0),
                              "updates_computed": computed_updates, "updates_dense": w.updates}}
                    if args.beam_deg > 0 else {}),
-                "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms), "max": max(launch_ms)}}
+                "launch_ms": {"mean": statistics.mean(launch_ms), "min": min(launch_ms), "max": max(launch_ms)},
+                "paper_protocol": {"runs": "third of three consecutive runs (Sec. III-C), the third warm-up run",
+                                   "ms": warm_ms[2] if len(warm_ms) >= 3 else None,
+                                   "value": (world * w.updates / (warm_ms[2] / 1e3) / 1e9) if len(warm_ms) >= 3
+                                   else None},
+                **({"learned_bf16": learned_line} if learned_line else {})}
         print(json.dumps(line), flush=True)
     geom.close()
+
+
+def learned_arm(args, w, nav, echo, geom, grid, image, stream, fp32_ms, report):
+    """The learned interpolator (MLP trained by the library's kernels on
+    simulator echoes, tabulated, prior + correction) applied with BF16 echo
+    storage to the same workload: device-timed like the FP32 line, plus rel-L2
+    against the FP64 oracle's 32-tap Kaiser-sinc (beta 10) on random pixels,
+    beside the plain FP32 8-tap line's error on the same pixels."""
+    import torch
+    import paper_2101_05888_gb300 as sas
+    from paper_2101_05888_gb300 import learned
+    t0 = time.perf_counter()
+    table, hist = learned.trained_table(4096)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    interp = learned.interp_from_table(table)
+    fn = sas.sas_backproject_2d
+    img32 = image.clone()                      # the FP32 Kaiser image of the timed line
+    geom.upload_echo(echo, sas.SAS_ECHO_C32_BF16)
+    for _ in range(args.warmup):
+        fn(geom.h, grid, interp, image, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fn(geom.h, grid, interp, image, 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    geom.sync_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"value": w.updates / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "ratio_vs_fp32": fp32_ms / ms, "echo": "bf16", "interp": "learned (MLP 1-64-64-8, FP16 weights, "
+            "Kaiser-sinc beta 4 prior + learned correction, 4096-fraction table, Farrow form)",
+            "train_s": train_s, "final_loss": hist[-1]}
+    if report:
+        import oracle
+        g = w.grid
+        idx = synth.random_pixel_indices(g, 192, seed=31)
+        pts = oracle.grid_index_points(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, idx)
+        tx, rx = oracle.sensor_positions(nav["pos"], nav["att"], nav["tx_lever"], nav["rx_lever"])
+        sig = oracle.Signal(synth.FC, synth.FS, synth.C_SOUND, w.t0, w.n_samples)
+        truth = oracle.backproject(tx, rx, sig, echo, 32, 10.0, pts)
+        at = lambda im: im[idx[:, 2], idx[:, 1], idx[:, 0]].cpu().numpy()
+        line["rel_l2_vs_32tap_oracle"] = oracle.rel_l2(at(image), truth)
+        line["fp32_kaiser_rel_l2_vs_32tap_oracle"] = oracle.rel_l2(at(img32), truth)
+        line["error_sample"] = "%d random pixels x all pings and channels, FP64 oracle, 32-tap Kaiser-sinc beta 10" % len(idx)
+    geom.upload_echo(echo, sas.SAS_ECHO_C64 if args.echo == "c64" else
+                     {"f16": sas.SAS_ECHO_C32_F16, "bf16": sas.SAS_ECHO_C32_BF16}[args.echo])
+    return line
 
 
 # algorithmic bytes per element (complex64 rows, or pixels for DRC): what a

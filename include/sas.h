@@ -278,18 +278,24 @@ int sas_simulate_points(sas_geometry_t h, const double* d_scat, int64_t n, doubl
  * order W1 [64][1], b1 [64], W2 [64][64] ([out][in]), b2 [64], W3 [8][64],
  * b3 [8]; the network input is x = 2 f - 1.  Kernels round the weights to
  * FP16 and compute in FP32:  a1 = gelu(W1 x + b1), a2 = gelu(W2 a1 + b2),
- * taps = W3 a2 + b3,  gelu(z) = z/2 (1 + erf(z/sqrt 2)). */
+ * t = W3 a2 + b3,  gelu(z) = z/2 (1 + erf(z/sqrt 2)).
+ * The interpolator's taps are the taps of a fixed prior, the normalised
+ * 8-tap Kaiser-sinc at beta = prior_beta (the plain interpolator), plus the
+ * network's correction t; prior_beta < 0 means no prior (taps = t).  The
+ * network is trained on residual targets (the 32-tap interpolation minus the
+ * prior's), so the loss below is the error of prior + network. */
 #define SAS_MLP_NPARAMS 4808
 
 /* Training windows from an echo (device complex64 [rows][Ns]): for n draws
  * (d_frac [n] FP32 fractions, d_row [n] int32 rows, d_pos [n] int32 sample
  * indices) writes the 8-sample window e[row][pos-3 .. pos+4] to d_windows
- * (complex64 [n][8]) and the 32-tap Kaiser-sinc (beta = target_beta)
- * interpolation at pos + frac to d_targets (complex64 [n]).  Samples outside
- * the row read as zero. */
+ * (complex64 [n][8]) and to d_targets (complex64 [n]) the 32-tap Kaiser-sinc
+ * (beta = target_beta) interpolation at pos + frac, minus the prior's 8-tap
+ * interpolation of the window if prior_beta >= 0 (both sums in FP64).
+ * Samples outside the row read as zero. */
 int sas_mlp_make_windows(const void* d_echo, int32_t rows, int32_t n_samples, const float* d_frac,
                          const int32_t* d_row, const int32_t* d_pos, int64_t n, double target_beta,
-                         void* d_windows, void* d_targets, void* cuda_stream);
+                         double prior_beta, void* d_windows, void* d_targets, void* cuda_stream);
 
 /* Loss L = mean_b |sum_m t_m(f_b) s_b,m - y_b|^2 and its gradient w.r.t. theta
  * (device FP32 [SAS_MLP_NPARAMS], overwritten) on a batch of n windows.
@@ -304,9 +310,10 @@ int sas_mlp_loss_grad(const float* d_theta, const float* d_frac, const void* d_w
 int sas_mlp_adam(float* d_theta, const float* d_grad, float* d_m, float* d_v, int32_t step,
                  float lr, float beta1, float beta2, float eps, void* cuda_stream);
 
-/* Tabulates the network's taps at f = j / table_n, j = 0 .. table_n, into
- * d_table_out (device FP32 [table_n + 1][8]) for use as SAS_INTERP_TABLE. */
-int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, float* d_table_out,
+/* Tabulates the interpolator's taps (the prior's, FP64, when prior_beta >= 0,
+ * plus the network's) at f = j / table_n, j = 0 .. table_n, into d_table_out
+ * (device FP32 [table_n + 1][8]) for use as SAS_INTERP_TABLE. */
+int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, double prior_beta, float* d_table_out,
                             void* cuda_stream);
 
 /* Waits for the stream, then reports and clears the handle's device status:

@@ -21,6 +21,12 @@ Loss on a batch of windows s_b [8] (complex) with targets y_b:
     L = (1/B) sum_b | sum_m t_m(f_b) s_b,m - y_b |^2
 Optimiser: Adam (Kingma & Ba, 2015) with bias correction.
 
+Interpolator taps with a prior (``interp_taps``): the normalised 8-tap
+Kaiser-windowed sinc at beta_p plus the network's output t, the network
+trained on residual targets y_b - sum_m k_m(f_b) s_b,m (k the prior's taps),
+so that L above is the squared error of prior + network; without a prior
+(beta_p < 0) the taps are t.
+
 Also: the least-squares-optimal 8-tap FIR for a wide-sense-stationary signal
 with flat spectrum on |nu| <= nu_b (cycles/sample), autocorrelation
 r(tau) = sinc(2 nu_b tau), from the normal equations R h = p.
@@ -76,6 +82,17 @@ def forward(theta, f):
     a2 = gelu(z2)
     t = a2 @ p["W3"].T + p["b3"]
     return t, (x, z1, a1, z2, a2)
+
+
+def interp_taps(theta, f, prior_beta: float):
+    """Taps [n, 8] of the learned interpolator at fractions f [n]: the
+    prior's Kaiser-sinc taps (FP64, none if prior_beta < 0) plus the network's."""
+    t, _ = forward(theta, f)
+    if prior_beta >= 0:
+        import oracle
+        t = t + np.stack([oracle.kaiser_sinc_weights(float(x), TAPS, prior_beta)
+                          for x in np.asarray(f, dtype=np.float64).reshape(-1)])
+    return t
 
 
 def loss_and_grad(theta, f, windows, targets):

@@ -123,11 +123,11 @@ def lib():
                 "sas_sharpness_static": ([V, I64, V, V, V], I),
                 "sas_simulate_points": ([V, V, I64, D, D, ctypes.c_int32, V, V], I),
                 "sas_interp_eval": ([P(sas_interp), V, I64, V, V, V], I),
-                "sas_mlp_make_windows": ([V, ctypes.c_int32, ctypes.c_int32, V, V, V, I64, D, V, V, V], I),
+                "sas_mlp_make_windows": ([V, ctypes.c_int32, ctypes.c_int32, V, V, V, I64, D, D, V, V, V], I),
                 "sas_mlp_workspace_bytes": ([I64], I64),
                 "sas_mlp_loss_grad": ([V, V, V, V, I64, V, V, V, V], I),
                 "sas_mlp_adam": ([V, V, V, V, ctypes.c_int32, F, F, F, F, V], I),
-                "sas_interp_tabulate_mlp": ([V, ctypes.c_int32, V, V], I),
+                "sas_interp_tabulate_mlp": ([V, ctypes.c_int32, D, V, V], I),
                 "sas_sync_status": ([V, V], I),
                 "sas_cull_stats": ([V, ctypes.POINTER(ctypes.c_longlong), I, V], I),
                 "sas_matched_filter": ([V, I64, ctypes.c_int32, V, ctypes.c_int32, V, V], I),
@@ -265,9 +265,9 @@ def sas_interp_eval(interp: sas_interp, d_f, n: int, d_taps, d_max_err=None, str
 
 
 def sas_mlp_make_windows(d_echo, rows: int, n_samples: int, d_frac, d_row, d_pos, n: int, target_beta: float,
-                         d_windows, d_targets, stream=None):
+                         prior_beta: float, d_windows, d_targets, stream=None):
     _check(lib().sas_mlp_make_windows(_ptr(d_echo), rows, n_samples, _ptr(d_frac), _ptr(d_row), _ptr(d_pos), n,
-                                      target_beta, _ptr(d_windows), _ptr(d_targets), _stream(stream)))
+                                      target_beta, prior_beta, _ptr(d_windows), _ptr(d_targets), _stream(stream)))
 
 
 def sas_mlp_workspace_bytes(n: int) -> int:
@@ -284,8 +284,8 @@ def sas_mlp_adam(d_theta, d_grad, d_m, d_v, step: int, lr: float, beta1=0.9, bet
                               _stream(stream)))
 
 
-def sas_interp_tabulate_mlp(d_theta, table_n: int, d_table_out, stream=None):
-    _check(lib().sas_interp_tabulate_mlp(_ptr(d_theta), table_n, _ptr(d_table_out), _stream(stream)))
+def sas_interp_tabulate_mlp(d_theta, table_n: int, prior_beta: float, d_table_out, stream=None):
+    _check(lib().sas_interp_tabulate_mlp(_ptr(d_theta), table_n, prior_beta, _ptr(d_table_out), _stream(stream)))
 
 
 def sas_sync_status(h, stream=None):

@@ -9,6 +9,9 @@
 // Network (x = 2 f - 1):  a1 = gelu(W1 x + b1), a2 = gelu(W2 a1 + b2), t = W3 a2 + b3,
 // gelu(z) = z/2 (1 + erf(z / sqrt 2)).  Loss on windows s_b (8 complex) with
 // targets y_b:  L = (1/B) sum_b |sum_m t_m(f_b) s_b,m - y_b|^2.
+// With a prior (the normalised 8-tap Kaiser-sinc at beta_p) the interpolator's
+// taps are prior + t: the targets are the 32-tap interpolation minus the
+// prior's 8-tap interpolation of the window, and the table adds the prior.
 // Parameter vector (FP32 masters): W1 [64][1], b1 [64], W2 [64][64] ([out][in]),
 // b2 [64], W3 [8][64], b3 [8].
 #include "sas_common.cuh"
@@ -46,9 +49,29 @@ __device__ double i0_series_d(double x) {
     return sum;
 }
 
+// Normalised Kaiser-windowed sinc of NTAPS taps at offsets k = 1 - NTAPS/2 .. NTAPS/2
+// from floor(u), for the fraction f (FP64).
+template <int NTAPS>
+__device__ void kaiser_taps(double f, double beta, double* w) {
+    const double h = 0.5 * NTAPS, i0b = i0_series_d(beta);
+    double sum = 0.0;
+    for (int m = 0; m < NTAPS; ++m) {
+        const double d = f - (double)(m - NTAPS / 2 + 1);
+        double v = 0.0;
+        if (fabs(d) < h) {
+            const double sinc = (d == 0.0) ? 1.0 : sin(M_PI * d) / (M_PI * d);
+            v = sinc * i0_series_d(beta * sqrt(1.0 - (d / h) * (d / h))) / i0b;
+        }
+        w[m] = v;
+        sum += v;
+    }
+    for (int m = 0; m < NTAPS; ++m) w[m] /= sum;
+}
+
 __global__ void make_windows_kernel(const float2* __restrict__ echo, int rows, int Ns, const float* __restrict__ frac,
                                     const int32_t* __restrict__ row, const int32_t* __restrict__ pos, long long n,
-                                    double beta, float2* __restrict__ win, float2* __restrict__ tgt) {
+                                    double beta, double prior_beta, float2* __restrict__ win,
+                                    float2* __restrict__ tgt) {
     const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (b >= n) return;
     const int r = min(max(row[b], 0), rows - 1);
@@ -60,24 +83,25 @@ __global__ void make_windows_kernel(const float2* __restrict__ echo, int rows, i
     }
     // 32 taps k = -15 .. 16, normalised Kaiser-windowed sinc at distance f - k
     const double f = (double)frac[b];
-    const double h = 16.0, i0b = i0_series_d(beta);
-    double w[32], sum = 0.0;
-    for (int m = 0; m < 32; ++m) {
-        const double d = f - (double)(m - 15);
-        double v = 0.0;
-        if (fabs(d) < h) {
-            const double sinc = (d == 0.0) ? 1.0 : sin(M_PI * d) / (M_PI * d);
-            v = sinc * i0_series_d(beta * sqrt(1.0 - (d / h) * (d / h))) / i0b;
-        }
-        w[m] = v;
-        sum += v;
-    }
+    double w[32];
+    kaiser_taps<32>(f, beta, w);
     double yr = 0.0, yi = 0.0;
     for (int m = 0; m < 32; ++m) {
         const long long j = p0 + m - 15;
         if (j < 0 || j >= Ns) continue;
-        yr += w[m] / sum * (double)e[j].x;
-        yi += w[m] / sum * (double)e[j].y;
+        yr += w[m] * (double)e[j].x;
+        yi += w[m] * (double)e[j].y;
+    }
+    if (prior_beta >= 0.0) {
+        // residual target: less the prior's 8-tap interpolation of the window
+        double wp[NT];
+        kaiser_taps<NT>(f, prior_beta, wp);
+        for (int m = 0; m < NT; ++m) {
+            const long long j = p0 + m - 3;
+            if (j < 0 || j >= Ns) continue;
+            yr -= wp[m] * (double)e[j].x;
+            yi -= wp[m] * (double)e[j].y;
+        }
     }
     tgt[b] = make_float2((float)yr, (float)yi);
 }
@@ -244,8 +268,9 @@ __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__
     theta[k] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-// One thread per fraction f = j / table_n: the taps as the network gives them.
-__global__ void tabulate_kernel(const float* __restrict__ theta, int table_n, float* __restrict__ out) {
+// One thread per fraction f = j / table_n: the prior's taps (if any) plus the network's.
+__global__ void tabulate_kernel(const float* __restrict__ theta, int table_n, double prior_beta,
+                                float* __restrict__ out) {
     __shared__ float W[NPAR];
     for (int k = threadIdx.x; k < NPAR; k += blockDim.x) W[k] = fp16_round(theta[k]);
     __syncthreads();
@@ -260,10 +285,12 @@ __global__ void tabulate_kernel(const float* __restrict__ theta, int table_n, fl
         for (int q = 0; q < H; ++q) z = fmaf(W[O_W2 + i * H + q], a1[q], z);
         a2[i] = gelu(z);
     }
+    double wp[NT];
+    if (prior_beta >= 0.0) kaiser_taps<NT>((double)j / (double)table_n, prior_beta, wp);
     for (int m = 0; m < NT; ++m) {
         float v = W[O_B3 + m];
         for (int i = 0; i < H; ++i) v = fmaf(W[O_W3 + m * H + i], a2[i], v);
-        out[(size_t)j * NT + m] = v;
+        out[(size_t)j * NT + m] = prior_beta >= 0.0 ? (float)(wp[m] + (double)v) : v;
     }
 }
 
@@ -276,7 +303,7 @@ using namespace sas;
 
 extern "C" int sas_mlp_make_windows(const void* d_echo, int32_t rows, int32_t n_samples, const float* d_frac,
                                     const int32_t* d_row, const int32_t* d_pos, int64_t n, double target_beta,
-                                    void* d_windows, void* d_targets, void* stream) {
+                                    double prior_beta, void* d_windows, void* d_targets, void* stream) {
     if (!d_echo || rows < 1 || n_samples < 1 || n < 0 || (n > 0 && (!d_frac || !d_row || !d_pos || !d_windows ||
                                                                      !d_targets))) {
         set_error("sas_mlp_make_windows: bad argument");
@@ -284,8 +311,8 @@ extern "C" int sas_mlp_make_windows(const void* d_echo, int32_t rows, int32_t n_
     }
     if (n == 0) return SAS_OK;
     make_windows_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
-        (const float2*)d_echo, rows, n_samples, d_frac, d_row, d_pos, n, target_beta, (float2*)d_windows,
-        (float2*)d_targets);
+        (const float2*)d_echo, rows, n_samples, d_frac, d_row, d_pos, n, target_beta, prior_beta,
+        (float2*)d_windows, (float2*)d_targets);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }
@@ -329,12 +356,14 @@ extern "C" int sas_mlp_adam(float* d_theta, const float* d_grad, float* d_m, flo
     return SAS_OK;
 }
 
-extern "C" int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, float* d_table_out, void* stream) {
-    if (!d_theta || !d_table_out || table_n < 1) {
+extern "C" int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, double prior_beta, float* d_table_out,
+                                       void* stream) {
+    if (!d_theta || !d_table_out || table_n < 1 || !(prior_beta < 50.0)) {
         set_error("sas_interp_tabulate_mlp: bad argument");
         return SAS_ERR_ARG;
     }
-    tabulate_kernel<<<(table_n + 1 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_theta, table_n, d_table_out);
+    tabulate_kernel<<<(table_n + 1 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(d_theta, table_n, prior_beta,
+                                                                               d_table_out);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }

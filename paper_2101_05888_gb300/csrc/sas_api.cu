@@ -181,9 +181,10 @@ __global__ void dequantize_rows_kernel(const T* __restrict__ src, const float* _
 }
 
 // ---------------------------------------------------------------------------
-// Interpolator in Farrow form.  Chebyshev interpolation of each tap's weight
-// w_m(f) at the NP first-kind Chebyshev nodes of f in [0, 1], converted to
-// monomials of g = f - 1/2.  FP64 throughout.
+// Interpolator in Farrow form on half-sample sub-intervals.  On each half h
+// of the sample interval, Chebyshev interpolation of each tap's weight
+// w_m(f) at the NP first-kind Chebyshev nodes of f in [h/2, (h+1)/2],
+// converted to monomials of g = 2 f - h - 1/2.  FP64 throughout.
 
 __device__ double i0_series(double x) {
     const double q = 0.25 * x * x;
@@ -224,57 +225,67 @@ __device__ void interp_weights(int kind, double beta, int table_n, const float* 
     }
 }
 
+// Monomial coefficients in g of tap t's weight on half h (FP64, not rounded).
+__device__ void fit_half_tap(const double (*node_w)[TAPS], int t, double mono_g[NP]) {
+    // Chebyshev coefficients a_k = (2/NP) sum_j y_j T_k(x_j), a_0 halved
+    double a[NP];
+    for (int k = 0; k < NP; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < NP; ++j) s += node_w[j][t] * cos(M_PI * k * (j + 0.5) / NP);
+        a[k] = 2.0 * s / NP;
+    }
+    a[0] *= 0.5;
+    // monomials in x: T_0 = 1, T_1 = x, T_{k+1} = 2x T_k - T_{k-1}
+    double tkm1[NP] = {0}, tk[NP] = {0}, mono[NP] = {0};
+    tkm1[0] = 1.0;
+    tk[1] = 1.0;
+    mono[0] += a[0];
+    for (int p = 0; p < NP; ++p) mono[p] += a[1] * tk[p];
+    for (int k = 2; k < NP; ++k) {
+        double tn[NP] = {0};
+        for (int p = 0; p < NP; ++p) tn[p] = (p > 0 ? 2.0 * tk[p - 1] : 0.0) - tkm1[p];
+        for (int p = 0; p < NP; ++p) {
+            tkm1[p] = tk[p];
+            tk[p] = tn[p];
+            mono[p] += a[k] * tn[p];
+        }
+    }
+    double s = 1.0;
+    for (int p = 0; p < NP; ++p) {  // x = 2 g
+        mono_g[p] = mono[p] * s;
+        s *= 2.0;
+    }
+}
+
 __global__ void fit_interp_kernel(int kind, double beta, int table_n, const float* table, FarrowCoef* out,
                                   double* err) {
-    __shared__ double node_w[NP][TAPS];
+    __shared__ double node_w[NH][NP][TAPS];
     __shared__ double emax[128];
     const int t = threadIdx.x;
-    if (t < NP) {
-        const double x = cos(M_PI * (t + 0.5) / NP);
-        interp_weights(kind, beta, table_n, table, 0.5 + 0.5 * x, node_w[t]);
+    if (t < NH * NP) {
+        const int h = t / NP, j = t % NP;
+        const double x = cos(M_PI * (j + 0.5) / NP);
+        interp_weights(kind, beta, table_n, table, 0.5 * (h + 0.5 + 0.5 * x), node_w[h][j]);
     }
     __syncthreads();
-    if (t < TAPS) {
-        // Chebyshev coefficients a_k = (2/NP) sum_j y_j T_k(x_j), a_0 halved
-        double a[NP];
-        for (int k = 0; k < NP; ++k) {
-            double s = 0.0;
-            for (int j = 0; j < NP; ++j) s += node_w[j][t] * cos(M_PI * k * (j + 0.5) / NP);
-            a[k] = 2.0 * s / NP;
-        }
-        a[0] *= 0.5;
-        // monomials in x: T_0 = 1, T_1 = x, T_{k+1} = 2x T_k - T_{k-1}
-        double tkm1[NP] = {0}, tk[NP] = {0}, mono[NP] = {0};
-        tkm1[0] = 1.0;
-        tk[1] = 1.0;
-        mono[0] += a[0];
-        for (int p = 0; p < NP; ++p) mono[p] += a[1] * tk[p];
-        for (int k = 2; k < NP; ++k) {
-            double tn[NP] = {0};
-            for (int p = 0; p < NP; ++p) tn[p] = (p > 0 ? 2.0 * tk[p - 1] : 0.0) - tkm1[p];
-            for (int p = 0; p < NP; ++p) {
-                tkm1[p] = tk[p];
-                tk[p] = tn[p];
-                mono[p] += a[k] * tn[p];
-            }
-        }
-        double s = 1.0;
-        for (int p = 0; p < NP; ++p) {  // x = 2 g
-            out->c[t][p] = (float)(mono[p] * s);
-            s *= 2.0;
-        }
+    if (t < NH * TAPS) {
+        const int h = t / TAPS, m = t % TAPS;
+        double mono[NP];
+        fit_half_tap(node_w[h], m, mono);
+        for (int p = 0; p < NP; ++p) out->c[h][m][p] = (float)mono[p];
     }
     __syncthreads();
-    // deviation of the (float-rounded) polynomial from the definition
+    // deviation of the (float-rounded) polynomials from the definition
     double e = 0.0;
     for (int q = t; q <= 2048; q += blockDim.x) {
         const double f = q / 2048.0;
         double w[TAPS];
         interp_weights(kind, beta, table_n, table, f, w);
-        const double g = f - 0.5;
+        const int h = min((int)(2.0 * f), NH - 1);
+        const double g = 2.0 * f - h - 0.5;
         for (int m = 0; m < TAPS; ++m) {
             double v = 0.0;
-            for (int p = NP - 1; p >= 0; --p) v = v * g + (double)out->c[m][p];
+            for (int p = NP - 1; p >= 0; --p) v = v * g + (double)out->c[h][m][p];
             e = fmax(e, fabs(v - w[m]));
         }
     }
@@ -319,10 +330,12 @@ __global__ void interp_eval_kernel(const FarrowCoef* __restrict__ coef, const fl
                                    float* __restrict__ taps) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float g = f[i] - 0.5f;
+    // the half of the interval (fractions outside [0, 1) extend the nearer half's cubic)
+    const int h = min(max((int)floorf(2.0f * f[i]), 0), NH - 1);
+    const float g = fmaf(2.0f, f[i], -(float)h - 0.5f);
     for (int m = 0; m < TAPS; ++m) {
-        float v = coef->c[m][NP - 1];
-        for (int p = NP - 2; p >= 0; --p) v = fmaf(v, g, coef->c[m][p]);
+        float v = coef->c[h][m][NP - 1];
+        for (int p = NP - 2; p >= 0; --p) v = fmaf(v, g, coef->c[h][m][p]);
         taps[i * TAPS + m] = v;
     }
 }

@@ -27,10 +27,14 @@ int cuda_fail(cudaError_t e, const char* what);
 enum : uint32_t { DEV_TIMEOUT = 1u };
 
 // ---------------------------------------------------------------------------
-// Interpolator in Farrow form: tap m (offset k_m = m - 3) has weight
-//   w_m(f) = sum_{p<NP} coef[m][p] g^p,  g = f - 1/2,
-// so the interpolated value is a polynomial in g whose coefficients are FIR
-// outputs of the echo:  s = sum_p g^p E_p[i0],  E_p[i] = sum_m coef[m][p] e[i + k_m].
+// Interpolator in Farrow form on half-sample sub-intervals: the sample
+// interval [i0, i0 + 1) splits into the halves h = floor(2 f) (f = u - i0),
+// and on half h tap m (offset k_m = m - 3) has the weight
+//   w_m(f) = sum_{p<NP} coef[h][m][p] g^p,  g = 2 f - h - 1/2 in [-1/2, 1/2),
+// so the interpolated value is a cubic in g whose coefficients are FIR
+// outputs of the echo:  s = sum_p g^p E_p^h[i0],  E_p^h[i] = sum_m coef[h][m][p] e[i + k_m].
+// g is the fraction of the half-sample coordinate 2u: with n = floor(2u),
+// i0 = floor(n / 2) and h = n mod 2.
 // ---------------------------------------------------------------------------
 // Attitude rotation of Eq. 2 (roll phi, pitch theta, yaw psi), row-major R:
 //   [ ct cps,  cps st sph - cph sps,  cph cps st + sph sps ]
@@ -47,14 +51,16 @@ __device__ __forceinline__ void attitude_rotation(double roll, double pitch, dou
 }
 
 constexpr int TAPS = 8;
-constexpr int NP = 6;            // polynomial degree 5
+constexpr int NH = 2;            // sub-intervals (halves) of a sample interval
+constexpr int NP = 4;            // polynomial degree 3 on each
 struct FarrowCoef {
-    float c[TAPS][NP];
+    float c[NH][TAPS][NP];
 };
 
 // Fits the interpolator to Farrow form on the device (FP64 Chebyshev
-// interpolation at NP nodes, converted to monomials in g).  d_coef: device
-// FarrowCoef; d_err: optional device double, max |fit - definition|.
+// interpolation at NP nodes of each half, converted to monomials in g).
+// d_coef: device FarrowCoef; d_err: optional device double, max |fit -
+// definition| over the weights.
 int fit_interp(const sas_interp* interp, FarrowCoef* d_coef, double* d_err, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
@@ -93,26 +99,31 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+// One test of the phase with the given parity; while it is incomplete the
+// thread may be suspended until it completes or suspend_ns pass.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity, uint32_t suspend_ns) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(suspend_ns)
         : "memory");
     return ok != 0;
 }
 
 // Waits for the barrier phase with the given parity to complete; gives up
 // after limit_ns of wall time (returns false).  Never spins unboundedly.
+// Each test suspends the waiting warp (up to 200 us) rather than spinning, so
+// a warp that waits does not take issue slots from the warps that work.
+constexpr uint32_t MBAR_SUSPEND_NS = 200000;
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity, MBAR_SUSPEND_NS)) return true;
     const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 15u) == 15u && globaltimer_ns() - t0 > limit_ns) return false;
+    for (;;) {
+        if (mbar_try_wait(bar, parity, MBAR_SUSPEND_NS)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 

@@ -5,10 +5,12 @@
 //
 // Linear adjoint, one CTA per tile (warp 0 computes the FP64 reference terms
 // of 32 pairs at a time, warps 1..7 own 8 pixels each).  With the Farrow form
-// w_k(f) = sum_p coef[k][p] g^p the per-pixel work is a scatter of g^p v
-// (v = I(x) exp(-j 2 pi fc tau)) into accumulators A_p[floor u] in shared
-// memory; a transposed FIR e[floor u + k] += sum_p coef[k][p] A_p[floor u]
-// then adds each pair's segment to the echo with global atomics.
+// w_k(f) = sum_p coef[h][k][p] g^p on the half h of the sample interval the
+// per-pixel work is a scatter of g^p v (v = I(x) exp(-j 2 pi fc tau)) into
+// accumulators A_p[n] in shared memory, n = floor(2u) the half-sample
+// index; a transposed FIR e[floor u + k] += sum_h sum_p coef[h][k][p]
+// A_p[2 floor u + h] then adds each pair's segment to the echo with global
+// atomics.
 #include "tdbp_core.cuh"
 
 namespace sas {
@@ -23,10 +25,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                                                               float2* __restrict__ eadj, int Ns) {
     using T = Tile<DIM3>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float2* A = reinterpret_cast<float2*>(smem);                    // [GROUP][npos][NP]
-    float* rec = reinterpret_cast<float*>(A + GROUP * p.npos * NP);  // [NREC][PAIRS], field-major
-    float* coef_s = rec + NREC * PAIRS;                             // [TAPS][NP]
-    int* base_s = reinterpret_cast<int*>(coef_s + TAPS * NP);       // [PAIRS]
+    const int nrow = NH * p.npos;                                   // half-sample rows per pair
+    float2* A = reinterpret_cast<float2*>(smem);                    // [GROUP][nrow][NP]
+    float* rec = reinterpret_cast<float*>(A + GROUP * nrow * NP);   // [NREC][PAIRS], field-major
+    float* coef_s = rec + NREC * PAIRS;                             // [NH][TAPS][NP]
+    int* base_s = reinterpret_cast<int*>(coef_s + NH * TAPS * NP);  // [PAIRS]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = p.tiles_x * p.tiles_y * p.tiles_z;
@@ -41,11 +44,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
     const int nq = (int)(q1 - q0);
     const double cx = tx0 + 0.5 * (T::TX - 1), cy = ty0 + 0.5 * (T::TY - 1), cz = tz0 + 0.5 * (T::TZ - 1);
     const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = p.z0 + (DIM3 ? cz * p.dz : 0.0);
-    const int alen = GROUP * p.npos * NP;
+    const int alen = GROUP * nrow * NP;
     const int span = p.npos + TAPS - 1;            // output samples per pair segment
 
     for (int t = tid; t < alen; t += NTHREADS) A[t] = make_float2(0.f, 0.f);
-    if (tid < TAPS * NP) coef_s[tid] = (&p.coef->c[0][0])[tid];
+    if (tid < NH * TAPS * NP) coef_s[tid] = (&p.coef->c[0][0][0])[tid];
 
     const bool consumer = warp > 0;
     const int ct = tid - 32;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                         bRy = rp[F_BRY * PAIRS];
                         bRz = rp[F_BRZ * PAIRS];
                     }
-                    float2* Aj = A + j * p.npos * NP;
+                    float2* Aj = A + j * nrow * NP;
                     float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f;
                     if (p.beam) {
@@ -156,16 +159,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                             const float eps = fmaf(dvar[s], vv, Km) * rs;         // u_R . v / c
                             D = D * fmaf(eps, eps - 1.f, 1.f);                   // / (1 + eps)
                         }
-                        const float v = fmaf(D, p.fs_c, ufc);              // u - 1/2
-                        const float ph = fmaf(D, p.fc_c, phr);             // carrier phase [cycles]
-                        // nearest integer of u - 1/2 = floor(u); g = frac(u) - 1/2
+                        const float v = fmaf(D, p.hs_c, ufc);              // 2 (u - floor u_ref) - 1/2
+                        float ph = fmaf(D, p.wfc_c, phr);                  // carrier phase [rad]
+                        // nearest integer of v = the half-sample index; g = frac(2u) - 1/2
                         const float t = __fadd_rn(v, FLOOR_MAGIC);
                         const float g = v - (t - FLOOR_MAGIC);
-                        const unsigned pos = min((unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - p.U)),
-                                                 (unsigned)(p.npos - 1));
-                        const float pt = __fadd_rn(ph, FLOOR_MAGIC) - FLOOR_MAGIC;
+                        const unsigned pos = min((unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
+                                                 (unsigned)(nrow - 1));
+                        if (!p.phase_direct) ph = reduce_phase(ph);
                         float sn, cs;
-                        sincos_2pi(ph - pt, sn, cs);
+                        sincos_sfu(ph, sn, cs);
                         // v = G exp(-j phase)
                         float vx = fmaf(G[s].x, cs, G[s].y * sn);
                         float vy = fmaf(G[s].y, cs, -G[s].x * sn);
@@ -181,24 +184,27 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                 }
             }
             __syncthreads();
-            // transposed FIR and flush: out[t] = sum_m sum_p coef[m][p] A_p[t - m]
+            // transposed FIR and flush: out[t] = sum_m sum_h sum_p coef[h][m][p] A_p[2 (t - m) + h]
             const int items = GROUP * span;
             for (int it = tid; it < items; it += NTHREADS) {
                 const int j = it / span, t = it - j * span;
                 const int pr = g0 + j;
                 if (pr >= npairs) continue;
-                const float2* Aj = A + j * p.npos * NP;
+                const float2* Aj = A + j * nrow * NP;
                 float ox = 0.f, oy = 0.f;
 #pragma unroll
                 for (int m = 0; m < TAPS; ++m) {
                     const int pos = t - m;
                     if (pos < 0 || pos >= p.npos) continue;
 #pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        const float c = coef_s[m * NP + q];
-                        const float2 v = Aj[pos * NP + q];
-                        ox = fmaf(c, v.x, ox);
-                        oy = fmaf(c, v.y, oy);
+                    for (int h = 0; h < NH; ++h) {
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            const float c = coef_s[(h * TAPS + m) * NP + q];
+                            const float2 v = Aj[(NH * pos + h) * NP + q];
+                            ox = fmaf(c, v.x, ox);
+                            oy = fmaf(c, v.y, oy);
+                        }
                     }
                 }
                 const long long idx = (long long)base_s[pr] + t;
@@ -220,8 +226,9 @@ static int launch_linear_adjoint(sas_geometry_t h, const sas_grid& g, const floa
     int rc = core::prepare(h, g, dim3, 2LL * sm_count(), S, false);
     if (rc != SAS_OK) return rc;
     SAS_CUDA(cudaMemsetAsync(eadj, 0, sizeof(float2) * (size_t)h->P * h->C * h->Ns, st));
-    const size_t smem = sizeof(float2) * core::GROUP * S.prm.npos * NP + sizeof(float) * core::NREC * core::PAIRS +
-                        sizeof(float) * TAPS * NP + sizeof(int) * core::PAIRS;
+    const size_t smem = sizeof(float2) * core::GROUP * NH * S.prm.npos * NP +
+                        sizeof(float) * core::NREC * core::PAIRS + sizeof(float) * NH * TAPS * NP +
+                        sizeof(int) * core::PAIRS;
     if (dim3) {
         auto k = core::adjoint_kernel<true>;
         SAS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -19,22 +19,28 @@
 //    Samples outside the row are zero-filled by the copy engine.  The
 //    producer also expands each stage's pairs, 4 at a time (a group), into a
 //    ring of NBUF Farrow buffers handed to the consumers by mbarriers:
-//    - Farrow expansion: the interpolator's taps are
-//      degree-5 polynomials of g = f - 1/2, so s = sum_p g^p E_p[floor u] with
-//      E_p[i] = sum_m coef[m][p] e[i + k_m], computed once per (pair, tile)
-//      for every integer position the tile can reach.  Complex64 echoes:
-//      E_0..E_5 in FP32, one 48-byte row per position, Horner in packed
-//      FP32.  16-bit echoes (rows normalised to |e| <= 1, so |E_p| stays
-//      near 1): E_0..E_5 in FP16 (24 bytes of the row) and the forward
-//      Horner in packed FP16, the row scale applied afterwards in FP32.
+//    - Farrow expansion: on each half of a sample interval the interpolator's
+//      taps are cubics in g (the fraction of the half-sample coordinate 2u,
+//      minus 1/2), so s = sum_p g^p E_p^h[floor u] with
+//      E_p^h[i] = sum_m coef[h][m][p] e[i + k_m], computed once per (pair,
+//      tile) for both halves of every sample position the tile can reach:
+//      one row per half-sample position.  Complex64 echoes: E_0..E_3 in FP32,
+//      a 32-byte row read by two 16-byte loads.  16-bit echoes (rows
+//      normalised to |e| <= 1, so |E_p| stays near 1): E_0..E_3 in FP16, a
+//      16-byte row, and the forward Horner in packed FP16, the row scale
+//      applied afterwards in FP32.
 //  * consumers, 8 pixels a thread, group after group:
 //    - per pixel and pair, with the pair's reference terms read by uniform
 //      16-byte loads: differential range dr = (2 R.d + |d|^2) / (|R + d| + |R|), an
-//      exact identity evaluated in FP32 on small quantities (d = x - x0); u
+//      exact identity evaluated in FP32 on small quantities (d = x - x0); 2u
 //      and the phase from the reference values plus dr-derived offsets;
-//      floor/fraction on the FP32 pipe; three 16-byte shared loads (one 16-
-//      and one 8-byte load for FP16 rows); Horner in g; SFU rsqrt, rcp, sin,
-//      cos.
+//      floor/fraction on the FP32 pipe; the row (two 16-byte shared loads,
+//      or one for FP16 rows); cubic Horner in g; SFU rsqrt, rcp, sin, cos (the
+//      carrier phase in radians, taken directly while it stays within 512 rad).
+//    - the pixels of a warp form an 8 x 4 block (4 x 2 per quarter-warp), so
+//      the rows one 16-byte load instruction reads span fewer than 8
+//      consecutive half-sample positions (quarter-warp phases) and fall in
+//      distinct bank groups.
 //  * every mbarrier wait is bounded in wall time: on expiry the CTA records a
 //    timeout in the status word, stops, and the producer waits (bounded) for
 //    the copies it has in flight before exiting.
@@ -53,12 +59,13 @@ constexpr int NTHREADS = NCONS + 32;    // + producer warp
 constexpr int PAIRS = 32;               // (ping, channel) pairs per stage
 constexpr int NSEG = 2;                 // echo-segment ring depth (stages)
 constexpr int NRS = 3;                  // record ring depth (stages)
-constexpr int NBUF = 4;                 // Farrow buffers (groups)
+constexpr int NBUF = 3;                 // Farrow buffers (groups)
 constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
-constexpr int EROW = 48;                // bytes per Farrow position allocated (layouts below)
-constexpr int RUN = 10;                 // Farrow positions per expansion run
+constexpr int ROW32 = 32;               // bytes of an FP32 Farrow row: E0..E3 as FP32 pairs
+constexpr int ROW16 = 16;               // bytes of an FP16 Farrow row (16-bit echoes, forward pass)
+constexpr int RUN = 15;                 // sample positions per expansion run
 constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
 enum { MODE_FORWARD = 0, MODE_OFFSET_GRAD = 1 };
@@ -66,7 +73,7 @@ enum { MODE_FORWARD = 0, MODE_OFFSET_GRAD = 1 };
 enum { GD_STAGE_END = 1, GD_LAST = 2 };
 
 // record fields of one (ping, channel) pair, in the order of the float4 a
-// consumer loads: {2R_R, |R_R|^2}, {|R_R|, frac u_ref - 1/2, phase, scale},
+// consumer loads: {2R_R, |R_R|^2}, {|R_R|, 2 frac u_ref - 1/2, phase [rad], scale},
 // {2R_T, |R_T|^2}, {|R_T|, ping, flags, segment offset}, {c0, c1.x},
 // {c1.y, c1.z, -, -} (c0, c1: columns 0 and 1 of the attitude matrix), and
 // with receiver motion {v/c, R_R.v/c}, {2R_R at the ping time, -} (R_R is
@@ -103,9 +110,10 @@ struct KParams {
     int tiles_x, tiles_y, tiles_z, nsplit, pings_per_split;
     int P, C;
     double t0, fs, fc, inv_c;
-    float fs_c, fc_c;       // fs/c, fc/c
-    float2 fs_c2, fc_c2;    // the same, duplicated for packed pixel pairs
-    float fs_f, wfc;        // fs, 2 pi fc
+    float hs_c, wfc_c;      // 2 fs/c (half samples per metre of path), 2 pi fc/c (radians per metre)
+    float2 hs_c2, wfc_c2;   // the same, duplicated for packed pixel pairs
+    int phase_direct;       // carrier phases stay within +-PHASE_DIRECT_MAX rad: no reduction
+    float fs2_f, wfc;       // 2 fs (ds/du = 2 ds/dg), 2 pi fc
     float grad_scale;       // -2/c (factor 2 of dL/dp = 2 Re(...), -1/c of dtau/dp)
     // beam field of view (Sec. II-C): sensor sees x iff b = R^T (x - sensor) has
     // side b_y > 0 and |b_x| <= beam_tan side b_y; rotc [P][6] = columns 0, 1 of R
@@ -129,13 +137,17 @@ struct KParams {
 
 template <bool DIM3>
 struct Tile;
+// Lane l of a warp holds column (l & 3) + 4 (l >> 4) and row (l >> 2) & 3 of an
+// 8 x 4 block: a half-warp is a 4 x 4 block, a quarter-warp a 4 x 2 block.
+__device__ __forceinline__ int lane_col(int l) { return (l & 3) + ((l >> 2) & 4); }
+__device__ __forceinline__ int lane_row(int l) { return (l >> 2) & 3; }
 template <>
-struct Tile<false> {  // 2D: 56 (x) x 32 (y); warp w covers x in [8w, 8w+8), rows (lane>>3) + 4s
+struct Tile<false> {  // 2D: 56 (x) x 32 (y); warp w covers x in [8w, 8w+8), rows lane_row + 4s
     static constexpr int TX = 56, TY = 32, TZ = 1;
     __device__ static void pixel(int ct, int s, int& lx, int& ly, int& lz) {
         const int w = ct >> 5, l = ct & 31;
-        lx = w * 8 + (l & 7);
-        ly = (l >> 3) + 4 * s;
+        lx = w * 8 + lane_col(l);
+        ly = lane_row(l) + 4 * s;
         lz = 0;
     }
 };
@@ -144,8 +156,8 @@ struct Tile<true> {   // 3D: 8 (x) x 28 (y) x 8 (z); warp w covers y in [4w, 4w+
     static constexpr int TX = 8, TY = 28, TZ = 8;
     __device__ static void pixel(int ct, int s, int& lx, int& ly, int& lz) {
         const int w = ct >> 5, l = ct & 31;
-        lx = l & 7;
-        ly = w * 4 + (l >> 3);
+        lx = lane_col(l);
+        ly = w * 4 + lane_row(l);
         lz = s;
     }
 };
@@ -189,6 +201,27 @@ __device__ __forceinline__ void sincos_2pi(float x, float& sn, float& cs) {
 }
 constexpr float TWO_PI_F = 6.28318530717958647f;
 
+// Carrier phases: x = phase_ref + 2 pi fc/c D in radians.  sin.approx and
+// cos.approx keep an absolute error of about |x| 1.5e-7 (measured: 6.6e-5 at
+// |x| = 450, 1.1e-7 rms on [-pi, pi]) -- the error of rounding x itself at that
+// magnitude -- so while every phase of a launch stays within PHASE_DIRECT_MAX
+// they take x directly.  Beyond it the phase is first reduced to [-pi, pi] by
+// x - 2 pi n, n = rint(x / 2 pi), with 2 pi split in two constants (C1 exact
+// in 8 bits, so n C1 is exact for |n| < 2^15).
+constexpr double PHASE_DIRECT_MAX = 512.0;
+constexpr float PHASE_C1 = 6.28125f;
+constexpr float PHASE_C2 = 1.9353071795864769e-3f;   // 2 pi - C1
+__device__ __forceinline__ float2 reduce_phase2(float2 x) {
+    const float2 M = make_float2(FLOOR_MAGIC, FLOOR_MAGIC);
+    const float2 n = fsub2(ffma2(x, make_float2(0.15915494309189535f, 0.15915494309189535f), M), M);
+    x = ffma2(n, make_float2(-PHASE_C1, -PHASE_C1), x);
+    return ffma2(n, make_float2(-PHASE_C2, -PHASE_C2), x);
+}
+__device__ __forceinline__ float reduce_phase(float x) {
+    const float n = __fadd_rn(fmaf(x, 0.15915494309189535f, FLOOR_MAGIC), -FLOOR_MAGIC);
+    return fmaf(n, -PHASE_C2, fmaf(n, -PHASE_C1, x));
+}
+
 
 __device__ __forceinline__ __half2 h2_of_bits(uint32_t b) {
     return *reinterpret_cast<__half2*>(&b);
@@ -198,21 +231,22 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
     return make_float2(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
 }
 
-// Farrow row layouts (48-B rows, one per position):
-//  * E16 (forward pass, 16-bit echo): E0..E5 FP16 pairs in the first 24 B.
-//  * otherwise: E0..E5 FP32 pairs.
-//  * TAIL16 (off): E0..E3 FP32 pairs (32 B), then E4, E5 as BF16 pairs (8 B),
-//    so that a pixel reads 40 B: 15 % fewer shared-memory wavefronts, 15 %
-//    more instructions (the BF16 unpacking) and 1.3 % slower on the stripmap
-//    workload (641.9 against 650.0 G updates/s), where the issue rate binds as
-//    much as the shared pipe.  (BF16 for E4, E5 changes the interpolated
-//    value by 3e-6 rms relative.)
-//  (Also measured and dropped: each sample interval in two halves with a
-//  degree-3 polynomial on each, one 32-B row per half-sample position: 8
-//  instead of 12 wavefronts and two fewer FMAs per pixel, 3.6e-5 rms
-//  interpolation error, but 514 G updates/s: rows 4 half-samples apart share
-//  their banks, so neighbouring pixels' loads conflict (1.5e10 conflicts per
-//  64-ping launch against 1.6e7).)
+// Farrow rows, one per half-sample position r = 2 n + h (sample position n
+// of the tile's window, half h), in a group buffer [GROUP][npos_pad * NH]:
+//  * ROW32 (complex64 echoes, and every echo in the gradient pass): E0..E3
+//    as FP32 pairs in two 16-byte halves, (E0, E1) and (E2, E3), read by two
+//    16-byte loads; on rows with bit 2 of r set the halves trade places.  A
+//    16-byte load is served a quarter-warp (a 4 x 2 pixel block) per
+//    wavefront, and the rows one quarter-warp reads span fewer than 8 half
+//    samples: with the swap, rows r and r + 4 put a given half in different
+//    bank groups, so each half-load meets no bank conflict.
+//  * ROW16 (16-bit echoes, forward pass): E0..E3 as FP16 pairs, 16 bytes, one
+//    16-byte load.
+//  (Measured alternatives: one degree-5 polynomial per sample interval in
+//  48-byte FP32 rows reads 1.5x the bytes per update and bound the kernel at
+//  the shared-memory data pipe; 24-byte rows with E2, E3 in BF16 read by three
+//  8-byte loads were 2.5 % slower, and the BF16 rounding made the forward
+//  pass depart from the exact transpose of the adjoint by 2e-5.)
 
 
 // FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
@@ -227,10 +261,11 @@ __device__ __forceinline__ PairGeo pair_geo(const KParams& p, double X0, double 
 }
 
 // FP64 reference terms of a pair written to the record rc (field f at
-// rc[f * stride]): 2R and |R|^2, |R| for transmitter and receiver, the fraction of
-// u_ref = (tau_ref - t0) fs minus 1/2 (so that rounding u - 1/2 to the
-// nearest integer gives floor(u)) and the carrier phase fc tau_ref mod 1
-// (cycles).
+// rc[f * stride]): 2R and |R|^2, |R| for transmitter and receiver, twice the
+// fraction of u_ref = (tau_ref - t0) fs minus 1/2 (so that rounding
+// 2(u - floor u_ref) - 1/2 to the nearest integer gives the half-sample index
+// floor(2(u - floor u_ref))) and the carrier phase 2 pi fc tau_ref reduced to
+// [-pi, pi) (radians).
 // Returns the raw sample index of Farrow position 0, tap 0: floor(u_ref) - U - 3.
 // LT0, LR0 >= 0: leg lengths at x0 in water metres (seabed refraction) that
 // replace |R_T|, |R_R| in tau_ref; the differential fields stay the straight ones.
@@ -280,8 +315,9 @@ __device__ __forceinline__ int pair_record(const KParams& p, PairGeo G, float* r
     rc[F_RZ * stride] = (float)(2.0 * G.Rz);
     rc[F_NR2 * stride] = (float)nR2;
     rc[F_NR * stride] = (float)nR;
-    rc[F_UF * stride] = (float)(u - iref - 0.5);
-    rc[F_PH * stride] = (float)(ph - floor(ph));
+    rc[F_UF * stride] = (float)(2.0 * (u - iref) - 0.5);
+    const double phf = ph - floor(ph);   // [0, 1) cycles -> [-pi, pi) rad
+    rc[F_PH * stride] = (float)(2.0 * M_PI * (phf < 0.5 ? phf : phf - 1.0));
     return (int)iref - p.U - 3;
 }
 
@@ -556,13 +592,15 @@ struct Layout {
 // bytes (slot_bytes: of 128; a Farrow row is 48 bytes; 32-float records),
 // so the 16-byte descriptor loads and stores are aligned.
 static_assert((NRS * PAIRS * NREC * 4) % 16 == 0 && (NRS * PAIRS * NREC_REFR * 4) % 16 == 0 &&
-                  (TAPS * NP * 4) % 16 == 0 && (NCW * 4 * 8) % 16 == 0,
+                  (NH * TAPS * NP * 4) % 16 == 0 && (NCW * 4 * 8) % 16 == 0 && (NH * ROW32) % 16 == 0 &&
+                  (NH * ROW16) % 16 == 0,
               "shared-memory parts must keep 16-byte alignment");
-inline size_t smem_bytes(int slot_bytes, int npos_pad, int nrec = NREC) {
-    return (size_t)NSEG * PAIRS * slot_bytes            // echo segments
-           + (size_t)NBUF * GROUP * npos_pad * EROW     // Farrow rows
-           + (size_t)NRS * PAIRS * nrec * 4             // records
-           + (size_t)TAPS * NP * 4                      // coefficients
+// row_bytes: ROW32 or ROW16 (row_bytes_of)
+inline size_t smem_bytes(int slot_bytes, int npos_pad, int nrec, int row_bytes) {
+    return (size_t)NSEG * PAIRS * slot_bytes                   // echo segments
+           + (size_t)NBUF * GROUP * npos_pad * NH * row_bytes  // Farrow rows
+           + (size_t)NRS * PAIRS * nrec * 4                    // records
+           + (size_t)NH * TAPS * NP * 4                        // coefficients
            + (size_t)NCW * 4 * 8                        // cross-warp reduction (gradient)
            + (size_t)NBUF * 16                          // group descriptors
            + (size_t)(NSEG + NRS + 2 * NBUF) * 8 + 16;  // mbarriers, abort flag
@@ -578,21 +616,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     using T = Tile<DIM3>;
     static_assert(!REFRACT || (MODE == MODE_FORWARD && !BEAM && !MOTION), "refraction: forward pass only");
     constexpr int KREC = REFRACT ? NREC_REFR : NREC;   // record fields
-    // FP16 Farrow rows for 16-bit echoes in the forward pass; FP32 rows with
-    // a BF16 tail for complex64 echoes in the forward pass
+    // FP16 Farrow rows for 16-bit echoes in the forward pass; otherwise rows
+    // of FP32 E0, E1 and BF16 E2, E3
     constexpr bool E16 = (MODE == MODE_FORWARD) && (sizeof(ET) == 4);
-    constexpr bool TAIL16 = false;
+    constexpr int ROWB = E16 ? ROW16 : ROW32;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
     unsigned char* seg = smem;                                           // [NSEG][PAIRS] echo segments
     unsigned char* ebuf = seg + (size_t)NSEG * PAIRS * p.slot_bytes;     // [NBUF][GROUP] Farrow rows
-    const int ebuf_pair = p.npos_pad * EROW;          // positions padded to whole expansion runs
+    const int ebuf_pair = p.npos_pad * NH * ROWB;     // positions padded to whole expansion runs
     float* rec = reinterpret_cast<float*>(ebuf + (size_t)NBUF * GROUP * ebuf_pair);   // [NRS][PAIRS][KREC]
-    float* coef_s = rec + NRS * PAIRS * KREC;                            // [TAPS][NP]
+    float* coef_s = rec + NRS * PAIRS * KREC;                            // [NH][TAPS][NP]
     // every part so far has a size that is a multiple of 16 bytes (see smem_bytes)
-    double* wred = reinterpret_cast<double*>(coef_s + TAPS * NP);         // [NCW][4]
+    double* wred = reinterpret_cast<double*>(coef_s + NH * TAPS * NP);    // [NCW][4]
     // [NBUF] group descriptors (written before, read after the efull barrier)
     int4* gdesc = reinterpret_cast<int4*>(wred + NCW * 4);
     uint64_t* full = reinterpret_cast<uint64_t*>(gdesc + NBUF);          // [NSEG] copies landed + records
@@ -647,7 +685,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (tid < TAPS * NP) coef_s[tid] = (&p.coef->c[0][0])[tid];
+    if (tid < NH * TAPS * NP) coef_s[tid] = (&p.coef->c[0][0][0])[tid];
     __syncthreads();
     const unsigned bmask = REFRACT ? s_bmask : 0u;
     const double Zr = REFRACT ? s_zr : Zc;
@@ -776,16 +814,22 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             return cnt;
         };
 
-        // expansion: lane = (run slot, power); 5 run slots of 6 powers, lanes 30, 31 idle
-        constexpr int RSLOTS = 32 / NP;
-        const int Ep = lane % NP, Erun = lane < RSLOTS * NP ? lane / NP : (1 << 30);
+        // expansion: lane = (run slot, half, power): 4 run slots x 2 halves x 4 powers
+        constexpr int LPR = NH * NP;          // lanes per run
+        constexpr int RSLOTS = 32 / LPR;
+        static_assert(RSLOTS * LPR == 32, "every lane expands");
+        const int Ep = lane % NP, Eh = (lane / NP) % NH, Erun = lane / LPR;
         const int runs_per_pair = (p.npos + RUN - 1) / RUN;
         float2 cc2[TAPS];
 #pragma unroll
-        for (int m = 0; m < TAPS; ++m) cc2[m] = make_float2(coef_s[m * NP + Ep], coef_s[m * NP + Ep]);
-        // byte offset of this lane's power in a row
-        const int e_off = E16 ? Ep * 4 : (TAIL16 && Ep >= 4 ? 32 + (Ep - 4) * 4 : Ep * 8);
-        const bool e_f32 = !TAIL16 || Ep < 4;
+        for (int m = 0; m < TAPS; ++m) {
+            const float c = coef_s[(Eh * TAPS + m) * NP + Ep];
+            cc2[m] = make_float2(c, c);
+        }
+        // byte offset of this lane's power in a row (FP32 rows: in the first
+        // 16-byte half for E0, E1, the second for E2, E3, swapped on rows with
+        // bit 2 of the row index set)
+        const int e_off = Ep * (E16 ? 4 : 8);
         int G = 0;   // groups emitted
         auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
             const int b = G % NBUF;
@@ -804,21 +848,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     float2 w[RUN + TAPS - 1];
 #pragma unroll
                     for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
-                    // (RUN = 9 would start the runs 12 r words apart modulo the 32 banks and
-                    // make these stores conflict-free, but the extra run per pair costs the
-                    // producer more than the conflicts: 3 % slower on the stripmap workload)
-                    unsigned char* dst = eb + j * ebuf_pair + pos0 * EROW + e_off;
+                    // row of half h at sample position n: NH n + h
+                    unsigned char* dst = eb + j * ebuf_pair + (NH * pos0 + Eh) * ROWB + e_off;
 #pragma unroll
                     for (int kq = 0; kq < RUN; ++kq) {
                         float2 e = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
-                        if (E16)
-                            *reinterpret_cast<__half2*>(dst + kq * EROW) = __floats2half2_rn(e.x, e.y);
-                        else if (e_f32)
-                            *reinterpret_cast<float2*>(dst + kq * EROW) = e;
-                        else
-                            *reinterpret_cast<__nv_bfloat162*>(dst + kq * EROW) = __floats2bfloat162_rn(e.x, e.y);
+                        unsigned char* d = dst + kq * (NH * ROWB);
+                        if (E16) {
+                            *reinterpret_cast<__half2*>(d) = __floats2half2_rn(e.x, e.y);
+                        } else {
+                            const int r = NH * (pos0 + kq) + Eh;
+                            *reinterpret_cast<float2*>(d + ((r & 4) ? (Ep < 2 ? 16 : -16) : 0)) = e;
+                        }
                     }
                 }
             }
@@ -1002,14 +1045,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                       const unsigned char* erow, const float4 q6, const float4 q7, const float4* hr, int rfl) {
         constexpr bool MASKED = decltype(masked)::value;
         const float tRx = q0.x, tRy = q0.y, tRz = q0.z, nR2 = q0.w;
-        const float nR = q1.x, ufc = q1.y, phr = q1.z;
+        const float nR = q1.x, ufc = q1.y, phr = q1.z;   // phr: reference carrier phase [rad]
         const float scl = E16 ? q1.w : 1.0f;
         const float tRv = DIM3 ? tRz : tRy;
         const float X = fixed_dot<DIM3>(tRx, tRy, dxv, dyv_c);
         const float2 Xv = make_float2(X, X), tRvv = make_float2(tRv, tRv);
         const float2 nR2v = make_float2(nR2, nR2), nRv = make_float2(nR, nR);
         const float2 ufv = make_float2(ufc, ufc), phv = make_float2(phr, phr);
-        const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC), twopi2 = make_float2(TWO_PI_F, TWO_PI_F);
+        const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC);
         // motion: (R_R + d).v / c = Km + d_var v_var / c
         float2 Kmv = make_float2(0.f, 0.f), vvv = make_float2(0.f, 0.f);
         if constexpr (MOTION) {
@@ -1065,14 +1108,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     }
                 }
             }
-            const float2 v = ffma2(D, p.fs_c2, ufv);                      // u - 1/2, rel. to floor(u_ref)
-            const float2 ph = ffma2(D, p.fc_c2, phv);                     // carrier phase [cycles]
-            // the nearest integer of u - 1/2 is floor(u): it sits in the mantissa of
-            // t = v + 1.5*2^23 (round to nearest), and g = v - that = frac(u) - 1/2;
-            // the phase is reduced to [-1/2, 1/2] cycles the same way
+            const float2 v = ffma2(D, p.hs_c2, ufv);                      // 2 (u - floor u_ref) - 1/2
+            float2 x2 = ffma2(D, p.wfc_c2, phv);                          // carrier phase [rad]
+            // the nearest integer of v = 2(u - floor u_ref) - 1/2 is the half-sample
+            // index floor(2(u - floor u_ref)): it sits in the mantissa of
+            // t = v + 1.5*2^23 (round to nearest), and g = v - that = frac(2u) - 1/2
             const float2 t = fadd2(v, magic2);
             const float2 g2 = fsub2(v, fsub2(t, magic2));
-            const float2 x2 = fmul2(fsub2(ph, fsub2(fadd2(ph, magic2), magic2)), twopi2);   // [-pi, pi]
+            if (!p.phase_direct) x2 = reduce_phase2(x2);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
             const int s = 2 * k + j;
@@ -1086,9 +1129,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 const float wz = DIM3 ? fmaf(0.5f, bRz, dvs) : 0.5f * bRz;
                 seen = ((tmask >> s) & 1u) && (!rmask_needed || beam_sees(p, wx, wy, wz, rot));
             }
-            const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - p.U)),
-                                     (unsigned)(p.npos - 1));
-            const float4* e = reinterpret_cast<const float4*>(erow + pos * EROW);
+            // half-sample row: floor(2(u - floor u_ref)) + 2U, clamped into the buffer
+            const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
+                                     (unsigned)(NH * p.npos - 1));
+            const unsigned char* e = erow + pos * ROWB;
             float sn, cs;
             sincos_sfu(j ? x2.y : x2.x, sn, cs);
             if (MASKED && !seen) {
@@ -1096,15 +1140,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 cs = 0.f;
             }
             if (E16) {
-                // packed FP16 Horner over E_5 .. E_0, scale and accumulate in FP32
-                const uint4 lo = *reinterpret_cast<const uint4*>(e);
-                const uint2 hi = *reinterpret_cast<const uint2*>(e + 1);
+                // packed FP16 Horner over E_3 .. E_0, scale and accumulate in FP32
+                const uint4 r = *reinterpret_cast<const uint4*>(e);
                 const __half2 g16 = __float2half2_rn(g);
-                __half2 h = __hfma2(h2_of_bits(hi.y), g16, h2_of_bits(hi.x));
-                h = __hfma2(h, g16, h2_of_bits(lo.w));
-                h = __hfma2(h, g16, h2_of_bits(lo.z));
-                h = __hfma2(h, g16, h2_of_bits(lo.y));
-                h = __hfma2(h, g16, h2_of_bits(lo.x));
+                __half2 h = __hfma2(h2_of_bits(r.w), g16, h2_of_bits(r.z));
+                h = __hfma2(h, g16, h2_of_bits(r.y));
+                h = __hfma2(h, g16, h2_of_bits(r.x));
                 const float2 hv = __half22float2(h);
                 const float vx = hv.x * scl, vy = hv.y * scl;
                 acc[s].x = fmaf(vx, cs, fmaf(-vy, sn, acc[s].x));
@@ -1112,41 +1153,29 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 continue;
             }
             const float2 gg2 = make_float2(g, g);
-            if constexpr (TAIL16) {
-                // E5, E4 from BF16 pairs, E3 .. E0 FP32; packed FP32 Horner
-                const float4 e01 = e[0], e23 = e[1];
-                const uint2 t45 = *reinterpret_cast<const uint2*>(e + 2);
-                float2 v = ffma2(bf2_to_f2(t45.y), gg2, bf2_to_f2(t45.x));
-                v = ffma2(v, gg2, make_float2(e23.z, e23.w));
-                v = ffma2(v, gg2, make_float2(e23.x, e23.y));
-                v = ffma2(v, gg2, make_float2(e01.z, e01.w));
-                v = ffma2(v, gg2, make_float2(e01.x, e01.y));
-                acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
-                acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
-                continue;
-            }
-            const float4 e01 = e[0], e23 = e[1], e45 = e[2];
+            const int sw = (pos & 4u) << 2;    // halves swapped on rows with bit 2 set
+            const float4 e01 = *reinterpret_cast<const float4*>(e + sw);
+            const float4 e23 = *reinterpret_cast<const float4*>(e + (16 ^ sw));
+            const float2 e0 = make_float2(e01.x, e01.y), e1 = make_float2(e01.z, e01.w);
+            const float2 e2 = make_float2(e23.x, e23.y), e3 = make_float2(e23.z, e23.w);
             if (MODE == MODE_FORWARD) {
-                // packed FP32 Horner over E_5 .. E_0
-                float2 v = ffma2(make_float2(e45.z, e45.w), gg2, make_float2(e45.x, e45.y));
-                v = ffma2(v, gg2, make_float2(e23.z, e23.w));
-                v = ffma2(v, gg2, make_float2(e23.x, e23.y));
-                v = ffma2(v, gg2, make_float2(e01.z, e01.w));
-                v = ffma2(v, gg2, make_float2(e01.x, e01.y));
+                // packed FP32 Horner over E_3 .. E_0
+                float2 v = ffma2(e3, gg2, e2);
+                v = ffma2(v, gg2, e1);
+                v = ffma2(v, gg2, e0);
                 acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
                 acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
             } else {
-                // value and derivative in g: b = s(g), d = s'(g)
-                float2 b = make_float2(e45.z, e45.w);
-                float2 d = make_float2(0.f, 0.f);
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e45.x, e45.y));
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.z, e23.w));
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e23.x, e23.y));
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.z, e01.w));
-                d = ffma2(d, gg2, b); b = ffma2(b, gg2, make_float2(e01.x, e01.y));
-                // a = fs s' + j 2 pi fc s ;  r = Re{ conj(G) a exp(j phase) }  (0 outside the beam)
-                const float ax = fmaf(p.fs_f, d.x, -p.wfc * b.y);
-                const float ay = fmaf(p.fs_f, d.y, p.wfc * b.x);
+                // value and derivative in g: b = s(g), d = ds/dg (ds/du = 2 d)
+                float2 b = e3;
+                float2 d = e3;
+                b = ffma2(b, gg2, e2);
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, e1);
+                d = ffma2(d, gg2, b); b = ffma2(b, gg2, e0);
+                // a = fs s' + j 2 pi fc s = 2 fs d + j 2 pi fc b ;  r = Re{ conj(G) a exp(j phase) }
+                // (0 outside the beam)
+                const float ax = fmaf(p.fs2_f, d.x, -p.wfc * b.y);
+                const float ay = fmaf(p.fs2_f, d.y, p.wfc * b.x);
                 const float Hx = fmaf(acc[s].x, cs, acc[s].y * sn);       // conj(G) exp(j phase)
                 const float Hy = fmaf(acc[s].x, sn, -acc[s].y * cs);
                 // dtau/d(dp) carries 1 / (1 + eps) with receiver motion
@@ -1317,8 +1346,10 @@ inline void tile_dims(int dim3, int& TXs, int& TYs, int& TZs) {
 }
 
 // Fills the launch description for grid g; min_ctas: aim for at least this
-// many CTAs by splitting the pings of each tile (0 = never split).
-int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, Setup& S, bool need_echo = true);
+// many CTAs by splitting the pings of each tile (0 = never split); mode: the
+// tdbp_kernel mode the launch runs (sets the Farrow row format).
+int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, Setup& S, bool need_echo = true,
+            int mode = MODE_FORWARD);
 
 template <int MODE>
 int launch_mode(const Setup& S, int echo_dtype, int dim3, cudaStream_t st);

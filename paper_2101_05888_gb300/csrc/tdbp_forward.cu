@@ -8,7 +8,7 @@
 namespace sas {
 namespace core {
 
-int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, Setup& S, bool need_echo) {
+int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, Setup& S, bool need_echo, int mode) {
     int TXs, TYs, TZs;
     tile_dims(dim3, TXs, TYs, TZs);
     const double dz = dim3 ? g.dz : 0.0;
@@ -32,9 +32,13 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
         return SAS_ERR_UNSUPPORTED;
     }
     const int npos_pad = (npos + RUN - 1) / RUN * RUN;
-    // expansion runs read up to RUN + 7 samples past a run start: pad the slot
-    const int slot_bytes = ((seglen + RUN + 8) * elem + 127) / 128 * 128;
-    const size_t smem = smem_bytes(slot_bytes, npos_pad, refract ? (int)NREC_REFR : (int)NREC);
+    // expansion runs of the padded positions read up to sample
+    // (offset < align) + npos_pad + 6 of the slot: pad the slot past the copied segment
+    const int slot_samples = std::max(seglen, npos_pad + align + 6);
+    const int slot_bytes = (slot_samples * elem + 127) / 128 * 128;
+    // FP16 rows for 16-bit echoes in the forward pass, else FP32 / BF16 rows
+    const int row_bytes = (mode == MODE_FORWARD && elem == 4) ? ROW16 : ROW32;
+    const size_t smem = smem_bytes(slot_bytes, npos_pad, refract ? (int)NREC_REFR : (int)NREC, row_bytes);
     if (smem > 227 * 1024) {
         set_error("shared memory need %zu exceeds the per-block limit", smem);
         return SAS_ERR_UNSUPPORTED;
@@ -54,11 +58,15 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     prm.tiles_z = (nz + TZs - 1) / TZs;
     prm.P = h->P; prm.C = h->C;
     prm.t0 = h->sig.t0; prm.fs = h->sig.fs; prm.fc = h->sig.fc; prm.inv_c = 1.0 / h->sig.c;
-    prm.fs_c = (float)(h->sig.fs / h->sig.c);
-    prm.fc_c = (float)(h->sig.fc / h->sig.c);
-    prm.fs_c2 = make_float2(prm.fs_c, prm.fs_c);
-    prm.fc_c2 = make_float2(prm.fc_c, prm.fc_c);
-    prm.fs_f = (float)h->sig.fs;
+    prm.hs_c = (float)(2.0 * h->sig.fs / h->sig.c);
+    prm.wfc_c = (float)(2.0 * M_PI * h->sig.fc / h->sig.c);
+    prm.hs_c2 = make_float2(prm.hs_c, prm.hs_c);
+    prm.wfc_c2 = make_float2(prm.wfc_c, prm.wfc_c);
+    // largest carrier phase a pixel can take from its reference: the reference in
+    // [-pi, pi) plus 2 pi fc times the differential delay, which the window bound
+    // U - 2 samples limits to (U - 2) / fs
+    prm.phase_direct = M_PI + 2.0 * M_PI * h->sig.fc * (U - 2) / h->sig.fs <= PHASE_DIRECT_MAX;
+    prm.fs2_f = (float)(2.0 * h->sig.fs);
     prm.wfc = (float)(2.0 * M_PI * h->sig.fc);
     prm.grad_scale = (float)(-2.0 / h->sig.c);
     prm.U = U; prm.npos = npos; prm.npos_pad = npos_pad; prm.seglen = seglen; prm.seg_align = align; prm.slot_bytes = slot_bytes;

@@ -50,7 +50,7 @@ int launch_offset_grad(sas_geometry_t h, const sas_grid& g, const float2* grad_i
                        cudaStream_t st) {
     const int dim3 = g.nz > 1;
     core::Setup S;
-    int rc = core::prepare(h, g, dim3, 2LL * sm_count(), S);
+    int rc = core::prepare(h, g, dim3, 2LL * sm_count(), S, true, core::MODE_OFFSET_GRAD);
     if (rc != SAS_OK) return rc;
     const long long ntiles = (long long)S.prm.tiles_x * S.prm.tiles_y * S.prm.tiles_z;
     const size_t need = (size_t)ntiles * h->P * 3 * sizeof(double);

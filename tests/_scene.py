@@ -44,3 +44,13 @@ def image_at(img, idx):
     """Values of a [nz][ny][nx] image (numpy) at indices idx [n,3] = (ix, iy, iz)."""
     idx = np.asarray(idx)
     return img[idx[:, 2], idx[:, 1], idx[:, 0]]
+
+
+def in_band(echo, nu_b=0.25):
+    """The part of echo rows (last axis) inside |nu| <= nu_b cycles/sample:
+    FFT, zero the rest, inverse FFT (complex128)."""
+    E = np.fft.fft(np.asarray(echo, dtype=np.complex128), axis=-1)
+    nu = np.fft.fftfreq(E.shape[-1])
+    E[..., np.abs(nu) > nu_b] = 0.0
+    return np.fft.ifft(E, axis=-1)
+

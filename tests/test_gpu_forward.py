@@ -43,18 +43,32 @@ def test_geometry_positions_match_oracle():
     geom.close()
 
 
-@pytest.mark.parametrize("beta,bound", [(4.0, 3e-5), (6.0, 6e-5)])
+@pytest.mark.parametrize("beta,bound", [(4.0, 4.3e-4), (6.0, 4.4e-4)])
 def test_interpolator_farrow_form_matches_definition(beta, bound):
-    """The degree-5 Farrow form (Chebyshev interpolation at 6 nodes) against
-    the definition; bound = the FP64 interpolation error of that construction
-    (2.5e-5 at beta 4, 4.8e-5 at beta 6) plus FP32 rounding."""
-    f = np.random.default_rng(1).random(4000).astype(np.float32)
+    """The Farrow form (a cubic on each half of the sample interval, Chebyshev
+    interpolation at 4 nodes per half) against the definition; bound = the
+    weight error of that construction with FP32 coefficients (4.18e-4 at
+    beta 4, 4.26e-4 at beta 6) plus FP32 rounding.  On echoes sampled at twice
+    their band (|nu| <= 1/4, the workloads' band) the interpolated value is
+    within 5e-5 rms of the definition's: the weight error is concentrated
+    where such signals have no energy."""
+    rng = np.random.default_rng(1)
+    f = rng.random(4000).astype(np.float32)
     taps = torch.empty((4000, 8), dtype=torch.float32, device="cuda")
     err = torch.zeros(1, dtype=torch.float64, device="cuda")
     sas.sas_interp_eval(sas.kaiser(beta), torch.from_numpy(f).cuda(), 4000, taps, err)
     ref = np.stack([oracle.kaiser_sinc_weights(float(x), 8, beta) for x in f])
-    assert np.abs(taps.cpu().numpy() - ref).max() < bound
+    got = taps.cpu().numpy().astype(np.float64)
+    assert np.abs(got - ref).max() < bound
     assert float(err.item()) < bound
+    row = synth.bandlimited_noise((1, 8192), synth.NU_BAND, 1.0, 5)[0]
+    i0 = rng.integers(8, 8192 - 8, 4000)
+    win = np.stack([row[i - 3:i + 5] for i in i0])
+    s_ref, s_got = (ref * win).sum(1), (got * win).sum(1)
+    band_err = np.linalg.norm(s_got - s_ref) / np.linalg.norm(s_ref)
+    print("Farrow form, beta %g: max weight error %.3g, band-limited value error %.3g rms" % (
+        beta, np.abs(got - ref).max(), band_err))
+    assert band_err < 5e-5
 
 
 def test_small_2d_full_image():

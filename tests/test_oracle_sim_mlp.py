@@ -108,3 +108,18 @@ def test_fir_mse_against_monte_carlo():
         mc = np.mean(np.abs(est - xf) ** 2)
         an = mlp.fir_mse(h, f, nu_b)
         assert abs(mc - an) <= 0.1 * an + 1e-9
+
+
+def test_interp_taps_prior_plus_network():
+    """With a zero network the learned interpolator's taps are its prior, the
+    normalised Kaiser-sinc (unit sum at every fraction); without a prior they
+    are the network's output alone."""
+    import oracle
+    f = np.linspace(0.0, 0.999, 37)
+    zero = np.zeros(mlp.N_PARAMS)
+    t = mlp.interp_taps(zero, f, 4.0)
+    assert np.allclose(t.sum(axis=1), 1.0, atol=1e-13)
+    assert np.allclose(t[5], oracle.kaiser_sinc_weights(f[5], 8, 4.0), atol=1e-15)
+    theta = np.random.default_rng(3).normal(0.0, 0.1, mlp.N_PARAMS)
+    assert np.allclose(mlp.interp_taps(theta, f, -1.0), mlp.forward(theta, f)[0])
+    assert np.allclose(mlp.interp_taps(theta, f, 6.0) - mlp.interp_taps(zero, f, 6.0), mlp.forward(theta, f)[0])
