@@ -84,7 +84,8 @@ int encode_echo_map(CUtensorMap* map, const void* base, int elem_bytes, int Ns, 
 // with R_i the attitude rotation of Eq. 2 (attitude_rotation).
 __global__ void geometry_kernel(int P, int C, const double* __restrict__ pos, const double* __restrict__ att,
                                 const double* __restrict__ lever, const double* __restrict__ off,
-                                double* __restrict__ tx, double* __restrict__ rx, float* __restrict__ rotc) {
+                                double* __restrict__ tx, double* __restrict__ rx, float* __restrict__ rotc,
+                                float2* __restrict__ txs, float2* __restrict__ rxs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
     double R[9];
@@ -104,12 +105,14 @@ __global__ void geometry_kernel(int P, int C, const double* __restrict__ pos, co
         o[0] = b0 + R[0] * l[0] + R[1] * l[1] + R[2] * l[2];
         o[1] = b1 + R[3] * l[0] + R[4] * l[1] + R[5] * l[2];
         o[2] = b2 + R[6] * l[0] + R[7] * l[1] + R[8] * l[2];
+        float2* os = (c < 0) ? txs + 3 * (size_t)i : rxs + 3 * ((size_t)i * C + c);
+        for (int k = 0; k < 3; ++k) os[k] = df_split(o[k]);
     }
 }
 
 static int run_geometry(sas_geometry_t h, cudaStream_t st) {
     geometry_kernel<<<(h->P + 127) / 128, 128, 0, st>>>(h->P, h->C, h->d_pos, h->d_att, h->d_lever, h->d_off,
-                                                        h->d_tx, h->d_rx, h->d_rotc);
+                                                        h->d_tx, h->d_rx, h->d_rotc, h->d_txs, h->d_rxs);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }
@@ -390,6 +393,8 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     const size_t o_tx = o;  o = align256(o + P * 3 * 8);
     const size_t o_rx = o;  o = align256(o + P * C * 3 * 8);
     const size_t o_rc = o;  o = align256(o + P * 6 * 4);
+    const size_t o_txs = o; o = align256(o + P * 3 * 8);
+    const size_t o_rxs = o; o = align256(o + P * C * 3 * 8);
     const size_t o_vl = o;  o = align256(o + P * 3 * 8);
     const size_t o_st = o;  o = align256(o + 16);
     const size_t o_cu = o;  o = align256(o + 4 * 8);
@@ -408,6 +413,8 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     h->d_tx = (double*)(b + o_tx);
     h->d_rx = (double*)(b + o_rx);
     h->d_rotc = (float*)(b + o_rc);
+    h->d_txs = (float2*)(b + o_txs);
+    h->d_rxs = (float2*)(b + o_rxs);
     h->d_vel = (double*)(b + o_vl);
     h->d_status = (uint32_t*)(b + o_st);
     h->d_cull = (unsigned long long*)(b + o_cu);

@@ -171,6 +171,45 @@ __device__ __forceinline__ float opaque(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi) / 2, about
+// 48 significant bits, on the FP32 pipe (the FP64 pipe of this GPU is slow
+// and its long latency chains stalled the per-pair reference terms).  Sums
+// use the two-sum of Knuth, products the exact FMA residual (Dekker's
+// product with a fused multiply-add); every operation is written with explicit
+// roundings so that no contraction or reassociation changes it.
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl df_fast(float a, float b) {   // |a| >= |b| (or a = 0)
+    const float s = __fadd_rn(a, b);
+    return dfl{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bb = __fsub_rn(s, x.hi);
+    const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    return df_fast(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return dfl{-x.hi, -x.lo}; }
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+    return df_fast(p, e);
+}
+// square root of a > 0: the FP32 root refined by one Newton step on the residual
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+    const float r = __fsqrt_rn(a.hi);
+    const float e = __fadd_rn(fmaf(-r, r, a.hi), a.lo);   // a - r^2 (exact FMA residual of the high part)
+    return df_fast(r, __fmul_rn(e, __fdiv_rn(0.5f, r)));
+}
+__device__ __forceinline__ float df_float(dfl x) { return __fadd_rn(x.hi, x.lo); }
+// the double-float nearest a double (host and device)
+__host__ __device__ inline float2 df_split(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
 // elementwise max / min of pairs (two scalar operations)
 __device__ __forceinline__ float2 fmax2(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 __device__ __forceinline__ float2 fmin2(float2 a, float2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
@@ -197,6 +236,8 @@ struct sas_geometry_s {
     double* d_off;     // [P][3]
     double* d_tx;      // [P][3]
     double* d_rx;      // [P][C][3]
+    float2* d_txs;     // [P][3] the same as double-floats (hi, lo)
+    float2* d_rxs;     // [P][C][3]
     float* d_rotc;     // [P][6]: columns 0 and 1 of the attitude matrix (beam tests)
     double* d_vel;     // [P][3]: receiver velocity during reception (valid if has_vel)
     int has_vel;       // 0: stop-and-hop

@@ -81,9 +81,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
         const long long qs = q0 + (long long)k * PAIRS;
         __syncthreads();   // previous stage's records no longer in use
         if (warp == 0 && qs + lane < q1) {
-            const int i = (int)((qs + lane) / p.C);
-            base_s[lane] = pair_record(p, pair_geo(p, X0, Y0, Z0, qs + lane, i), rec + lane, PAIRS,
-                                       p.vel ? p.vel + 3 * (size_t)i : nullptr);
+            const int i = (int)((unsigned)(qs + lane) / (unsigned)p.C);
+            // the forward pass's reference terms: double-float for stop-and-hop, FP64 with motion
+            if (p.vel) {
+                base_s[lane] = pair_record(p, pair_geo(p, X0, Y0, Z0, qs + lane, i), rec + lane, PAIRS,
+                                           p.vel + 3 * (size_t)i);
+            } else {
+                const float2 a = df_split(X0), b = df_split(Y0), c = df_split(Z0);
+                const dfl X0d[3] = {dfl{a.x, a.y}, dfl{b.x, b.y}, dfl{c.x, c.y}};
+                base_s[lane] = pair_record_df(p, pair_geo_df(p, X0d, (int)(qs + lane), i), rec + lane, PAIRS);
+            }
         }
         __syncthreads();
         float r[F_NT + 1];

