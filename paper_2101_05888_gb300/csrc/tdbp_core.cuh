@@ -237,19 +237,19 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
 // Farrow rows, one per half-sample position r = 2 n + h (sample position n
 // of the tile's window, half h), in a group buffer [GROUP][npos_pad * NH]:
 //  * ROW32 (complex64 echoes, and every echo in the gradient pass): E0..E3
-//    as FP32 pairs in two 16-byte halves, (E0, E1) and (E2, E3), read by two
-//    16-byte loads; on rows with bit 2 of r set the halves trade places.  A
-//    16-byte load is served a quarter-warp (a 4 x 2 pixel block) per
-//    wavefront, and the rows one quarter-warp reads span fewer than 8 half
-//    samples: with the swap, rows r and r + 4 put a given half in different
-//    bank groups, so each half-load meets no bank conflict.
+//    as FP32 pairs in two planes of 16-byte rows, (E0, E1) and (E2, E3), read
+//    by two 16-byte loads.  A 16-byte load is served a quarter-warp (a 4 x 2
+//    pixel block) per wavefront, and the rows one quarter-warp reads span fewer
+//    than 8 half samples, so they fall in distinct bank groups of a plane.
 //  * ROW16 (16-bit echoes, forward pass): E0..E3 as FP16 pairs, 16 bytes, one
 //    16-byte load.
 //  (Measured alternatives: one degree-5 polynomial per sample interval in
 //  48-byte FP32 rows reads 1.5x the bytes per update and bound the kernel at
 //  the shared-memory data pipe; 24-byte rows with E2, E3 in BF16 read by three
 //  8-byte loads were 2.5 % slower, and the BF16 rounding made the forward
-//  pass depart from the exact transpose of the adjoint by 2e-5.)
+//  pass depart from the exact transpose of the adjoint by 2e-5; one 32-byte
+//  row per position with its halves swapped every fourth row spent five
+//  integer operations a pixel on the addresses.)
 
 
 // FP64 vectors from the pair's sensors to the tile centre (X0, Y0, Z0):
@@ -909,10 +909,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             const float c = coef_s[(Eh * TAPS + m) * NP + Ep];
             cc2[m] = make_float2(c, c);
         }
-        // byte offset of this lane's power in a row (FP32 rows: in the first
-        // 16-byte half for E0, E1, the second for E2, E3, swapped on rows with
-        // bit 2 of the row index set)
-        const int e_off = Ep * (E16 ? 4 : 8);
+        // byte offset of this lane's power: FP16 rows hold E0..E3 in 16 bytes;
+        // FP32 rows are split in two planes of 16-byte rows, (E0, E1) then (E2, E3)
+        const int e_off = E16 ? Ep * 4 : ((Ep >> 1) * (p.npos_pad * NH * (ROW32 / 2)) + (Ep & 1) * 8);
+        const int e_rstride = E16 ? ROWB : ROW32 / 2;   // bytes from one row to the next in this lane's plane
         int G = 0;   // groups emitted
         auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
             const int b = G % NBUF;
@@ -932,19 +932,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
 #pragma unroll
                     for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
                     // row of half h at sample position n: NH n + h
-                    unsigned char* dst = eb + j * ebuf_pair + (NH * pos0 + Eh) * ROWB + e_off;
+                    unsigned char* dst = eb + j * ebuf_pair + (NH * pos0 + Eh) * e_rstride + e_off;
 #pragma unroll
                     for (int kq = 0; kq < RUN; ++kq) {
                         float2 e = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
-                        unsigned char* d = dst + kq * (NH * ROWB);
-                        if (E16) {
+                        unsigned char* d = dst + kq * (NH * (E16 ? ROWB : ROW32 / 2));
+                        if (E16)
                             *reinterpret_cast<__half2*>(d) = __floats2half2_rn(e.x, e.y);
-                        } else {
-                            const int r = NH * (pos0 + kq) + Eh;
-                            *reinterpret_cast<float2*>(d + ((r & 4) ? (Ep < 2 ? 16 : -16) : 0)) = e;
-                        }
+                        else
+                            *reinterpret_cast<float2*>(d) = e;
                     }
                 }
             }
@@ -1136,6 +1134,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         const float2 nR2v = make_float2(nR2, nR2), nRv = make_float2(nR, nR);
         const float2 ufv = make_float2(ufc, ufc), phv = make_float2(phr, phr);
         const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC);
+        const unsigned char* erow_b = erow + p.npos_pad * NH * (ROW32 / 2);   // second plane (FP32 rows)
         // motion: (R_R + d).v / c = Km + d_var v_var / c
         float2 Kmv = make_float2(0.f, 0.f), vvv = make_float2(0.f, 0.f);
         if constexpr (MOTION) {
@@ -1215,7 +1214,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             // half-sample row: floor(2(u - floor u_ref)) + 2U, clamped into the buffer
             const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
                                      (unsigned)(NH * p.npos - 1));
-            const unsigned char* e = erow + pos * ROWB;
+            const unsigned char* e = erow + pos * ROWB;   // FP16 rows
             float sn, cs;
             sincos_sfu(j ? x2.y : x2.x, sn, cs);
             if (MASKED && !seen) {
@@ -1236,9 +1235,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 continue;
             }
             const float2 gg2 = make_float2(g, g);
-            const int sw = (pos & 4u) << 2;    // halves swapped on rows with bit 2 set
-            const float4 e01 = *reinterpret_cast<const float4*>(e + sw);
-            const float4 e23 = *reinterpret_cast<const float4*>(e + (16 ^ sw));
+            // (E0, E1) from the first plane, (E2, E3) from the second
+            const float4 e01 = *reinterpret_cast<const float4*>(erow + pos * (ROW32 / 2));
+            const float4 e23 = *reinterpret_cast<const float4*>(erow_b + pos * (ROW32 / 2));
             const float2 e0 = make_float2(e01.x, e01.y), e1 = make_float2(e01.z, e01.w);
             const float2 e2 = make_float2(e23.x, e23.y), e3 = make_float2(e23.z, e23.w);
             if (MODE == MODE_FORWARD) {
