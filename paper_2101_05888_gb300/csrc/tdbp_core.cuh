@@ -653,6 +653,11 @@ static_assert((NRS * PAIRS * NREC * 4) % 16 == 0 && (NRS * PAIRS * NREC_REFR * 4
                   (NH * ROW16) % 16 == 0,
               "shared-memory parts must keep 16-byte alignment");
 // row_bytes: ROW32 or ROW16 (row_bytes_of)
+// positions per pair of the Farrow ring in the fixed-layout kernels (a
+// multiple of RUN; tiles of 1.5 cm pixels at 40 kHz need 57)
+constexpr int NPOS_FIXED = 60;
+static_assert(NPOS_FIXED % RUN == 0, "whole expansion runs");
+
 inline size_t smem_bytes(int slot_bytes, int npos_pad, int nrec, int row_bytes) {
     return (size_t)NSEG * PAIRS * slot_bytes                   // echo segments
            + (size_t)NBUF * GROUP * npos_pad * NH * row_bytes  // Farrow rows
@@ -668,7 +673,10 @@ inline size_t smem_bytes(int slot_bytes, int npos_pad, int nrec, int row_bytes) 
 // in tiles on a beam edge); without it every candidate pair is computed.
 // MOTION: the receivers move during reception (per-ping velocity).
 // REFRACT: seabed refraction (forward pass, without BEAM and MOTION).
-template <typename ET, bool DIM3, int MODE, bool BEAM, bool MOTION, bool REFRACT = false>
+// FIXED: the Farrow ring has NPOS_FIXED positions per pair (p.npos_pad ==
+// NPOS_FIXED), so the second FP32 plane sits at a constant offset from the
+// first and a consumer addresses both with one computed address.
+template <typename ET, bool DIM3, int MODE, bool BEAM, bool MOTION, bool REFRACT = false, bool FIXED = false>
 __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant__ CUtensorMap tmap, const KParams p) {
     using T = Tile<DIM3>;
     static_assert(!REFRACT || (MODE == MODE_FORWARD && !BEAM && !MOTION), "refraction: forward pass only");
@@ -683,7 +691,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
 
     unsigned char* seg = smem;                                           // [NSEG][PAIRS] echo segments
     unsigned char* ebuf = seg + (size_t)NSEG * PAIRS * p.slot_bytes;     // [NBUF][GROUP] Farrow rows
-    const int ebuf_pair = p.npos_pad * NH * ROWB;     // positions padded to whole expansion runs
+    const int npos_pad = FIXED ? NPOS_FIXED : p.npos_pad;
+    const int ebuf_pair = npos_pad * NH * ROWB;       // positions padded to whole expansion runs
     float* rec = reinterpret_cast<float*>(ebuf + (size_t)NBUF * GROUP * ebuf_pair);   // [NRS][PAIRS][KREC]
     float* coef_s = rec + NRS * PAIRS * KREC;                            // [NH][TAPS][NP]
     // every part so far has a size that is a multiple of 16 bytes (see smem_bytes)
@@ -911,7 +920,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         }
         // byte offset of this lane's power: FP16 rows hold E0..E3 in 16 bytes;
         // FP32 rows are split in two planes of 16-byte rows, (E0, E1) then (E2, E3)
-        const int e_off = E16 ? Ep * 4 : ((Ep >> 1) * (p.npos_pad * NH * (ROW32 / 2)) + (Ep & 1) * 8);
+        const int e_off = E16 ? Ep * 4 : ((Ep >> 1) * (npos_pad * NH * (ROW32 / 2)) + (Ep & 1) * 8);
         const int e_rstride = E16 ? ROWB : ROW32 / 2;   // bytes from one row to the next in this lane's plane
         int G = 0;   // groups emitted
         auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
@@ -1134,7 +1143,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         const float2 nR2v = make_float2(nR2, nR2), nRv = make_float2(nR, nR);
         const float2 ufv = make_float2(ufc, ufc), phv = make_float2(phr, phr);
         const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC);
-        const unsigned char* erow_b = erow + p.npos_pad * NH * (ROW32 / 2);   // second plane (FP32 rows)
+        const unsigned char* erow_b = erow + npos_pad * NH * (ROW32 / 2);     // second plane (FP32 rows)
         // motion: (R_R + d).v / c = Km + d_var v_var / c
         float2 Kmv = make_float2(0.f, 0.f), vvv = make_float2(0.f, 0.f);
         if constexpr (MOTION) {

@@ -31,7 +31,9 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
         set_error("pixel spacing too coarse: a tile's delay span needs %d samples (max 256)", seglen);
         return SAS_ERR_UNSUPPORTED;
     }
-    const int npos_pad = (npos + RUN - 1) / RUN * RUN;
+    int npos_pad = (npos + RUN - 1) / RUN * RUN;
+    // spans that fit take the fixed ring layout (see tdbp_kernel's FIXED)
+    if (!refract && npos_pad <= NPOS_FIXED) npos_pad = NPOS_FIXED;
     // expansion runs of the padded positions read up to sample
     // (offset < align) + npos_pad + 6 of the slot: pad the slot past the copied segment
     const int slot_samples = std::max(seglen, npos_pad + align + 6);
@@ -139,6 +141,8 @@ static int launch_one(const Setup& S, cudaStream_t st) {
         set_error("the offset gradient is not available with the refraction model");
         return SAS_ERR_UNSUPPORTED;
     }
+    if (!S.prm.refract && !S.prm.beam && !mv && S.prm.npos_pad == NPOS_FIXED)
+        kern = tdbp_kernel<ET, DIM3, MODE, false, false, false, true>;
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());

@@ -11,6 +11,7 @@ static int launch_one_grad(const Setup& S, cudaStream_t st) {
     const bool mv = S.prm.vel != nullptr;
     auto kern = S.prm.beam ? (mv ? tdbp_kernel<ET, DIM3, MODE, true, true> : tdbp_kernel<ET, DIM3, MODE, true, false>)
                            : (mv ? tdbp_kernel<ET, DIM3, MODE, false, true> : tdbp_kernel<ET, DIM3, MODE, false, false>);
+    if (!S.prm.beam && !mv && S.prm.npos_pad == NPOS_FIXED) kern = tdbp_kernel<ET, DIM3, MODE, false, false, false, true>;
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());
