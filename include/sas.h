@@ -256,9 +256,17 @@ int sas_sharpness_static(const void* d_image, int64_t n, double* d_out3, void* d
  * d_taps (device FP32 [n][taps]) exactly as the backprojection kernels apply
  * them, and writes to *d_max_err (device FP64, may be NULL) the largest
  * deviation of that form from the interpolator's definition over a fine
- * fraction grid. */
+ * fraction grid.  The kernels apply each tap's weight as a polynomial in the
+ * fraction on each half of the sample interval (a Farrow form, Sec. II-A's
+ * interpolation evaluated without a per-update tap table): a cubic for
+ * complex64 echoes, in the gradient pass and in the adjoint, and a quadratic
+ * for 16-bit echoes in the forward pass.  sas_interp_eval evaluates the cubic
+ * form; sas_interp_eval_form the one of the given degree (3 or 2; any other
+ * value is SAS_ERR_ARG). */
 int sas_interp_eval(const sas_interp* interp, const float* d_f, int64_t n, float* d_taps,
                     double* d_max_err, void* cuda_stream);
+int sas_interp_eval_form(const sas_interp* interp, int degree, const float* d_f, int64_t n, float* d_taps,
+                         double* d_max_err, void* cuda_stream);
 
 /* Echo simulator (Eq. 1 for point scatterers, spreading loss omitted),
  * complex baseband after matched filtering, using the handle's current sensor

@@ -43,7 +43,7 @@ ENTRY_POINTS = [
     "sas_geometry_positions", "sas_geometry_destroy", "sas_echo_upload", "sas_echo_download",
     "sas_backproject_2d", "sas_backproject_3d", "sas_backproject_adjoint", "sas_sharpness",
     "sas_sharpness_static", "sas_simulate_points",
-    "sas_interp_eval", "sas_mlp_make_windows", "sas_mlp_workspace_bytes", "sas_mlp_loss_grad",
+    "sas_interp_eval", "sas_interp_eval_form", "sas_mlp_make_windows", "sas_mlp_workspace_bytes", "sas_mlp_loss_grad",
     "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_cull_stats",
     "sas_matched_filter", "sas_whiten", "sas_tvg", "sas_drc",
     "sas_debug_starve_copies",
@@ -123,6 +123,7 @@ def lib():
                 "sas_sharpness_static": ([V, I64, V, V, V], I),
                 "sas_simulate_points": ([V, V, I64, D, D, ctypes.c_int32, V, V], I),
                 "sas_interp_eval": ([P(sas_interp), V, I64, V, V, V], I),
+                "sas_interp_eval_form": ([P(sas_interp), I, V, I64, V, V, V], I),
                 "sas_mlp_make_windows": ([V, ctypes.c_int32, ctypes.c_int32, V, V, V, I64, D, D, V, V, V], I),
                 "sas_mlp_workspace_bytes": ([I64], I64),
                 "sas_mlp_loss_grad": ([V, V, V, V, I64, V, V, V, V], I),
@@ -262,6 +263,11 @@ def sas_simulate_points(h, d_scat, n: int, bandwidth: float, pulse_T: float, hal
 def sas_interp_eval(interp: sas_interp, d_f, n: int, d_taps, d_max_err=None, stream=None):
     _check(lib().sas_interp_eval(ctypes.byref(interp), _ptr(d_f), n, _ptr(d_taps), _ptr(d_max_err),
                                  _stream(stream)))
+
+
+def sas_interp_eval_form(interp: sas_interp, degree: int, d_f, n: int, d_taps, d_max_err=None, stream=None):
+    _check(lib().sas_interp_eval_form(ctypes.byref(interp), degree, _ptr(d_f), n, _ptr(d_taps), _ptr(d_max_err),
+                                      _stream(stream)))
 
 
 def sas_mlp_make_windows(d_echo, rows: int, n_samples: int, d_frac, d_row, d_pos, n: int, target_beta: float,

@@ -228,59 +228,45 @@ __device__ void interp_weights(int kind, double beta, int table_n, const float* 
     }
 }
 
-// Monomial coefficients in g of tap t's weight on half h (FP64, not rounded).
-__device__ void fit_half_tap(const double (*node_w)[TAPS], int t, double mono_g[NP]) {
-    // Chebyshev coefficients a_k = (2/NP) sum_j y_j T_k(x_j), a_0 halved
-    double a[NP];
-    for (int k = 0; k < NP; ++k) {
+// Monomial coefficients in g of tap t's weight on half h, from its values at
+// the N Chebyshev nodes of the half (FP64, not rounded).
+template <int N>
+__device__ void fit_half_tap(const double (*node_w)[TAPS], int t, double mono_g[N]) {
+    // Chebyshev coefficients a_k = (2/N) sum_j y_j T_k(x_j), a_0 halved
+    double a[N];
+    for (int k = 0; k < N; ++k) {
         double s = 0.0;
-        for (int j = 0; j < NP; ++j) s += node_w[j][t] * cos(M_PI * k * (j + 0.5) / NP);
-        a[k] = 2.0 * s / NP;
+        for (int j = 0; j < N; ++j) s += node_w[j][t] * cos(M_PI * k * (j + 0.5) / N);
+        a[k] = 2.0 * s / N;
     }
     a[0] *= 0.5;
     // monomials in x: T_0 = 1, T_1 = x, T_{k+1} = 2x T_k - T_{k-1}
-    double tkm1[NP] = {0}, tk[NP] = {0}, mono[NP] = {0};
+    double tkm1[N] = {0}, tk[N] = {0}, mono[N] = {0};
     tkm1[0] = 1.0;
     tk[1] = 1.0;
     mono[0] += a[0];
-    for (int p = 0; p < NP; ++p) mono[p] += a[1] * tk[p];
-    for (int k = 2; k < NP; ++k) {
-        double tn[NP] = {0};
-        for (int p = 0; p < NP; ++p) tn[p] = (p > 0 ? 2.0 * tk[p - 1] : 0.0) - tkm1[p];
-        for (int p = 0; p < NP; ++p) {
+    for (int p = 0; p < N; ++p) mono[p] += a[1] * tk[p];
+    for (int k = 2; k < N; ++k) {
+        double tn[N] = {0};
+        for (int p = 0; p < N; ++p) tn[p] = (p > 0 ? 2.0 * tk[p - 1] : 0.0) - tkm1[p];
+        for (int p = 0; p < N; ++p) {
             tkm1[p] = tk[p];
             tk[p] = tn[p];
             mono[p] += a[k] * tn[p];
         }
     }
     double s = 1.0;
-    for (int p = 0; p < NP; ++p) {  // x = 2 g
+    for (int p = 0; p < N; ++p) {  // x = 2 g
         mono_g[p] = mono[p] * s;
         s *= 2.0;
     }
 }
 
-__global__ void fit_interp_kernel(int kind, double beta, int table_n, const float* table, FarrowCoef* out,
-                                  double* err) {
-    __shared__ double node_w[NH][NP][TAPS];
-    __shared__ double emax[128];
-    const int t = threadIdx.x;
-    if (t < NH * NP) {
-        const int h = t / NP, j = t % NP;
-        const double x = cos(M_PI * (j + 0.5) / NP);
-        interp_weights(kind, beta, table_n, table, 0.5 * (h + 0.5 + 0.5 * x), node_w[h][j]);
-    }
-    __syncthreads();
-    if (t < NH * TAPS) {
-        const int h = t / TAPS, m = t % TAPS;
-        double mono[NP];
-        fit_half_tap(node_w[h], m, mono);
-        for (int p = 0; p < NP; ++p) out->c[h][m][p] = (float)mono[p];
-    }
-    __syncthreads();
-    // deviation of the (float-rounded) polynomials from the definition
+// max over f in [0, 1] (2049 points, strided by thread) of |Farrow form - definition|
+template <int N>
+__device__ double form_error(int kind, double beta, int table_n, const float* table, const float (*c)[TAPS][N]) {
     double e = 0.0;
-    for (int q = t; q <= 2048; q += blockDim.x) {
+    for (int q = threadIdx.x; q <= 2048; q += blockDim.x) {
         const double f = q / 2048.0;
         double w[TAPS];
         interp_weights(kind, beta, table_n, table, f, w);
@@ -288,16 +274,48 @@ __global__ void fit_interp_kernel(int kind, double beta, int table_n, const floa
         const double g = 2.0 * f - h - 0.5;
         for (int m = 0; m < TAPS; ++m) {
             double v = 0.0;
-            for (int p = NP - 1; p >= 0; --p) v = v * g + (double)out->c[h][m][p];
+            for (int p = N - 1; p >= 0; --p) v = v * g + (double)c[h][m][p];
             e = fmax(e, fabs(v - w[m]));
         }
     }
-    emax[t] = e;
+    return e;
+}
+
+__global__ void fit_interp_kernel(int kind, double beta, int table_n, const float* table, FarrowCoef* out,
+                                  double* err) {
+    __shared__ double node_c[NH][NP][TAPS], node_q[NH][NQ][TAPS];
+    __shared__ double emax[2][128];
+    const int t = threadIdx.x;
+    if (t < NH * NP) {
+        const int h = t / NP, j = t % NP;
+        const double x = cos(M_PI * (j + 0.5) / NP);
+        interp_weights(kind, beta, table_n, table, 0.5 * (h + 0.5 + 0.5 * x), node_c[h][j]);
+    } else if (t < NH * NP + NH * NQ) {
+        const int h = (t - NH * NP) / NQ, j = (t - NH * NP) % NQ;
+        const double x = cos(M_PI * (j + 0.5) / NQ);
+        interp_weights(kind, beta, table_n, table, 0.5 * (h + 0.5 + 0.5 * x), node_q[h][j]);
+    }
     __syncthreads();
-    if (t == 0) {
+    if (t < NH * TAPS) {
+        const int h = t / TAPS, m = t % TAPS;
+        double mono[NP];
+        fit_half_tap<NP>(node_c[h], m, mono);
+        for (int p = 0; p < NP; ++p) out->c[h][m][p] = (float)mono[p];
+    } else if (t < 2 * NH * TAPS) {
+        const int h = (t - NH * TAPS) / TAPS, m = (t - NH * TAPS) % TAPS;
+        double mono[NQ];
+        fit_half_tap<NQ>(node_q[h], m, mono);
+        for (int p = 0; p < NQ; ++p) out->q[h][m][p] = (float)mono[p];
+    }
+    __syncthreads();
+    // deviation of the (float-rounded) polynomials from the definition
+    emax[0][t] = form_error<NP>(kind, beta, table_n, table, out->c);
+    emax[1][t] = form_error<NQ>(kind, beta, table_n, table, out->q);
+    __syncthreads();
+    if (t < 2) {
         double m = 0.0;
-        for (int k = 0; k < blockDim.x; ++k) m = fmax(m, emax[k]);
-        if (err) *err = m;
+        for (int k = 0; k < blockDim.x; ++k) m = fmax(m, emax[t][k]);
+        if (err) err[t] = m;
     }
 }
 
@@ -329,16 +347,17 @@ int fit_interp(const sas_interp* it, FarrowCoef* d_coef, double* d_err, cudaStre
     return SAS_OK;
 }
 
-__global__ void interp_eval_kernel(const FarrowCoef* __restrict__ coef, const float* __restrict__ f, long long n,
+template <int N>
+__global__ void interp_eval_kernel(const float (*__restrict__ c)[TAPS][N], const float* __restrict__ f, long long n,
                                    float* __restrict__ taps) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    // the half of the interval (fractions outside [0, 1) extend the nearer half's cubic)
+    // the half of the interval (fractions outside [0, 1) extend the nearer half's polynomial)
     const int h = min(max((int)floorf(2.0f * f[i]), 0), NH - 1);
     const float g = fmaf(2.0f, f[i], -(float)h - 0.5f);
     for (int m = 0; m < TAPS; ++m) {
-        float v = coef->c[h][m][NP - 1];
-        for (int p = NP - 2; p >= 0; --p) v = fmaf(v, g, coef->c[h][m][p]);
+        float v = c[h][m][N - 1];
+        for (int p = N - 2; p >= 0; --p) v = fmaf(v, g, c[h][m][p]);
         taps[i * TAPS + m] = v;
     }
 }
@@ -399,7 +418,7 @@ extern "C" int sas_geometry_create(const sas_nav* nav, const sas_signal* sig, vo
     const size_t o_st = o;  o = align256(o + 16);
     const size_t o_cu = o;  o = align256(o + 4 * 8);
     const size_t o_cf = o;  o = align256(o + sizeof(FarrowCoef));
-    const size_t o_fe = o;  o = align256(o + 8);
+    const size_t o_fe = o;  o = align256(o + 2 * 8);
     cudaError_t e = cudaMalloc(&h->slab, o);
     if (e != cudaSuccess) {
         delete h;
@@ -696,28 +715,39 @@ extern "C" int sas_backproject_adjoint(sas_geometry_t h, const sas_grid* g, cons
     return launch_adjoint(a);
 }
 
-extern "C" int sas_interp_eval(const sas_interp* it, const float* d_f, int64_t n, float* d_taps, double* d_max_err,
-                               void* stream) {
-    if (!it || (n > 0 && (!d_f || !d_taps)) || n < 0) {
-        set_error("sas_interp_eval: bad argument");
+extern "C" int sas_interp_eval_form(const sas_interp* it, int degree, const float* d_f, int64_t n, float* d_taps,
+                                    double* d_max_err, void* stream) {
+    if (!it || (n > 0 && (!d_f || !d_taps)) || n < 0 || (degree != NP - 1 && degree != NQ - 1)) {
+        set_error("sas_interp_eval_form: bad argument");
         return SAS_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    const size_t cf_bytes = (sizeof(FarrowCoef) + 255) / 256 * 256;
     FarrowCoef* d_coef = nullptr;
-    SAS_CUDA(cudaMallocAsync(&d_coef, 256 + 256, st));
-    double* d_err = (double*)((char*)d_coef + 256);
+    SAS_CUDA(cudaMallocAsync(&d_coef, cf_bytes + 16, st));
+    double* d_err = (double*)((char*)d_coef + cf_bytes);
     int rc = fit_interp(it, d_coef, d_err, st);
+    const bool cubic = degree == NP - 1;
     if (rc == SAS_OK && n > 0) {
-        interp_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_coef, d_f, n, d_taps);
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        if (cubic)
+            interp_eval_kernel<NP><<<nb, 256, 0, st>>>(d_coef->c, d_f, n, d_taps);
+        else
+            interp_eval_kernel<NQ><<<nb, 256, 0, st>>>(d_coef->q, d_f, n, d_taps);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_fail(e, "interp_eval_kernel");
     }
     if (rc == SAS_OK && d_max_err) {
-        cudaError_t e = cudaMemcpyAsync(d_max_err, d_err, 8, cudaMemcpyDeviceToDevice, st);
+        cudaError_t e = cudaMemcpyAsync(d_max_err, d_err + (cubic ? 0 : 1), 8, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "copy fit error");
     }
     cudaFreeAsync(d_coef, st);
     return rc;
+}
+
+extern "C" int sas_interp_eval(const sas_interp* it, const float* d_f, int64_t n, float* d_taps, double* d_max_err,
+                               void* stream) {
+    return sas_interp_eval_form(it, NP - 1, d_f, n, d_taps, d_max_err, stream);
 }
 
 extern "C" int sas_sync_status(sas_geometry_t h, void* stream) {

@@ -53,14 +53,16 @@ __device__ __forceinline__ void attitude_rotation(double roll, double pitch, dou
 constexpr int TAPS = 8;
 constexpr int NH = 2;            // sub-intervals (halves) of a sample interval
 constexpr int NP = 4;            // polynomial degree 3 on each
+constexpr int NQ = 3;            // degree 2 on each (16-bit echoes, forward pass)
 struct FarrowCoef {
-    float c[NH][TAPS][NP];
+    float c[NH][TAPS][NP];       // cubic form
+    float q[NH][TAPS][NQ];       // quadratic form of the same interpolator
 };
 
-// Fits the interpolator to Farrow form on the device (FP64 Chebyshev
-// interpolation at NP nodes of each half, converted to monomials in g).
-// d_coef: device FarrowCoef; d_err: optional device double, max |fit -
-// definition| over the weights.
+// Fits the interpolator to both Farrow forms on the device (FP64 Chebyshev
+// interpolation at NP, resp. NQ, nodes of each half, converted to monomials
+// in g).  d_coef: device FarrowCoef; d_err: optional device double[2], max
+// |fit - definition| over the weights of the cubic and of the quadratic form.
 int fit_interp(const sas_interp* interp, FarrowCoef* d_coef, double* d_err, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

@@ -64,7 +64,7 @@ constexpr int GROUP = 4;                // pairs per Farrow group
 constexpr int GPS = PAIRS / GROUP;      // groups per stage
 constexpr int PX = 8;                   // pixels per consumer thread
 constexpr int ROW32 = 32;               // bytes of an FP32 Farrow row: E0..E3 as FP32 pairs
-constexpr int ROW16 = 16;               // bytes of an FP16 Farrow row (16-bit echoes, forward pass)
+constexpr int ROW24 = 24;               // bytes of a quadratic FP32 Farrow row (16-bit echoes, forward pass)
 constexpr int RUN = 15;                 // sample positions per expansion run
 constexpr int BAR_CONS = 1;             // named barrier of the consumer warps
 
@@ -226,13 +226,6 @@ __device__ __forceinline__ float reduce_phase(float x) {
 }
 
 
-__device__ __forceinline__ __half2 h2_of_bits(uint32_t b) {
-    return *reinterpret_cast<__half2*>(&b);
-}
-// the two BF16 halves of a packed pair as FP32 (exact: BF16 is the top half of FP32)
-__device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
-    return make_float2(__uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
-}
 
 // Farrow rows, one per half-sample position r = 2 n + h (sample position n
 // of the tile's window, half h), in a group buffer [GROUP][npos_pad * NH]:
@@ -241,8 +234,13 @@ __device__ __forceinline__ float2 bf2_to_f2(uint32_t b) {
 //    by two 16-byte loads.  A 16-byte load is served a quarter-warp (a 4 x 2
 //    pixel block) per wavefront, and the rows one quarter-warp reads span fewer
 //    than 8 half samples, so they fall in distinct bank groups of a plane.
-//  * ROW16 (16-bit echoes, forward pass): E0..E3 as FP16 pairs, 16 bytes, one
-//    16-byte load.
+//  * ROW24 (16-bit echoes, forward pass): the quadratic form, E0..E2 as FP32
+//    pairs, (E0, E1) in a plane of 16-byte rows and E2 in a plane of 8-byte
+//    rows, read by a 16-byte and an 8-byte load.  The 16-bit echo's error
+//    budget admits the quadratic's interpolation error (7.5e-4 rms on echoes
+//    band-limited to a quarter of the sample rate, against 3.7e-5 for the
+//    cubic), and it saves a quarter of the expansion and a packed FMA a
+//    pixel.
 //  (Measured alternatives: one degree-5 polynomial per sample interval in
 //  48-byte FP32 rows reads 1.5x the bytes per update and bound the kernel at
 //  the shared-memory data pipe; 24-byte rows with E2, E3 in BF16 read by three
@@ -646,13 +644,14 @@ struct Layout {
 // Shared-memory layout (in this order): echo segments, Farrow rows, records,
 // coefficients, reduction scratch, group descriptors, mbarriers, abort flag.
 // Every part before the descriptors has a size that is a multiple of 16
-// bytes (slot_bytes: of 128; a Farrow row is 48 bytes; 32-float records),
+// bytes (slot_bytes: of 128; the Farrow rows of a sample position: 64 or 48
+// bytes; records of a multiple of 4 floats),
 // so the 16-byte descriptor loads and stores are aligned.
 static_assert((NRS * PAIRS * NREC * 4) % 16 == 0 && (NRS * PAIRS * NREC_REFR * 4) % 16 == 0 &&
                   (NH * TAPS * NP * 4) % 16 == 0 && (NCW * 4 * 8) % 16 == 0 && (NH * ROW32) % 16 == 0 &&
-                  (NH * ROW16) % 16 == 0,
+                  (NH * ROW24) % 16 == 0,
               "shared-memory parts must keep 16-byte alignment");
-// row_bytes: ROW32 or ROW16 (row_bytes_of)
+// row_bytes: ROW32 or ROW24
 // positions per pair of the Farrow ring in the fixed-layout kernels (a
 // multiple of RUN; tiles of 1.5 cm pixels at 40 kHz need 57)
 constexpr int NPOS_FIXED = 60;
@@ -684,7 +683,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // FP16 Farrow rows for 16-bit echoes in the forward pass; otherwise rows
     // of FP32 E0, E1 and BF16 E2, E3
     constexpr bool E16 = (MODE == MODE_FORWARD) && (sizeof(ET) == 4);
-    constexpr int ROWB = E16 ? ROW16 : ROW32;
+    constexpr int ROWB = E16 ? ROW24 : ROW32;
+    constexpr int NPK = E16 ? NQ : NP;                 // coefficients of a row (cubic or quadratic)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (tid < NH * TAPS * NP) coef_s[tid] = (&p.coef->c[0][0][0])[tid];
+    if (tid < NH * TAPS * NPK) coef_s[tid] = E16 ? (&p.coef->q[0][0][0])[tid] : (&p.coef->c[0][0][0])[tid];
     __syncthreads();
     const unsigned bmask = REFRACT ? s_bmask : 0u;
     const double Zr = REFRACT ? s_zr : Zc;
@@ -906,22 +906,27 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             return cnt;
         };
 
-        // expansion: lane = (run slot, half, power): 4 run slots x 2 halves x 4 powers
-        constexpr int LPR = NH * NP;          // lanes per run
+        // expansion.  Cubic rows: lane = (run slot, half, power), 4 run slots x
+        // 2 halves x 4 powers.  Quadratic rows (16-bit echoes): lane = (run slot,
+        // half), 16 run slots x 2 halves, each lane computing the three powers of
+        // its half, so that a 16-bit sample is converted by two lanes, not six.
+        constexpr int LPR = E16 ? NH : NH * NP;   // lanes per run
         constexpr int RSLOTS = 32 / LPR;
-        static_assert(RSLOTS * LPR == 32, "every lane expands");
-        const int Ep = lane % NP, Eh = (lane / NP) % NH, Erun = lane / LPR;
+        const int Ep = E16 ? 0 : lane % NP, Eh = (lane / (E16 ? 1 : NP)) % NH, Erun = lane / LPR;
         const int runs_per_pair = (p.npos + RUN - 1) / RUN;
-        float2 cc2[TAPS];
+        float2 cc2[E16 ? NQ : 1][TAPS];
 #pragma unroll
-        for (int m = 0; m < TAPS; ++m) {
-            const float c = coef_s[(Eh * TAPS + m) * NP + Ep];
-            cc2[m] = make_float2(c, c);
-        }
-        // byte offset of this lane's power: FP16 rows hold E0..E3 in 16 bytes;
-        // FP32 rows are split in two planes of 16-byte rows, (E0, E1) then (E2, E3)
-        const int e_off = E16 ? Ep * 4 : ((Ep >> 1) * (npos_pad * NH * (ROW32 / 2)) + (Ep & 1) * 8);
-        const int e_rstride = E16 ? ROWB : ROW32 / 2;   // bytes from one row to the next in this lane's plane
+        for (int q = 0; q < (E16 ? NQ : 1); ++q)
+#pragma unroll
+            for (int m = 0; m < TAPS; ++m) {
+                const float c = coef_s[(Eh * TAPS + m) * NPK + (E16 ? q : Ep)];
+                cc2[q][m] = make_float2(c, c);
+            }
+        // the first plane holds (E0, E1) in 16-byte rows, the second (E2, E3) in
+        // 16-byte rows (cubic) or E2 in 8-byte rows (quadratic); a cubic lane's
+        // byte offset of its power
+        const int plane1 = npos_pad * NH * 16;          // bytes of a pair's first plane
+        const int e_off = (Ep >> 1) * plane1 + (Ep & 1) * 8;
         int G = 0;   // groups emitted
         auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
             const int b = G % NBUF;
@@ -936,22 +941,34 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     const int pr = pr0 + j;
                     const unsigned char* slot = seg + ((size_t)ss * PAIRS + pr) * p.slot_bytes;
                     const int off = __float_as_int(rc[pr * KREC + F_OFF]) + pos0;
-                    const float sc = E16 ? 1.0f : rc[pr * KREC + F_SCALE];
+                    const float sc = rc[pr * KREC + F_SCALE];
                     float2 w[RUN + TAPS - 1];
 #pragma unroll
                     for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
                     // row of half h at sample position n: NH n + h
-                    unsigned char* dst = eb + j * ebuf_pair + (NH * pos0 + Eh) * e_rstride + e_off;
+                    unsigned char* dst = eb + j * ebuf_pair + (NH * pos0 + Eh) * 16 + e_off;
+                    if constexpr (E16) {
+                        unsigned char* dst2 = eb + j * ebuf_pair + plane1 + (NH * pos0 + Eh) * 8;
 #pragma unroll
-                    for (int kq = 0; kq < RUN; ++kq) {
-                        float2 e = make_float2(0.f, 0.f);
+                        for (int kq = 0; kq < RUN; ++kq) {
+                            float2 e0 = make_float2(0.f, 0.f), e1 = e0, e2 = e0;
 #pragma unroll
-                        for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[m], w[kq + m], e);
-                        unsigned char* d = dst + kq * (NH * (E16 ? ROWB : ROW32 / 2));
-                        if (E16)
-                            *reinterpret_cast<__half2*>(d) = __floats2half2_rn(e.x, e.y);
-                        else
-                            *reinterpret_cast<float2*>(d) = e;
+                            for (int m = 0; m < TAPS; ++m) {
+                                e0 = ffma2(cc2[0][m], w[kq + m], e0);
+                                e1 = ffma2(cc2[1][m], w[kq + m], e1);
+                                e2 = ffma2(cc2[NQ - 1][m], w[kq + m], e2);
+                            }
+                            *reinterpret_cast<float4*>(dst + kq * (NH * 16)) = make_float4(e0.x, e0.y, e1.x, e1.y);
+                            *reinterpret_cast<float2*>(dst2 + kq * (NH * 8)) = e2;
+                        }
+                    } else {
+#pragma unroll
+                        for (int kq = 0; kq < RUN; ++kq) {
+                            float2 e = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[0][m], w[kq + m], e);
+                            *reinterpret_cast<float2*>(dst + kq * (NH * 16)) = e;
+                        }
                     }
                 }
             }
@@ -1136,14 +1153,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         constexpr bool MASKED = decltype(masked)::value;
         const float tRx = q0.x, tRy = q0.y, tRz = q0.z, nR2 = q0.w;
         const float nR = q1.x, ufc = q1.y, phr = q1.z;   // phr: reference carrier phase [rad]
-        const float scl = E16 ? q1.w : 1.0f;
         const float tRv = DIM3 ? tRz : tRy;
         const float X = fixed_dot<DIM3>(tRx, tRy, dxv, dyv_c);
         const float2 Xv = make_float2(X, X), tRvv = make_float2(tRv, tRv);
         const float2 nR2v = make_float2(nR2, nR2), nRv = make_float2(nR, nR);
         const float2 ufv = make_float2(ufc, ufc), phv = make_float2(phr, phr);
         const float2 magic2 = make_float2(FLOOR_MAGIC, FLOOR_MAGIC);
-        const unsigned char* erow_b = erow + npos_pad * NH * (ROW32 / 2);     // second plane (FP32 rows)
+        const unsigned char* erow_b = erow + npos_pad * NH * 16;   // the pair's second plane
         // motion: (R_R + d).v / c = Km + d_var v_var / c
         float2 Kmv = make_float2(0.f, 0.f), vvv = make_float2(0.f, 0.f);
         if constexpr (MOTION) {
@@ -1223,30 +1239,26 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             // half-sample row: floor(2(u - floor u_ref)) + 2U, clamped into the buffer
             const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
                                      (unsigned)(NH * p.npos - 1));
-            const unsigned char* e = erow + pos * ROWB;   // FP16 rows
             float sn, cs;
             sincos_sfu(j ? x2.y : x2.x, sn, cs);
             if (MASKED && !seen) {
                 sn = 0.f;
                 cs = 0.f;
             }
+            const float2 gg2 = make_float2(g, g);
+            // (E0, E1) from the first plane
+            const float4 e01 = *reinterpret_cast<const float4*>(erow + pos * 16);
             if (E16) {
-                // packed FP16 Horner over E_3 .. E_0, scale and accumulate in FP32
-                const uint4 r = *reinterpret_cast<const uint4*>(e);
-                const __half2 g16 = __float2half2_rn(g);
-                __half2 h = __hfma2(h2_of_bits(r.w), g16, h2_of_bits(r.z));
-                h = __hfma2(h, g16, h2_of_bits(r.y));
-                h = __hfma2(h, g16, h2_of_bits(r.x));
-                const float2 hv = __half22float2(h);
-                const float vx = hv.x * scl, vy = hv.y * scl;
-                acc[s].x = fmaf(vx, cs, fmaf(-vy, sn, acc[s].x));
-                acc[s].y = fmaf(vx, sn, fmaf(vy, cs, acc[s].y));
+                // quadratic: E2 from the second plane; packed FP32 Horner over E_2 .. E_0
+                const float2 e2 = *reinterpret_cast<const float2*>(erow_b + pos * 8);
+                float2 v = ffma2(e2, gg2, make_float2(e01.z, e01.w));
+                v = ffma2(v, gg2, make_float2(e01.x, e01.y));
+                acc[s].x = fmaf(v.x, cs, fmaf(-v.y, sn, acc[s].x));
+                acc[s].y = fmaf(v.x, sn, fmaf(v.y, cs, acc[s].y));
                 continue;
             }
-            const float2 gg2 = make_float2(g, g);
-            // (E0, E1) from the first plane, (E2, E3) from the second
-            const float4 e01 = *reinterpret_cast<const float4*>(erow + pos * (ROW32 / 2));
-            const float4 e23 = *reinterpret_cast<const float4*>(erow_b + pos * (ROW32 / 2));
+            // cubic: (E2, E3) from the second plane
+            const float4 e23 = *reinterpret_cast<const float4*>(erow_b + pos * 16);
             const float2 e0 = make_float2(e01.x, e01.y), e1 = make_float2(e01.z, e01.w);
             const float2 e2 = make_float2(e23.x, e23.y), e3 = make_float2(e23.z, e23.w);
             if (MODE == MODE_FORWARD) {

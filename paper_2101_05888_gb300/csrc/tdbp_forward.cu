@@ -38,8 +38,8 @@ int prepare(sas_geometry_t h, const sas_grid& g, int dim3, long long min_ctas, S
     // (offset < align) + npos_pad + 6 of the slot: pad the slot past the copied segment
     const int slot_samples = std::max(seglen, npos_pad + align + 6);
     const int slot_bytes = (slot_samples * elem + 127) / 128 * 128;
-    // FP16 rows for 16-bit echoes in the forward pass, else FP32 / BF16 rows
-    const int row_bytes = (mode == MODE_FORWARD && elem == 4) ? ROW16 : ROW32;
+    // quadratic rows for 16-bit echoes in the forward pass, else cubic rows
+    const int row_bytes = (mode == MODE_FORWARD && elem == 4) ? ROW24 : ROW32;
     const size_t smem = smem_bytes(slot_bytes, npos_pad, refract ? (int)NREC_REFR : (int)NREC, row_bytes);
     if (smem > 227 * 1024) {
         set_error("shared memory need %zu exceeds the per-block limit", smem);

@@ -71,6 +71,38 @@ def test_interpolator_farrow_form_matches_definition(beta, bound):
     assert band_err < 5e-5
 
 
+@pytest.mark.parametrize("beta,bound", [(4.0, 4.9e-3), (6.0, 4.87e-3)])
+def test_interpolator_quadratic_form_matches_definition(beta, bound):
+    """The quadratic Farrow form the 16-bit forward pass applies (Chebyshev
+    interpolation at 3 nodes per half) against the definition; bound = the
+    weight error of that construction (4.895e-3 at beta 4, 4.862e-3 at beta
+    6, FP64 fit) plus FP32 rounding.  On echoes band-limited to |nu| <= 1/4 the
+    interpolated value is within 1e-3 rms of the definition's (7.5e-4 for this
+    construction): the 16-bit path's budget is 3e-3."""
+    rng = np.random.default_rng(2)
+    f = rng.random(4000).astype(np.float32)
+    taps = torch.empty((4000, 8), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sas.sas_interp_eval_form(sas.kaiser(beta), 2, torch.from_numpy(f).cuda(), 4000, taps, err)
+    ref = np.stack([oracle.kaiser_sinc_weights(float(x), 8, beta) for x in f])
+    got = taps.cpu().numpy().astype(np.float64)
+    assert np.abs(got - ref).max() < bound
+    assert float(err.item()) < bound
+    # the cubic form is the other degree, and only 2 and 3 exist
+    sas.sas_interp_eval_form(sas.kaiser(beta), 3, torch.from_numpy(f).cuda(), 4000, taps, err)
+    assert np.abs(taps.cpu().numpy().astype(np.float64) - ref).max() < 4.5e-4
+    with pytest.raises(sas.SasError):
+        sas.sas_interp_eval_form(sas.kaiser(beta), 4, torch.from_numpy(f).cuda(), 4000, taps, err)
+    row = synth.bandlimited_noise((1, 8192), synth.NU_BAND, 1.0, 6)[0]
+    i0 = rng.integers(8, 8192 - 8, 4000)
+    win = np.stack([row[i - 3:i + 5] for i in i0])
+    s_ref, s_got = (ref * win).sum(1), (got * win).sum(1)
+    band_err = np.linalg.norm(s_got - s_ref) / np.linalg.norm(s_ref)
+    print("quadratic Farrow form, beta %g: max weight error %.3g, band-limited value error %.3g rms" % (
+        beta, np.abs(got - ref).max(), band_err))
+    assert band_err < 1e-3
+
+
 def test_small_2d_full_image():
     """128 pings x 4 RX x 2048 samples, 256^2 pixels at 2 cm, 10 points at 20 dB."""
     w = synth.workload("small_2d")
@@ -169,7 +201,7 @@ def test_3d_small_volume():
 
 @pytest.mark.parametrize("store", [sas.SAS_ECHO_C32_F16, sas.SAS_ECHO_C32_BF16])
 def test_16bit_echo_storage(store):
-    """16-bit storage: the kernel (FP16 Farrow rows and Horner, FP32
+    """16-bit storage: the kernel (quadratic Farrow form, FP32 rows and
     accumulation) applied to the stored echo matches the oracle on that echo to
     1e-3, and the whole path is within 3e-3 of the FP64 oracle on the unrounded
     echo."""
@@ -188,7 +220,7 @@ def test_16bit_echo_storage(store):
     ref = oracle.backproject(tx, rx, oracle_signal(w), echo, 8, BETA, pix).reshape(img.shape)
     e_kernel, e_total = oracle.rel_l2(img, ref_q), oracle.rel_l2(img, ref)
     print("16-bit echo (%d): kernel arithmetic %.3g, total vs FP64 on the unrounded echo %.3g" % (store, e_kernel, e_total))
-    assert e_kernel < 1e-3      # FP16 Farrow rows and Horner
+    assert e_kernel < 1e-3      # the quadratic form's interpolation error
     assert e_total < 3e-3
     geom.close()
 
