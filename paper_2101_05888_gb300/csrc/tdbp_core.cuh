@@ -906,27 +906,30 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             return cnt;
         };
 
-        // expansion.  Cubic rows: lane = (run slot, half, power), 4 run slots x
-        // 2 halves x 4 powers.  Quadratic rows (16-bit echoes): lane = (run slot,
-        // half), 16 run slots x 2 halves, each lane computing the three powers of
-        // its half, so that a 16-bit sample is converted by two lanes, not six.
-        constexpr int LPR = E16 ? NH : NH * NP;   // lanes per run
-        constexpr int RSLOTS = 32 / LPR;
-        const int Ep = E16 ? 0 : lane % NP, Eh = (lane / (E16 ? 1 : NP)) % NH, Erun = lane / LPR;
+        // expansion: a lane computes the powers of one half of a run of RUN
+        // sample positions and writes them as whole rows of a plane.  Cubic rows:
+        // lane = (plane, run slot, half), 2 x 8 x 2, each lane computing the two
+        // powers of its plane, (E0, E1) or (E2, E3).  Quadratic rows (16-bit
+        // echoes): lane = (run slot, half), 16 x 2, each lane computing E0, E1, E2,
+        // so that a 16-bit sample is converted by two lanes.  A quarter-warp
+        // writes the four runs of one pair (when the span takes four runs): rows
+        // 30 apart, which fall in distinct bank groups.
+        constexpr int NPL = E16 ? NQ : 2;         // powers per lane
+        constexpr int RSLOTS = E16 ? 16 : 8;
+        const int Eh = lane & 1, Erun = (lane >> 1) & (RSLOTS - 1), Eq = E16 ? 0 : lane >> 4;
         const int runs_per_pair = (p.npos + RUN - 1) / RUN;
-        float2 cc2[E16 ? NQ : 1][TAPS];
+        float2 cc2[NPL][TAPS];
 #pragma unroll
-        for (int q = 0; q < (E16 ? NQ : 1); ++q)
+        for (int q = 0; q < NPL; ++q)
 #pragma unroll
             for (int m = 0; m < TAPS; ++m) {
-                const float c = coef_s[(Eh * TAPS + m) * NPK + (E16 ? q : Ep)];
+                const float c = coef_s[(Eh * TAPS + m) * NPK + 2 * Eq + q];
                 cc2[q][m] = make_float2(c, c);
             }
         // the first plane holds (E0, E1) in 16-byte rows, the second (E2, E3) in
-        // 16-byte rows (cubic) or E2 in 8-byte rows (quadratic); a cubic lane's
-        // byte offset of its power
+        // 16-byte rows (cubic) or E2 in 8-byte rows (quadratic)
         const int plane1 = npos_pad * NH * 16;          // bytes of a pair's first plane
-        const int e_off = (Ep >> 1) * plane1 + (Ep & 1) * 8;
+        const int e_off = Eq * plane1;
         int G = 0;   // groups emitted
         auto emit = [&](int rs, int pr0, int ng, int flags, int ss) {
             const int b = G % NBUF;
@@ -947,27 +950,30 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     for (int t = 0; t < RUN + TAPS - 1; ++t) w[t] = load_sample<ET>(slot, off + t, sc);
                     // row of half h at sample position n: NH n + h
                     unsigned char* dst = eb + j * ebuf_pair + (NH * pos0 + Eh) * 16 + e_off;
+                    float2 e[NPL];
                     if constexpr (E16) {
                         unsigned char* dst2 = eb + j * ebuf_pair + plane1 + (NH * pos0 + Eh) * 8;
 #pragma unroll
                         for (int kq = 0; kq < RUN; ++kq) {
-                            float2 e0 = make_float2(0.f, 0.f), e1 = e0, e2 = e0;
 #pragma unroll
-                            for (int m = 0; m < TAPS; ++m) {
-                                e0 = ffma2(cc2[0][m], w[kq + m], e0);
-                                e1 = ffma2(cc2[1][m], w[kq + m], e1);
-                                e2 = ffma2(cc2[NQ - 1][m], w[kq + m], e2);
-                            }
-                            *reinterpret_cast<float4*>(dst + kq * (NH * 16)) = make_float4(e0.x, e0.y, e1.x, e1.y);
-                            *reinterpret_cast<float2*>(dst2 + kq * (NH * 8)) = e2;
+                            for (int q = 0; q < NPL; ++q) e[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int m = 0; m < TAPS; ++m)
+#pragma unroll
+                                for (int q = 0; q < NPL; ++q) e[q] = ffma2(cc2[q][m], w[kq + m], e[q]);
+                            *reinterpret_cast<float4*>(dst + kq * (NH * 16)) = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
+                            *reinterpret_cast<float2*>(dst2 + kq * (NH * 8)) = e[NPL - 1];
                         }
                     } else {
 #pragma unroll
                         for (int kq = 0; kq < RUN; ++kq) {
-                            float2 e = make_float2(0.f, 0.f);
 #pragma unroll
-                            for (int m = 0; m < TAPS; ++m) e = ffma2(cc2[0][m], w[kq + m], e);
-                            *reinterpret_cast<float2*>(dst + kq * (NH * 16)) = e;
+                            for (int q = 0; q < NPL; ++q) e[q] = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int m = 0; m < TAPS; ++m)
+#pragma unroll
+                                for (int q = 0; q < NPL; ++q) e[q] = ffma2(cc2[q][m], w[kq + m], e[q]);
+                            *reinterpret_cast<float4*>(dst + kq * (NH * 16)) = make_float4(e[0].x, e[0].y, e[1].x, e[1].y);
                         }
                     }
                 }
