@@ -46,7 +46,8 @@ typedef enum {
     SAS_ERR_OOM = -3,         /* device allocation failed */
     SAS_ERR_TIMEOUT = -4,     /* a kernel's bounded wait ran out (results invalid) */
     SAS_ERR_UNSUPPORTED = -5, /* valid but unsupported configuration */
-    SAS_ERR_STATE = -6        /* call out of order (e.g. no echo uploaded) */
+    SAS_ERR_STATE = -6,       /* call out of order (e.g. no echo uploaded) */
+    SAS_ERR_CHECK = -7        /* checked build: a kernel's index check fired (results invalid) */
 } sas_status;
 
 /* Storage type of the echo inside the handle. */
@@ -325,12 +326,21 @@ int sas_interp_tabulate_mlp(const float* d_theta, int32_t table_n, double prior_
                             void* cuda_stream);
 
 /* Waits for the stream, then reports and clears the handle's device status:
- * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check.
+ * SAS_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check,
+ * else SAS_ERR_CHECK if (checked build only) a backprojection or adjoint
+ * kernel computed a Farrow-row index outside the window the host sized for
+ * its tile (the kernel clamped it: no access left the buffer, but the
+ * result is wrong).
  * After a timeout the results of the calls since the last check are invalid,
  * and a kernel may have left while one of its own bulk copies was still in
  * flight: treat the device state as suspect and recreate the handle (and
  * re-upload the echo) before relying on further results. */
 int sas_sync_status(sas_geometry_t h, void* cuda_stream);
+
+/* Build options of the loaded library: bit 0 set when it was compiled with
+ * SAS_CHECKED (the checked build: index checks in the kernels record what
+ * they find in the status word instead of only clamping; slower). */
+int sas_build_flags(void);
 
 /* ---- Data conditioning (Sec. II-E) and range compression ----------------
  * Rows are complex64 [rows][n], device, caller-owned; d_out may equal d_in.

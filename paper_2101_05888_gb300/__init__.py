@@ -18,7 +18,10 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsas.so")
+# SAS_CHECKED=1 in the environment loads the checked build (index checks in
+# the kernels report through sas_sync_status; build it with build(checked=True))
+CHECKED = os.environ.get("SAS_CHECKED") == "1"
+LIB_PATH = os.path.join(_HERE, "libsas_checked.so" if CHECKED else "libsas.so")
 
 SAS_OK = 0
 SAS_ERR_ARG = -1
@@ -27,6 +30,7 @@ SAS_ERR_OOM = -3
 SAS_ERR_TIMEOUT = -4
 SAS_ERR_UNSUPPORTED = -5
 SAS_ERR_STATE = -6
+SAS_ERR_CHECK = -7
 
 SAS_ECHO_C64 = 0
 SAS_ECHO_C32_F16 = 1
@@ -44,7 +48,7 @@ ENTRY_POINTS = [
     "sas_backproject_2d", "sas_backproject_3d", "sas_backproject_adjoint", "sas_sharpness",
     "sas_sharpness_static", "sas_simulate_points",
     "sas_interp_eval", "sas_interp_eval_form", "sas_mlp_make_windows", "sas_mlp_workspace_bytes", "sas_mlp_loss_grad",
-    "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_cull_stats",
+    "sas_mlp_adam", "sas_interp_tabulate_mlp", "sas_sync_status", "sas_build_flags", "sas_cull_stats",
     "sas_matched_filter", "sas_whiten", "sas_tvg", "sas_drc",
     "sas_debug_starve_copies",
     "sas_dpc_delays", "sas_dpc_footprints", "sas_dpc_model_delays", "sas_dpc_solve", "sas_debug_dpc_solve_chunk",
@@ -130,6 +134,7 @@ def lib():
                 "sas_mlp_adam": ([V, V, V, V, ctypes.c_int32, F, F, F, F, V], I),
                 "sas_interp_tabulate_mlp": ([V, ctypes.c_int32, D, V, V], I),
                 "sas_sync_status": ([V, V], I),
+                "sas_build_flags": ([], I),
                 "sas_cull_stats": ([V, ctypes.POINTER(ctypes.c_longlong), I, V], I),
                 "sas_matched_filter": ([V, I64, ctypes.c_int32, V, ctypes.c_int32, V, V], I),
                 "sas_whiten": ([V, V, I64, ctypes.c_int32, D, V, V], I),
@@ -296,6 +301,10 @@ def sas_interp_tabulate_mlp(d_theta, table_n: int, prior_beta: float, d_table_ou
 
 def sas_sync_status(h, stream=None):
     _check(lib().sas_sync_status(h, _stream(stream)))
+
+
+def sas_build_flags() -> int:
+    return int(lib().sas_build_flags())
 
 
 def sas_cull_stats(h, reset: int = 0, stream=None):

@@ -761,10 +761,22 @@ extern "C" int sas_sync_status(sas_geometry_t h, void* stream) {
     SAS_CUDA(cudaMemcpy(&v, h->d_status, 4, cudaMemcpyDeviceToHost));
     if (v) {
         SAS_CUDA(cudaMemset(h->d_status, 0, 4));
-        set_error("a kernel's bounded wait ran out (status 0x%x); its results are invalid", v);
-        return SAS_ERR_TIMEOUT;
+        if (v & DEV_TIMEOUT) {
+            set_error("a kernel's bounded wait ran out (status 0x%x); its results are invalid", v);
+            return SAS_ERR_TIMEOUT;
+        }
+        set_error("a kernel's Farrow-row index left the tile's window (status 0x%x); its results are invalid", v);
+        return SAS_ERR_CHECK;
     }
     return SAS_OK;
+}
+
+extern "C" int sas_build_flags(void) {
+#ifdef SAS_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 extern "C" int sas_cull_stats(sas_geometry_t h, long long* out, int reset, void* stream) {

@@ -24,7 +24,20 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 // Device status bits (handle status word).
-enum : uint32_t { DEV_TIMEOUT = 1u };
+enum : uint32_t { DEV_TIMEOUT = 1u, DEV_ROW_RANGE = 2u };
+
+// The Farrow row a kernel reads, clamped into [0, last].  The host sizes the
+// window so that the clamp never moves an index; in the checked build
+// (compiled with -DSAS_CHECKED) an index it had to move sets DEV_ROW_RANGE in
+// the handle's status word, which sas_sync_status reports.
+__device__ __forceinline__ unsigned row_index(unsigned raw, unsigned last, uint32_t* status) {
+#ifdef SAS_CHECKED
+    if (raw > last) atomicOr(status, DEV_ROW_RANGE);
+#else
+    (void)status;
+#endif
+    return min(raw, last);
+}
 
 // ---------------------------------------------------------------------------
 // Interpolator in Farrow form on half-sample sub-intervals: the sample

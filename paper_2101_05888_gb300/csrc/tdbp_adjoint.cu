@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                         // nearest integer of v = the half-sample index; g = frac(2u) - 1/2
                         const float t = __fadd_rn(v, FLOOR_MAGIC);
                         const float g = v - (t - FLOOR_MAGIC);
-                        const unsigned pos = min((unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
-                                                 (unsigned)(nrow - 1));
+                        const unsigned pos = row_index(
+                            (unsigned)(__float_as_int(t) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)), (unsigned)(nrow - 1),
+                            p.status);
                         if (!p.phase_direct) ph = reduce_phase(ph);
                         float sn, cs;
                         sincos_sfu(ph, sn, cs);

@@ -1243,8 +1243,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 seen = ((tmask >> s) & 1u) && (!rmask_needed || beam_sees(p, wx, wy, wz, rot));
             }
             // half-sample row: floor(2(u - floor u_ref)) + 2U, clamped into the buffer
-            const unsigned pos = min((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
-                                     (unsigned)(NH * p.npos - 1));
+            const unsigned pos = row_index((unsigned)(__float_as_int(tj) - (__float_as_int(FLOOR_MAGIC) - NH * p.U)),
+                                           (unsigned)(NH * p.npos - 1), p.status);
             float sn, cs;
             sincos_sfu(j ? x2.y : x2.x, sn, cs);
             if (MASKED && !seen) {
