@@ -143,6 +143,42 @@ def test_delays_match_oracle():
     geom.close()
 
 
+@pytest.mark.parametrize("store", [sas.SAS_ECHO_C32_F16, sas.SAS_ECHO_C32_BF16])
+def test_delays_16bit_storage_match_oracle(store):
+    """The delay estimator on 16-bit echo storage (four-byte staging copies
+    and the per-row scale in the kernel) against the oracle's estimator on the
+    stored echo as the library decodes it (the same precision budget as on
+    complex64: the kernel's arithmetic, not the rounding of the storage)."""
+    pl, vy, vz, meas = _scene(P=6, K=10)
+    echo, p = _speckle_echo(pl, vy, vz)
+    geom = sas.Geometry(p, pl.att, pl.tx_lever, pl.rx_lever, sas.make_signal(FC, FS, C_SOUND, 0.0, echo.shape[2]))
+    geom.upload_echo(echo.astype(np.complex64), store)
+    stored = geom.download_echo().cpu().numpy().astype(np.complex128)
+    assert oracle.rel_l2(stored, echo) < (2e-3 if store == sas.SAS_ECHO_C32_F16 else 8e-3)
+    K, W, L = 10, 128, 8
+    centres = np.round(np.linspace(0.025, 0.05, K) * FS).astype(np.int32)
+    M = meas.ping.size
+    co, fi, rh = (torch.empty(M, dtype=torch.float64, device="cuda") for _ in range(3))
+    sas.sas_dpc_delays(geom.h, 2, _dev(centres, torch.int32), K, W, L, co, fi, rh)
+    torch.cuda.synchronize()
+    co, fi, rh = co.cpu().numpy(), fi.cpu().numpy(), rh.cpu().numpy()
+    checked = 0
+    for m in range(M):
+        i, c, k = meas.ping[m], meas.chan[m], m % K
+        R = np.abs(mn.correlate(stored[i, c + 2], stored[i + 1, c], int(centres[k]), W, L))
+        top = np.sort(R)[-2:]
+        if top[1] < top[0] * (1 + 1e-4):
+            continue                                    # near-tie of the peak lag: FP32 and FP64 may differ
+        rc, rf, rr = mn.estimate_delay(stored[i, c + 2], stored[i + 1, c], int(centres[k]), W, L, FS, FC)
+        assert abs(co[m] - rc) < 1e-4 / FS
+        assert abs(((fi[m] - rf) * FC + 0.5) % 1.0 - 0.5) < 1e-4
+        assert abs(rh[m] - rr) < 1e-5
+        checked += 1
+    assert checked > 0.9 * M
+    assert np.median(rh) > 0.8
+    geom.close()
+
+
 @pytest.mark.parametrize("W,L,edge", [(100, 3, False), (128, 15, False), (37, 0, False), (64, 8, True),
                                       (130, 8, True)])
 def test_delay_shapes_match_oracle(W, L, edge):
