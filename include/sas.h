@@ -169,10 +169,12 @@ int sas_geometry_set_velocity(sas_geometry_t h, const double* vel, int on_device
  * interface to a pixel strictly below it (z > z_interface) crosses the
  * interface where its travel time is stationary (Fermat; Snell's law) and
  * counts L = |P - s| + (c / c_sediment) |x - P| water metres; every other leg
- * is straight.  Applies to the forward backprojection (2D and 3D) of every
- * later call; c_sediment <= 0 switches the model off (the default).  The
- * adjoint, the offset gradient and the simulator return SAS_ERR_UNSUPPORTED
- * while it is on, and so does a backprojection that also has a velocity
+ * is straight.  Applies to the forward backprojection (2D and 3D), the linear
+ * adjoint and the offset gradient (the derivative of a refracted leg's length
+ * with respect to its sensor is minus the unit vector towards the crossing
+ * point) of every later call; c_sediment <= 0 switches the model off (the
+ * default).  The simulator returns SAS_ERR_UNSUPPORTED while it is on, and so
+ * does any of those calls when the handle also has a velocity
  * (sas_geometry_set_velocity) or a beam (sas_geometry_set_beam).
  * Errors: SAS_ERR_ARG (null handle, non-finite arguments). */
 int sas_geometry_set_refraction(sas_geometry_t h, double z_interface, double c_sediment);

@@ -700,10 +700,6 @@ extern "C" int sas_backproject_adjoint(sas_geometry_t h, const sas_grid* g, cons
     }
     int rc = check_grid(g, g && g->nz > 1);
     if (rc != SAS_OK) return rc;
-    if (h->c_sed > 0.0) {
-        set_error("sas_backproject_adjoint: not available with the refraction model");
-        return SAS_ERR_UNSUPPORTED;
-    }
     cudaStream_t st = (cudaStream_t)stream;
     if (d_grad_offsets && h->echo_dtype < 0) {
         set_error("sas_backproject_adjoint: the offset gradient needs an uploaded echo");

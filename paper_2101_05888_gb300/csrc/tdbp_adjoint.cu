@@ -20,16 +20,26 @@ int launch_offset_grad(sas_geometry_t h, const sas_grid& g, const float2* grad_i
 
 namespace core {
 
-template <bool DIM3>
+// Four consecutive fields f0 .. f0 + 3 of pair pr of a field-major record.
+__device__ __forceinline__ float4 rec_block(const float* rec, int f0, int pr) {
+    return make_float4(rec[f0 * PAIRS + pr], rec[(f0 + 1) * PAIRS + pr], rec[(f0 + 2) * PAIRS + pr],
+                       rec[(f0 + 3) * PAIRS + pr]);
+}
+
+// REFRACT: the seabed refraction model (the forward kernel's per-leg
+// crossing records and per-pixel solves, evaluated the same way).
+template <bool DIM3, bool REFRACT>
 __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, const float2* __restrict__ img,
                                                               float2* __restrict__ eadj, int Ns) {
     using T = Tile<DIM3>;
+    constexpr int KREC = REFRACT ? NREC_REFR : NREC;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nrow = NH * p.npos;                                   // half-sample rows per pair
     float2* A = reinterpret_cast<float2*>(smem);                    // [GROUP][nrow][NP]
-    float* rec = reinterpret_cast<float*>(A + GROUP * nrow * NP);   // [NREC][PAIRS], field-major
-    float* coef_s = rec + NREC * PAIRS;                             // [NH][TAPS][NP]
+    float* rec = reinterpret_cast<float*>(A + GROUP * nrow * NP);   // [KREC][PAIRS], field-major
+    float* coef_s = rec + KREC * PAIRS;                             // [NH][TAPS][NP]
     int* base_s = reinterpret_cast<int*>(coef_s + NH * TAPS * NP);  // [PAIRS]
+    int* rfl_s = base_s + PAIRS;                                    // [PAIRS] refraction flags
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = p.tiles_x * p.tiles_y * p.tiles_z;
@@ -44,6 +54,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
     const int nq = (int)(q1 - q0);
     const double cx = tx0 + 0.5 * (T::TX - 1), cy = ty0 + 0.5 * (T::TY - 1), cz = tz0 + 0.5 * (T::TZ - 1);
     const double X0 = p.x0 + cx * p.dx, Y0 = p.y0 + cy * p.dy, Z0 = p.z0 + (DIM3 ? cz * p.dz : 0.0);
+    // seabed refraction: the layers below the interface and the reference depth
+    double Zr = Z0;
+    const unsigned bmask = REFRACT ? refr_tile_layers<DIM3>(p, tz0, Z0, Zr) : 0u;
+    const float r_br = REFRACT ? (float)(Zr - p.z_int) : 0.f, r_zoff = REFRACT ? (float)(Zr - Z0) : 0.f;
     const int alen = GROUP * nrow * NP;
     const int span = p.npos + TAPS - 1;            // output samples per pair segment
 
@@ -52,7 +66,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
 
     const bool consumer = warp > 0;
     const int ct = tid - 32;
-    float dxv = 0.f, dyv_c = 0.f, d2c = 0.f;
+    float dxv = 0.f, dyv_c = 0.f, d2c = 0.f, r_d2h = 0.f;
     float dvar[PX], dT[PX];
     float2 G[PX];
     if (consumer) {
@@ -65,6 +79,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
         const float dv0 = DIM3 ? (float)((tz0 + lz - cz) * p.dz) : dyv_c;
         const float dvstep = DIM3 ? (float)p.dz : (float)(4.0 * p.dy);
         d2c = fixed_d2<DIM3>(dxv, dyv_c);
+        r_d2h = REFRACT ? fixed_d2<true>(dxv, dyv_c) : 0.f;
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
             T::pixel(ct, s, lx, ly, lz);
@@ -82,8 +97,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
         __syncthreads();   // previous stage's records no longer in use
         if (warp == 0 && qs + lane < q1) {
             const int i = (int)((unsigned)(qs + lane) / (unsigned)p.C);
-            // the forward pass's reference terms: double-float for stop-and-hop, FP64 with motion
-            if (p.vel) {
+            // the forward pass's reference terms: double-float for stop-and-hop, FP64 with
+            // motion or refraction
+            if (REFRACT) {
+                const PairGeo G = pair_geo(p, X0, Y0, Z0, qs + lane, i);
+                double LT0, LR0;
+                rfl_s[lane] = refr_pair_blocks(p, G, p.tx[3 * (size_t)i + 2], p.rx[3 * (size_t)(qs + lane) + 2], bmask,
+                                               Zr, Z0, rec + lane, PAIRS, LT0, LR0);
+                base_s[lane] = pair_record(p, G, rec + lane, PAIRS, nullptr, LT0, LR0);
+            } else if (p.vel) {
                 base_s[lane] = pair_record(p, pair_geo(p, X0, Y0, Z0, qs + lane, i), rec + lane, PAIRS,
                                            p.vel + 3 * (size_t)i);
             } else {
@@ -110,12 +132,32 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                         const float nT2 = __shfl_sync(0xffffffffu, r[F_NT2], pr);
                         const float nT = __shfl_sync(0xffffffffu, r[F_NT], pr);
                         const float Ax = fixed_dot<DIM3>(tT0, tT1, dxv, dyv_c);
+                        // seabed refraction of the transmitter leg
+                        const bool trefr = REFRACT && (rfl_s[pr] & FL_T_REFR);
+                        float4 tr0 = make_float4(0.f, 0.f, 0.f, 0.f), tr1 = tr0, tr2 = tr0;
+                        float rhoT = 0.f, drhoT = 0.f;
+                        if (REFRACT && trefr) {
+                            tr0 = rec_block(rec, F_TREF, pr);
+                            tr1 = rec_block(rec, F_TREF + 4, pr);
+                            tr2 = rec_block(rec, F_TREF + 8, pr);
+                            if (DIM3) refr_rho(tr0, Ax + r_d2h, rhoT, drhoT);
+                        }
 #pragma unroll
                         for (int s = 0; s < PX; ++s) {
                             const float d2 = fmaf(dvar[s], dvar[s], d2c);
                             const float a = __fadd_rn(fmaf(DIM3 ? tT2 : tT1, dvar[s], d2), Ax);
                             const float sm = nT2 + a;
                             dT[s] = a * rcp_sfu(fmaf(sm, rsqrt_sfu(sm), nT));
+                            if (REFRACT && trefr) {
+                                if ((bmask >> s) & 1u) {
+                                    if (!DIM3) refr_rho(tr0, a, rhoT, drhoT);
+                                    const float db = DIM3 ? dvar[s] - r_zoff : 0.f, b = fmaxf(r_br + db, 1e-7f);
+                                    float uxi, ua;
+                                    dT[s] = refr_leg_diff(p, tr0, tr1, tr2, rhoT, drhoT, b, db, r_br, uxi, ua);
+                                } else {
+                                    dT[s] += tr2.w;
+                                }
+                            }
                         }
                     }
                     const float tRx = __shfl_sync(0xffffffffu, r[F_RX], pr);
@@ -139,6 +181,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                         bRz = rp[F_BRZ * PAIRS];
                     }
                     float2* Aj = A + j * nrow * NP;
+                    // seabed refraction of the receiver leg
+                    const bool rrefr = REFRACT && (rfl_s[pr] & FL_R_REFR);
+                    float4 rr0 = make_float4(0.f, 0.f, 0.f, 0.f), rr1 = rr0, rr2 = rr0;
+                    float rhoR = 0.f, drhoR = 0.f;
+                    if (REFRACT && rrefr) {
+                        rr0 = rec_block(rec, F_RREF, pr);
+                        rr1 = rec_block(rec, F_RREF + 4, pr);
+                        rr2 = rec_block(rec, F_RREF + 8, pr);
+                        if (DIM3) refr_rho(rr0, Ax + r_d2h, rhoR, drhoR);
+                    }
                     float rot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                     float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f;
                     if (p.beam) {
@@ -162,6 +214,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) adjoint_kernel(const KParams p, c
                         const float sm = nR2 + a;
                         const float rs = rsqrt_sfu(sm);
                         float D = fmaf(a, rcp_sfu(fmaf(sm, rs, nR)), dT[s]);
+                        if (REFRACT && rrefr) {
+                            if ((bmask >> s) & 1u) {
+                                float rho = rhoR, drho = drhoR;
+                                if (!DIM3) refr_rho(rr0, a, rho, drho);
+                                const float db = DIM3 ? dvar[s] - r_zoff : 0.f, b = fmaxf(r_br + db, 1e-7f);
+                                float uxi, ua;
+                                D = refr_leg_diff(p, rr0, rr1, rr2, rho, drho, b, db, r_br, uxi, ua) + dT[s];
+                            } else {
+                                D += rr2.w;
+                            }
+                        }
                         if (p.vel) {
                             const float eps = fmaf(dvar[s], vv, Km) * rs;         // u_R . v / c
                             D = D * fmaf(eps, eps - 1.f, 1.f);                   // / (1 + eps)
@@ -233,19 +296,18 @@ static int launch_linear_adjoint(sas_geometry_t h, const sas_grid& g, const floa
     core::Setup S;
     int rc = core::prepare(h, g, dim3, 2LL * sm_count(), S, false);
     if (rc != SAS_OK) return rc;
-    SAS_CUDA(cudaMemsetAsync(eadj, 0, sizeof(float2) * (size_t)h->P * h->C * h->Ns, st));
-    const size_t smem = sizeof(float2) * core::GROUP * NH * S.prm.npos * NP +
-                        sizeof(float) * core::NREC * core::PAIRS + sizeof(float) * NH * TAPS * NP +
-                        sizeof(int) * core::PAIRS;
-    if (dim3) {
-        auto k = core::adjoint_kernel<true>;
-        SAS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<S.blocks, core::NTHREADS, smem, st>>>(S.prm, img, eadj, h->Ns);
-    } else {
-        auto k = core::adjoint_kernel<false>;
-        SAS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k<<<S.blocks, core::NTHREADS, smem, st>>>(S.prm, img, eadj, h->Ns);
+    if (S.prm.refract && (S.prm.beam || S.prm.vel)) {
+        set_error("the refraction model does not combine with receiver motion or a beam");
+        return SAS_ERR_UNSUPPORTED;
     }
+    SAS_CUDA(cudaMemsetAsync(eadj, 0, sizeof(float2) * (size_t)h->P * h->C * h->Ns, st));
+    const int krec = S.prm.refract ? (int)core::NREC_REFR : (int)core::NREC;
+    const size_t smem = sizeof(float2) * core::GROUP * NH * S.prm.npos * NP + sizeof(float) * krec * core::PAIRS +
+                        sizeof(float) * NH * TAPS * NP + 2 * sizeof(int) * core::PAIRS;
+    auto k = dim3 ? (S.prm.refract ? core::adjoint_kernel<true, true> : core::adjoint_kernel<true, false>)
+                  : (S.prm.refract ? core::adjoint_kernel<false, true> : core::adjoint_kernel<false, false>);
+    SAS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k<<<S.blocks, core::NTHREADS, smem, st>>>(S.prm, img, eadj, h->Ns);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }

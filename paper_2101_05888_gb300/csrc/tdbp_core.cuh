@@ -496,11 +496,49 @@ __device__ __forceinline__ double refr_leg_ref(const KParams& p, double hx, doub
     return W + p.refr_n * V;
 }
 
+// The refraction blocks of a pair's record (producer, FP64): per leg with
+// the sensor above the interface and some pixel layer of the tile below it,
+// the crossing at x_r = (x0, y0, Zr) and the offsets K_r, K_s of the
+// refracted and the straight slots from the leg at x0 (refracted if x0 is
+// below the interface); zeros otherwise.  Fields at rc[(F_RREF + f) stride]
+// (receiver) and rc[(F_TREF + f) stride] (transmitter).  Returns the
+// FL_*_REFR flags and the legs' lengths at x0 in water metres (LT0, LR0).
+__device__ __forceinline__ int refr_pair_blocks(const KParams& p, const PairGeo& G, double tz, double rz,
+                                                unsigned bmask, double Zr, double Zc, float* rc, int stride,
+                                                double& LT0, double& LR0) {
+    int rfl = 0;
+#pragma unroll
+    for (int leg = 0; leg < 2; ++leg) {
+        const double hx = leg ? G.Tx : G.Rx, hy = leg ? G.Ty : G.Ry, hz = leg ? G.Tz : G.Rz;
+        const double sz = leg ? tz : rz;
+        const double straight = sqrt(hx * hx + hy * hy + hz * hz);
+        float* blk = rc + (leg ? F_TREF : F_RREF) * stride;
+        double L0 = straight;
+        if (bmask && sz < p.z_int) {
+            const double Lr = refr_leg_ref(p, hx, hy, p.z_int - sz, Zr - p.z_int, blk, stride);
+            if (Zc > p.z_int) L0 = Lr;
+            blk[RF_KR * stride] = (float)(Lr - L0);
+            blk[RF_KS * stride] = (float)(straight - L0);
+            rfl |= leg ? FL_T_REFR : FL_R_REFR;
+        } else {
+#pragma unroll
+            for (int f = 0; f < RF_N; ++f) blk[f * stride] = 0.f;
+        }
+        (leg ? LT0 : LR0) = L0;
+    }
+    return rfl;
+}
+
 // Refracted leg of one pixel minus the leg at x_r, plus K_r (consumers, FP32).
 // r0, r1, r2: the leg's record blocks; rho = rho_r + drho: the pixel's
-// horizontal distance; b = b_r + db: its depth below the interface.
+// horizontal distance; b = b_r + db: its depth below the interface.  Also
+// returns the unit vector from the sensor to the crossing point, as
+// (uxi, ua) = (xi, a) / |W| (horizontal run and height over the segment's
+// length): the derivative of the leg's length with respect to the sensor's
+// position is minus that vector (the length is stationary in the crossing).
 __device__ __forceinline__ float refr_leg_diff(const KParams& p, const float4 r0, const float4 r1, const float4 r2,
-                                               float rho, float drho, float b, float db, float br) {
+                                               float rho, float drho, float b, float db, float br, float& uxi,
+                                               float& ua) {
     const float a = r0.x;
     const bool fsed = p.refr_fast_sed;
     const float A = fsed ? b : a, B = fsed ? a : b;
@@ -532,7 +570,10 @@ __device__ __forceinline__ float refr_leg_diff(const KParams& p, const float4 r0
     }
     const float xi = r0.w + dxi, sg = r1.x + dsig;
     const float W2 = fmaf(xi, xi, a * a), V2 = fmaf(sg, sg, b * b);
-    const float Dw = fmaf(W2, rsqrt_sfu(W2), r1.y), Ds = fmaf(V2, rsqrt_sfu(V2), r1.z);   // |W| + |W_r|, |V| + |V_r|
+    const float iW = rsqrt_sfu(W2);
+    uxi = xi * iW;
+    ua = a * iW;
+    const float Dw = fmaf(W2, iW, r1.y), Ds = fmaf(V2, rsqrt_sfu(V2), r1.z);   // |W| + |W_r|, |V| + |V_r|
     const float Nw = dxi * fmaf(2.f, r0.w, dxi);                                         // |W|^2 - |W_r|^2
     const float Ns = p.refr_nf * fmaf(dsig, fmaf(2.f, r1.x, dsig), db * (br + b));        // n (|V|^2 - |V_r|^2)
     return fmaf(fmaf(Nw, Ds, Ns * Dw), rcp_sfu(Dw * Ds), r2.z);
@@ -545,7 +586,7 @@ __device__ __forceinline__ float refr_leg_diff(const KParams& p, const float4 r0
 // that step, and the length is stationary in it).
 __device__ __forceinline__ float2 refr_leg_diff2(const KParams& p, const float4 r0, const float4 r1,
                                                  const float4 r2, float2 rho, float2 drho, float2 b, float2 db,
-                                                 float br) {
+                                                 float br, float2& uxi, float2& ua) {
     const float a = r0.x;
     const bool fsed = p.refr_fast_sed;
     const float2 a2 = make_float2(a, a);
@@ -593,7 +634,10 @@ __device__ __forceinline__ float2 refr_leg_diff2(const KParams& p, const float4 
     }
     const float2 xi = fadd2(make_float2(r0.w, r0.w), dxi), sg = fadd2(make_float2(r1.x, r1.x), dsig);
     const float2 W2 = ffma2(xi, xi, make_float2(a * a, a * a)), V2 = ffma2(sg, sg, fmul2(b, b));
-    const float2 Dw = ffma2(W2, make_float2(rsqrt_sfu(W2.x), rsqrt_sfu(W2.y)), make_float2(r1.y, r1.y));
+    const float2 iW = make_float2(rsqrt_sfu(W2.x), rsqrt_sfu(W2.y));
+    uxi = fmul2(xi, iW);
+    ua = fmul2(make_float2(a, a), iW);
+    const float2 Dw = ffma2(W2, iW, make_float2(r1.y, r1.y));
     const float2 Ds = ffma2(V2, make_float2(rsqrt_sfu(V2.x), rsqrt_sfu(V2.y)), make_float2(r1.z, r1.z));
     const float2 two = make_float2(2.f, 2.f);
     const float2 Nw = fmul2(dxi, ffma2(two, make_float2(r0.w, r0.w), dxi));
@@ -620,6 +664,26 @@ __device__ __forceinline__ void refr_rho(const float4 r0, float qh, float& rho, 
 // the interface.
 __device__ __forceinline__ double layer_z(const KParams& p, int iz) {
     return __dadd_rn(p.z0, __dmul_rn((double)iz, p.dz));
+}
+
+// Seabed refraction, per tile (FP64): the slots (pixel layers in 3D; all of
+// them in 2D) strictly below the interface, as a bit mask, and the depth Zr
+// of the reference point x_r = (x0, y0, Zr): the centre Zc if it is below,
+// else the deepest layer.
+template <bool DIM3>
+__device__ __forceinline__ unsigned refr_tile_layers(const KParams& p, int tz0, double Zc, double& Zr) {
+    unsigned bm = 0u;
+    double zdeep = -1.0e300;
+#pragma unroll 1
+    for (int s = 0; s < PX; ++s) {
+        const double zs = DIM3 ? layer_z(p, tz0 + s) : p.z0;
+        if (zs > p.z_int) {
+            bm |= 1u << s;
+            zdeep = fmax(zdeep, zs);
+        }
+    }
+    Zr = Zc > p.z_int ? Zc : zdeep;
+    return bm;
 }
 
 // Pixel offsets d from the tile centre: the fixed part of |d|^2 and of 2R.d
@@ -678,7 +742,7 @@ inline size_t smem_bytes(int slot_bytes, int npos_pad, int nrec, int row_bytes) 
 template <typename ET, bool DIM3, int MODE, bool BEAM, bool MOTION, bool REFRACT = false, bool FIXED = false>
 __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant__ CUtensorMap tmap, const KParams p) {
     using T = Tile<DIM3>;
-    static_assert(!REFRACT || (MODE == MODE_FORWARD && !BEAM && !MOTION), "refraction: forward pass only");
+    static_assert(!REFRACT || (!BEAM && !MOTION), "refraction: without the beam or receiver motion");
     constexpr int KREC = REFRACT ? NREC_REFR : NREC;   // record fields
     // FP16 Farrow rows for 16-bit echoes in the forward pass; otherwise rows
     // of FP32 E0, E1 and BF16 E2, E3
@@ -727,18 +791,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     __shared__ unsigned s_bmask;
     __shared__ double s_zr;
     if (REFRACT && tid == 0) {
-        unsigned bm = 0u;
-        double zdeep = -1.0e300;
-#pragma unroll 1
-        for (int s = 0; s < PX; ++s) {
-            const double zs = DIM3 ? layer_z(p, tz0 + s) : p.z0;
-            if (zs > p.z_int) {
-                bm |= 1u << s;
-                zdeep = fmax(zdeep, zs);
-            }
-        }
-        s_bmask = bm;
-        s_zr = Zc > p.z_int ? Zc : zdeep;
+        double zr;
+        s_bmask = refr_tile_layers<DIM3>(p, tz0, Zc, zr);
+        s_zr = zr;
     }
 
     if (tid == 0) {
@@ -855,29 +910,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     float* rc = rec + (rs * PAIRS + slot) * KREC;
                     double LT0 = -1.0, LR0 = -1.0;
                     int rfl = 0;
-                    if constexpr (REFRACT) {
-                        // per leg: crossing at x_r, and the offsets K_r, K_s of the refracted and the
-                        // straight slots from the leg at x0 (refracted if x0 is below the interface)
-#pragma unroll
-                        for (int leg = 0; leg < 2; ++leg) {
-                            const double hx = leg ? Gv.Tx : Gv.Rx, hy = leg ? Gv.Ty : Gv.Ry, hz = leg ? Gv.Tz : Gv.Rz;
-                            const double sz = leg ? p.tx[3 * (size_t)iv + 2] : p.rx[3 * (size_t)qv + 2];
-                            const double straight = sqrt(hx * hx + hy * hy + hz * hz);
-                            float* blk = rc + (leg ? F_TREF : F_RREF);
-                            double L0 = straight;
-                            if (bmask && sz < p.z_int) {
-                                const double Lr = refr_leg_ref(p, hx, hy, p.z_int - sz, Zr - p.z_int, blk, 1);
-                                if (Zc > p.z_int) L0 = Lr;
-                                blk[RF_KR] = (float)(Lr - L0);
-                                blk[RF_KS] = (float)(straight - L0);
-                                rfl |= leg ? FL_T_REFR : FL_R_REFR;
-                            } else {
-#pragma unroll
-                                for (int f = 0; f < RF_N; ++f) blk[f] = 0.f;
-                            }
-                            (leg ? LT0 : LR0) = L0;
-                        }
-                    }
+                    if constexpr (REFRACT)
+                        rfl = refr_pair_blocks(p, Gv, p.tx[3 * (size_t)iv + 2], p.rx[3 * (size_t)qv + 2], bmask, Zr,
+                                               Zc, rc, 1, LT0, LR0);
                     int base;
                     if constexpr (DFREC)
                         base = pair_record_df(p, Gd, rc, 1);
@@ -1096,6 +1131,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // gradient: fold the transmitter term of the finished ping into the
     // per-thread sum, reduce over the CTA in FP64 and write the tile's partial
     float tT0 = 0.f, tT1 = 0.f, tT2 = 0.f, tNT2 = 0.f, tNT = 0.f;   // transmitter terms of the current ping
+    // gradient with seabed refraction: the current ping's transmitter-leg blocks
+    float4 ftr0 = make_float4(0.f, 0.f, 0.f, 0.f), ftr1 = ftr0, ftr2 = ftr0;
+    bool ftrefr = false;
     auto flush_ping = [&](int ping) {
         if (MODE != MODE_OFFSET_GRAD) return;
         const float tTv = DIM3 ? tT2 : tT1;
@@ -1103,17 +1141,35 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
         float hx = 0.5f * tT0 + dxv;
         float hy = DIM3 ? 0.5f * tT1 + dyv_c : 0.f;
         float hz = DIM3 ? 0.f : 0.5f * tT2;
+        // (3D: the column's horizontal distance from the transmitter, refracted legs)
+        float rhoT = 0.f, drhoT = 0.f;
+        if (REFRACT && ftrefr && DIM3) refr_rho(ftr0, X + r_d2h, rhoT, drhoT);
 #pragma unroll
         for (int s = 0; s < PX; ++s) {
             const float dvs = PXS(dvp, s);
             const float a = __fadd_rn(fmaf(tTv, dvs, PXS(d2p, s)), X);
             const float sm = tNT2 + a;
-            const float kk = rsum[MODE == MODE_OFFSET_GRAD ? s : 0] * rsqrt_sfu(sm);   // r / |R_T + d|
+            const float rsm = rsum[MODE == MODE_OFFSET_GRAD ? s : 0];
             const float vy = DIM3 ? hy : 0.5f * tT1 + dvs;
             const float vz = DIM3 ? 0.5f * tT2 + dvs : hz;
-            gacc0 = fmaf(kk, hx, gacc0);
-            gacc1 = fmaf(kk, vy, gacc1);
-            gacc2 = fmaf(kk, vz, gacc2);
+            if (REFRACT && ftrefr && ((bmask >> s) & 1u)) {
+                // refracted leg: r times the unit vector from the transmitter to
+                // its crossing point, (xi h, a) / |W| with h the horizontal unit
+                // vector towards the pixel
+                if (!DIM3) refr_rho(ftr0, a, rhoT, drhoT);
+                float b, db, uxi, ua;
+                slot_depth(s, b, db);
+                (void)refr_leg_diff(p, ftr0, ftr1, ftr2, rhoT, drhoT, b, db, r_br, uxi, ua);
+                const float ih = rhoT > 0.f ? uxi * rcp_sfu(rhoT) : 0.f;
+                gacc0 = fmaf(rsm * ih, hx, gacc0);
+                gacc1 = fmaf(rsm * ih, vy, gacc1);
+                gacc2 = fmaf(rsm, ua, gacc2);
+            } else {
+                const float kk = rsm * rsqrt_sfu(sm);   // r / |R_T + d|
+                gacc0 = fmaf(kk, hx, gacc0);
+                gacc1 = fmaf(kk, vy, gacc1);
+                gacc2 = fmaf(kk, vz, gacc2);
+            }
             rsum[MODE == MODE_OFFSET_GRAD ? s : 0] = 0.f;
         }
         (void)hy;
@@ -1201,6 +1257,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 kap = ffma2(eps, fsub2(eps, one2), one2);                    // 1 / (1 + eps)
                 D = fmul2(D, kap);
             }
+            // refracted receiver legs of the two pixels (offset gradient): which
+            // ones, their horizontal distances and crossing directions
+            unsigned gbk = 0u;
+            float2 grho = make_float2(1.f, 1.f), guxi = make_float2(0.f, 0.f), gua = guxi;
             if constexpr (REFRACT) {
                 if (rrefr) {
                     const unsigned bk = (bmask >> (2 * k)) & 3u;   // which of the two slots are below
@@ -1213,9 +1273,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                         float2 b2, db2;
                         slot_depth(2 * k, b2.x, db2.x);
                         slot_depth(2 * k + 1, b2.y, db2.y);
-                        const float2 Dr = fadd2(refr_leg_diff2(p, rr0, rr1, rr2, rho2, drho2, b2, db2, r_br), dTp[k]);
+                        const float2 Dr = fadd2(refr_leg_diff2(p, rr0, rr1, rr2, rho2, drho2, b2, db2, r_br, guxi, gua),
+                                                dTp[k]);
                         D.x = (bk & 1u) ? Dr.x : D.x + rr2.w;
                         D.y = (bk & 2u) ? Dr.y : D.y + rr2.w;
+                        grho = rho2;
+                        gbk = bk;
                     } else {
                         D = fadd2(D, make_float2(rr2.w, rr2.w));
                     }
@@ -1291,14 +1354,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                 const float r = fmaf(Hx, ax, -Hy * ay) * (j ? kap.y : kap.x);
                 rsum[MODE == MODE_OFFSET_GRAD ? s : 0] += r;
                 // receiver unit vector (R_R + d) / |R_R + d| times r
-                const float kr = r * (j ? rs.y : rs.x);
                 const float dvs = PXS(dvp, s);
                 const float vx = fmaf(0.5f, tRx, dxv);
                 const float vy = DIM3 ? fmaf(0.5f, tRy, dyv_c) : fmaf(0.5f, tRy, dvs);
                 const float vz = DIM3 ? fmaf(0.5f, tRz, dvs) : 0.5f * tRz;
-                gacc0 = fmaf(kr, vx, gacc0);
-                gacc1 = fmaf(kr, vy, gacc1);
-                gacc2 = fmaf(kr, vz, gacc2);
+                if (REFRACT && ((gbk >> j) & 1u)) {
+                    // refracted receiver leg: the unit vector towards its crossing point
+                    const float rh = j ? grho.y : grho.x;
+                    const float ih = rh > 0.f ? (j ? guxi.y : guxi.x) * rcp_sfu(rh) : 0.f;
+                    gacc0 = fmaf(r * ih, vx, gacc0);
+                    gacc1 = fmaf(r * ih, vy, gacc1);
+                    gacc2 = fmaf(r, j ? gua.y : gua.x, gacc2);
+                } else {
+                    const float kr = r * (j ? rs.y : rs.x);
+                    gacc0 = fmaf(kr, vx, gacc0);
+                    gacc1 = fmaf(kr, vy, gacc1);
+                    gacc2 = fmaf(kr, vz, gacc2);
+                }
             }
             }
         }
@@ -1372,6 +1444,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                     tr2 = hr[F_TREF / 4 + 2];
                     if (DIM3) refr_rho(tr0, X + r_d2h, rhoT, drhoT);
                 }
+                if constexpr (REFRACT && MODE == MODE_OFFSET_GRAD) {
+                    ftrefr = trefr;
+                    ftr0 = tr0;
+                    ftr1 = tr1;
+                    ftr2 = tr2;
+                }
 #pragma unroll
                 for (int s = 0; s < PX; ++s) {
                     const float a = __fadd_rn(fmaf(tTv, PXS(dvp, s), PXS(d2p, s)), X);
@@ -1383,7 +1461,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
                             if (!DIM3) refr_rho(tr0, a, rhoT, drhoT);
                             float b, db;
                             slot_depth(s, b, db);
-                            PXS(dTp, s) = refr_leg_diff(p, tr0, tr1, tr2, rhoT, drhoT, b, db, r_br);
+                            float uxi, ua;
+                            PXS(dTp, s) = refr_leg_diff(p, tr0, tr1, tr2, rhoT, drhoT, b, db, r_br, uxi, ua);
                         } else {
                             PXS(dTp, s) += tr2.w;
                         }

@@ -11,7 +11,15 @@ static int launch_one_grad(const Setup& S, cudaStream_t st) {
     const bool mv = S.prm.vel != nullptr;
     auto kern = S.prm.beam ? (mv ? tdbp_kernel<ET, DIM3, MODE, true, true> : tdbp_kernel<ET, DIM3, MODE, true, false>)
                            : (mv ? tdbp_kernel<ET, DIM3, MODE, false, true> : tdbp_kernel<ET, DIM3, MODE, false, false>);
-    if (!S.prm.beam && !mv && S.prm.npos_pad == NPOS_FIXED) kern = tdbp_kernel<ET, DIM3, MODE, false, false, false, true>;
+    if (S.prm.refract) {
+        if (S.prm.beam || mv) {
+            set_error("the refraction model does not combine with receiver motion or a beam");
+            return SAS_ERR_UNSUPPORTED;
+        }
+        kern = tdbp_kernel<ET, DIM3, MODE, false, false, true>;
+    } else if (!S.prm.beam && !mv && S.prm.npos_pad == NPOS_FIXED) {
+        kern = tdbp_kernel<ET, DIM3, MODE, false, false, false, true>;
+    }
     SAS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     kern<<<S.blocks, NTHREADS, S.smem, st>>>(S.map, S.prm);
     SAS_CUDA(cudaGetLastError());

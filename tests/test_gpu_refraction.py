@@ -11,7 +11,7 @@ import oracle
 import paper_2101_05888_gb300 as sas
 from paper_2101_05888_gb300 import synth
 
-from _scene import grid_pixels, lib_signal, oracle_positions, oracle_signal
+from _scene import grid_pixels, in_band, lib_signal, oracle_positions, oracle_signal
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -152,19 +152,110 @@ def test_interface_below_the_grid_and_equal_speeds():
     geom.close()
 
 
+@pytest.mark.parametrize("cs,zint", [(1700.0, 0.013), (1450.0, -0.05)])
+def test_offset_gradient_3d_refraction_matches_oracle(cs, zint):
+    """The offset VJP with refracted legs (the derivative of a refracted leg's
+    length with respect to its sensor is minus the unit vector towards its
+    crossing point) against the oracle's gradient with the same medium; tiles
+    straddle the interface, so straight and refracted legs mix."""
+    w, nav = _volume(nx=16, ny=12, nz=12)
+    echo = synth.random_echo(w.n_pings, w.n_rx, w.n_samples, seed=66)
+    geom = sas.Geometry.from_nav(nav, lib_signal(w))
+    geom.set_refraction(zint, cs)
+    geom.upload_echo(echo)
+    G = synth.random_image((w.grid.nz, w.grid.ny, w.grid.nx), seed=67).astype(np.complex64)
+    grad = torch.empty((w.n_pings, 3), dtype=torch.float64, device="cuda")
+    sas.sas_backproject_adjoint(geom.h, sas.grid_from(w.grid), sas.kaiser(BETA), torch.from_numpy(G).cuda(),
+                                None, grad)
+    geom.sync_status()
+    tx, rx = oracle_positions(nav)
+    with oracle.medium(zint, cs):
+        ref = oracle.vjp_offsets(tx, rx, oracle_signal(w), echo, 8, BETA, grid_pixels(w.grid), G.reshape(-1))
+    straight = oracle.vjp_offsets(tx, rx, oracle_signal(w), echo, 8, BETA, grid_pixels(w.grid), G.reshape(-1))
+    got = grad.cpu().numpy()
+    print("refracted offset gradient (c_s %g): vs oracle %.3g, straight-path gradient differs by %.3g" % (
+        cs, oracle.rel_l2(got, ref), oracle.rel_l2(straight, ref)))
+    assert oracle.rel_l2(got, ref) < 1e-3
+    assert oracle.rel_l2(straight, ref) > 1e-2            # the model changes the gradient
+    geom.close()
+
+
+def test_offset_gradient_2d_slice_below_the_seabed():
+    """Every leg refracts, most past the critical distance (fast sediment)."""
+    w = synth.workload("small_2d", grid=synth.Grid(1.0, 20.0, 0.3, 0.02, 0.02, 0.0, 64, 48, 1),
+                       n_pings=24, n_rx=4, t0=0.02)
+    nav = synth.nav(w)
+    echo = synth.random_echo(w.n_pings, w.n_rx, w.n_samples, seed=68)
+    geom = sas.Geometry.from_nav(nav, lib_signal(w))
+    geom.set_refraction(0.0, 1700.0)
+    geom.upload_echo(echo)
+    G = synth.random_image((1, w.grid.ny, w.grid.nx), seed=69).astype(np.complex64)
+    grad = torch.empty((w.n_pings, 3), dtype=torch.float64, device="cuda")
+    sas.sas_backproject_adjoint(geom.h, sas.grid_from(w.grid), sas.kaiser(BETA), torch.from_numpy(G).cuda(),
+                                None, grad)
+    geom.sync_status()
+    tx, rx = oracle_positions(nav)
+    with oracle.medium(0.0, 1700.0):
+        ref = oracle.vjp_offsets(tx, rx, oracle_signal(w), echo, 8, BETA, grid_pixels(w.grid), G.reshape(-1))
+    assert oracle.rel_l2(grad.cpu().numpy(), ref) < 1e-3
+    geom.close()
+
+
+@pytest.mark.parametrize("dim3,cs,zint", [(True, 1700.0, 0.013), (True, 1450.0, -0.05), (False, 1700.0, 0.0)])
+def test_linear_adjoint_refraction_matches_oracle(dim3, cs, zint):
+    """The linear adjoint with refracted legs against the oracle's adjoint
+    with the same medium (in band at 1e-4, full band at 1e-3: the cubic
+    Farrow form's weight error lies out of band), and the GPU dot test
+    <B e, I> = <e, B^H I> with the refracting forward."""
+    if dim3:
+        w, nav = _volume(nx=14, ny=12, nz=10)
+    else:
+        w = synth.workload("small_2d", grid=synth.Grid(1.0, 20.0, 0.3, 0.02, 0.02, 0.0, 48, 40, 1),
+                           n_pings=16, n_rx=4, t0=0.02)
+        nav = synth.nav(w)
+    geom = sas.Geometry.from_nav(nav, lib_signal(w))
+    geom.set_refraction(zint, cs)
+    img = synth.random_image((w.grid.nz, w.grid.ny, w.grid.nx), seed=70).astype(np.complex64)
+    eadj = torch.empty((w.n_pings, w.n_rx, w.n_samples), dtype=torch.complex64, device="cuda")
+    sas.sas_backproject_adjoint(geom.h, sas.grid_from(w.grid), sas.kaiser(BETA), torch.from_numpy(img).cuda(), eadj)
+    geom.sync_status()
+    tx, rx = oracle_positions(nav)
+    with oracle.medium(zint, cs):
+        ref = oracle.backproject_adjoint(tx, rx, oracle_signal(w), img.reshape(-1), 8, BETA, grid_pixels(w.grid))
+    got = eadj.cpu().numpy()
+    e_band, e_full = oracle.rel_l2(in_band(got), in_band(ref)), oracle.rel_l2(got, ref)
+    # dot test against the GPU forward with the same model
+    echo = synth.random_echo(w.n_pings, w.n_rx, w.n_samples, seed=71)
+    geom.upload_echo(echo)
+    fwd = _image(geom, w)
+    lhs = np.vdot(img.astype(np.complex128).reshape(-1), fwd.astype(np.complex128).reshape(-1))
+    rhs = np.vdot(got.astype(np.complex128).reshape(-1), echo.astype(np.complex128).reshape(-1))
+    e_dot = abs(lhs - rhs) / abs(lhs)
+    print("refracted linear adjoint (3D %s, c_s %g): in band %.3g, full band %.3g, dot test %.3g" % (
+        dim3, cs, e_band, e_full, e_dot))
+    assert e_band < 1e-4
+    assert e_full < 1e-3
+    assert e_dot < 1e-5
+    geom.close()
+
+
 def test_unsupported_combinations_raise():
     w, nav = _volume(nx=8, ny=8, nz=8)
     geom = sas.Geometry.from_nav(nav, lib_signal(w))
     geom.upload_echo(synth.random_echo(w.n_pings, w.n_rx, w.n_samples, seed=65))
     geom.set_refraction(0.0, 1700.0)
     G = torch.zeros((w.grid.nz, w.grid.ny, w.grid.nx), dtype=torch.complex64, device="cuda")
+    adj = torch.zeros((w.n_pings, w.n_rx, w.n_samples), dtype=torch.complex64, device="cuda")
+    geom.set_velocity(np.zeros((w.n_pings, 3)))
+    with pytest.raises(sas.SasError) as e:
+        geom.backproject(sas.grid_from(w.grid), sas.kaiser(BETA))
+    assert e.value.code == sas.SAS_ERR_UNSUPPORTED
     grad = torch.empty((w.n_pings, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(sas.SasError) as e:
         sas.sas_backproject_adjoint(geom.h, sas.grid_from(w.grid), sas.kaiser(BETA), G, None, grad)
     assert e.value.code == sas.SAS_ERR_UNSUPPORTED
-    geom.set_velocity(np.zeros((w.n_pings, 3)))
     with pytest.raises(sas.SasError) as e:
-        geom.backproject(sas.grid_from(w.grid), sas.kaiser(BETA))
+        sas.sas_backproject_adjoint(geom.h, sas.grid_from(w.grid), sas.kaiser(BETA), G, adj, None)
     assert e.value.code == sas.SAS_ERR_UNSUPPORTED
     geom.set_velocity(None)
     geom.set_beam(np.deg2rad(30.0))
