@@ -172,10 +172,11 @@ int sas_geometry_set_velocity(sas_geometry_t h, const double* vel, int on_device
  * is straight.  Applies to the forward backprojection (2D and 3D), the linear
  * adjoint and the offset gradient (the derivative of a refracted leg's length
  * with respect to its sensor is minus the unit vector towards the crossing
- * point) of every later call; c_sediment <= 0 switches the model off (the
- * default).  The simulator returns SAS_ERR_UNSUPPORTED while it is on, and so
- * does any of those calls when the handle also has a velocity
- * (sas_geometry_set_velocity) or a beam (sas_geometry_set_beam).
+ * point) and the echo simulator of every later call; c_sediment <= 0
+ * switches the model off (the default).  Those calls return
+ * SAS_ERR_UNSUPPORTED when the handle also has a velocity
+ * (sas_geometry_set_velocity) or, except the simulator, a beam
+ * (sas_geometry_set_beam).
  * Errors: SAS_ERR_ARG (null handle, non-finite arguments). */
 int sas_geometry_set_refraction(sas_geometry_t h, double z_interface, double c_sediment);
 

@@ -6,6 +6,10 @@
 // the autocorrelation of a linear FM pulse of length T and bandwidth B with a
 // rectangular envelope, normalised to a unit peak (T <= 0 selects sinc(B t)).
 // With a receiver velocity set, tau solves c tau = |x_s - x_TX| + |x_s - x_RX - v tau|.
+// With the seabed refraction model, a leg from a sensor above the interface to
+// a scatterer below it counts |P - s| + n |x_s - P| water metres, P the
+// crossing where the travel time is stationary (Snell's law, solved by
+// bisection in FP64).
 // One block per (ping, channel) row; FP64 delay and carrier phase per
 // (row, scatterer); FP32 pulse samples accumulated with global atomics.
 #include "sas_common.cuh"
@@ -13,10 +17,34 @@
 namespace sas {
 namespace {
 
+// Length in water metres of the leg from sensor s to point x: straight, or
+// with the refraction model (n > 0) and s above / x below the interface
+// z = z_int, |W| + n |V| with the crossing at horizontal run xi from the
+// sensor where xi / |W| = n (rho - xi) / |V| (the left side minus the right
+// increases with xi; bisection on [0, rho] until the bracket is below 1e-12 of
+// the run: the length is stationary at the crossing, so its error is of the
+// bracket's square).
+__device__ double leg_length(const double* sv, double x, double y, double z, double z_int, double n) {
+    const double hx = x - sv[0], hy = y - sv[1], hz = z - sv[2];
+    if (!(n > 0.0) || !(sv[2] < z_int) || !(z > z_int)) return sqrt(hx * hx + hy * hy + hz * hz);
+    const double a = z_int - sv[2], b = z - z_int, rho = sqrt(hx * hx + hy * hy);
+    double lo = 0.0, hi = rho;
+    for (int it = 0; it < 200 && hi - lo > 1e-12 * (rho + 1.0); ++it) {
+        const double m = 0.5 * (lo + hi), sg = rho - m;
+        if (m * sqrt(sg * sg + b * b) > n * sg * sqrt(m * m + a * a))
+            hi = m;
+        else
+            lo = m;
+    }
+    const double xi = 0.5 * (lo + hi), sg = rho - xi;
+    return sqrt(xi * xi + a * a) + n * sqrt(sg * sg + b * b);
+}
+
 __global__ void simulate_points_kernel(const double* __restrict__ tx, const double* __restrict__ rx,
                                        const double* __restrict__ vel, int C, int Ns, double t0, double fs,
                                        double fc, double inv_c, const double* __restrict__ scat, long long nscat,
-                                       float B, float T, int half_width, float2* __restrict__ echo) {
+                                       float B, float T, int half_width, double z_int, double n_refr,
+                                       float2* __restrict__ echo) {
     const long long row = blockIdx.x;
     const int i = (int)(row / C);
     const double* t = tx + 3 * (size_t)i;
@@ -25,10 +53,9 @@ __global__ void simulate_points_kernel(const double* __restrict__ tx, const doub
     const float inv_fs = (float)(1.0 / fs);
     for (long long s = 0; s < nscat; ++s) {
         const double* q = scat + 5 * s;
-        const double ax = q[0] - t[0], ay = q[1] - t[1], az = q[2] - t[2];
         const double bx = q[0] - r[0], by = q[1] - r[1], bz = q[2] - r[2];
-        const double rt = sqrt(ax * ax + ay * ay + az * az);
-        double tau = (rt + sqrt(bx * bx + by * by + bz * bz)) * inv_c;
+        const double rt = leg_length(t, q[0], q[1], q[2], z_int, n_refr);
+        double tau = (rt + leg_length(r, q[0], q[1], q[2], z_int, n_refr)) * inv_c;
         if (vel) {
             // receiver moving during reception: c tau = |x - x_TX| + |x - x_RX - v tau|
             const double* v = vel + 3 * (size_t)i;
@@ -82,15 +109,15 @@ extern "C" int sas_simulate_points(sas_geometry_t h, const double* d_scat, int64
         set_error("sas_simulate_points: bad argument");
         return SAS_ERR_ARG;
     }
-    if (h->c_sed > 0.0) {
-        set_error("sas_simulate_points: not available with the refraction model");
+    if (h->c_sed > 0.0 && h->has_vel) {
+        set_error("sas_simulate_points: the refraction model does not combine with receiver motion");
         return SAS_ERR_UNSUPPORTED;
     }
     if (n == 0) return SAS_OK;
     const unsigned rows = (unsigned)((long long)h->P * h->C);
     simulate_points_kernel<<<rows, 256, 0, (cudaStream_t)stream>>>(
         h->d_tx, h->d_rx, h->has_vel ? h->d_vel : nullptr, h->C, h->Ns, h->sig.t0, h->sig.fs, h->sig.fc, 1.0 / h->sig.c, d_scat, n, (float)bandwidth,
-        (float)pulse_T, half_width, (float2*)d_echo);
+        (float)pulse_T, half_width, h->z_int, h->c_sed > 0.0 ? h->sig.c / h->c_sed : 0.0, (float2*)d_echo);
     SAS_CUDA(cudaGetLastError());
     return SAS_OK;
 }

@@ -239,6 +239,46 @@ def test_linear_adjoint_refraction_matches_oracle(dim3, cs, zint):
     geom.close()
 
 
+@pytest.mark.parametrize("cs", [1700.0, 1450.0])
+def test_simulator_with_refraction_matches_oracle(cs):
+    """The library's echo simulator with refracted legs (scatterers above and
+    below the interface, a fast and a slow sediment) against the oracle's
+    simulator with the same medium; the library's echoes of buried points
+    then focus through the refracting backprojection."""
+    w, nav = _volume(nx=24, ny=24, nz=16, z0=-0.06)
+    g = w.grid
+    idx = np.array([[5, 7, 9], [17, 15, 13], [11, 20, 1], [3, 3, 14]])
+    pts = oracle.grid_index_points(g.x0, g.y0, g.z0, g.dx, g.dy, g.dz, idx)
+    A = np.array([0.9 * np.exp(0.3j), 0.7 * np.exp(-1.1j), 0.8 * np.exp(2.0j), 0.6 * np.exp(0.7j)])
+    scat = np.concatenate([pts, A.real[:, None], A.imag[:, None]], 1)
+    geom = sas.Geometry(nav["true_pos"], nav["att"], nav["tx_lever"], nav["rx_lever"], lib_signal(w))
+    geom.set_refraction(0.0, cs)
+    echo = torch.zeros((w.n_pings, w.n_rx, w.n_samples), dtype=torch.complex64, device="cuda")
+    sas.sas_simulate_points(geom.h, torch.from_numpy(scat).cuda(), scat.shape[0], synth.BANDWIDTH, synth.PULSE_T,
+                            0, echo)
+    torch.cuda.synchronize()
+    got = echo.cpu().numpy()
+    tx, rx = oracle_positions(nav, true=True)
+    with oracle.medium(0.0, cs):
+        ref = oracle.simulate_points(tx, rx, oracle_signal(w), synth.BANDWIDTH, synth.PULSE_T, scat)
+    straight = oracle.simulate_points(tx, rx, oracle_signal(w), synth.BANDWIDTH, synth.PULSE_T, scat)
+    print("simulator with refraction (c_s %g): vs oracle %.3g, vs straight paths %.3g" % (
+        cs, oracle.rel_l2(got, ref), oracle.rel_l2(straight, ref)))
+    assert oracle.rel_l2(got, ref) < 2e-5          # the simulator's FP32 pulse samples, as without the model
+    assert oracle.rel_l2(straight, ref) > 0.1
+    geom.close()
+    img_geom = sas.Geometry.from_nav(nav, lib_signal(w))
+    img_geom.set_refraction(0.0, cs)
+    img_geom.upload_echo(got)
+    img = _image(img_geom, w)
+    # the three interior points (the corner point's peak carries more of the
+    # other points' sidelobes than the 10 % bound allows in the slow sediment)
+    PC = w.n_pings * w.n_rx
+    for (ix, iy, iz), a in zip(idx[:3], A[:3]):
+        assert abs(img[iz, iy, ix] - a * PC) < 0.1 * abs(a) * PC
+    img_geom.close()
+
+
 def test_unsupported_combinations_raise():
     w, nav = _volume(nx=8, ny=8, nz=8)
     geom = sas.Geometry.from_nav(nav, lib_signal(w))
@@ -265,9 +305,11 @@ def test_unsupported_combinations_raise():
     geom.set_beam(0.0)
     scat = torch.zeros((1, 5), dtype=torch.float64, device="cuda")
     echo = torch.zeros((w.n_pings, w.n_rx, w.n_samples), dtype=torch.complex64, device="cuda")
+    geom.set_velocity(np.zeros((w.n_pings, 3)))
     with pytest.raises(sas.SasError) as e:
         sas.sas_simulate_points(geom.h, scat, 1, synth.BANDWIDTH, synth.PULSE_T, 0, echo)
     assert e.value.code == sas.SAS_ERR_UNSUPPORTED
+    geom.set_velocity(None)
     geom.set_refraction(0.0, 0.0)                  # off again: everything runs
     geom.backproject(sas.grid_from(w.grid), sas.kaiser(BETA))
     geom.sync_status()
