@@ -484,8 +484,12 @@ __global__ void __launch_bounds__(TVG_THREADS, 2) tvg_median_kernel(const float2
     }
 }
 
-__global__ void tvg_gain_kernel(const double* __restrict__ med, int n, double alpha, float* __restrict__ gain) {
-    __shared__ double red[1024];
+// Every block forms the mean of the medians (the same sum in the same order:
+// the result does not depend on the block) and the gains of its 256 columns:
+// the FP64 square roots and divisions spread over the SMs.
+__global__ void __launch_bounds__(256) tvg_gain_kernel(const double* __restrict__ med, int n, double alpha,
+                                                       float* __restrict__ gain) {
+    __shared__ double red[256];
     double s = 0.0;
     for (int t = threadIdx.x; t < n; t += blockDim.x) s += med[t];
     red[threadIdx.x] = s;
@@ -495,7 +499,8 @@ __global__ void tvg_gain_kernel(const double* __restrict__ med, int n, double al
         __syncthreads();
     }
     const double pbar = red[0] / (double)n;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
         const double den = alpha * pbar + med[t];
         gain[t] = den > 0.0 ? (float)sqrt(1.0 / den) : 1.f;    // silent median, alpha = 0: no correction
     }
@@ -872,7 +877,7 @@ extern "C" int sas_tvg(const void* d_in, void* d_out, int64_t rows, int32_t n, d
         return cuda_fail(e0, "tvg");
     }
     tvg_median_kernel<<<(n + TVG_COLS - 1) / TVG_COLS, TVG_THREADS, TVG_SMEM, st>>>((const float2*)d_in, rows, n, med);
-    tvg_gain_kernel<<<1, 1024, 0, st>>>(med, n, alpha, gain);
+    tvg_gain_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(med, n, alpha, gain);
     const unsigned gx = (unsigned)((n + 255) / 256);
     const unsigned gy = (unsigned)std::max<long long>(1, std::min<long long>(rows, (16LL * sm_count() + gx - 1) / gx));
     scale_columns_kernel<<<dim3(gx, gy), 256, 0, st>>>((const float2*)d_in, (float2*)d_out, rows, n, gain);
