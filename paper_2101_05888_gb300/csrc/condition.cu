@@ -23,6 +23,7 @@
 #include "sas_common.cuh"
 
 #include <algorithm>
+#include <cmath>
 
 namespace sas {
 namespace {
@@ -372,9 +373,10 @@ __device__ __forceinline__ unsigned tvg_bits(float2 v) {
 
 // One level over the strip: every value of column c whose bits >> PSH equal
 // that rank's prefix >> PSH adds to bin (bits >> BSH) & (NB - 1) of h[r][c].
+// (rows: the rows the select sees, physical rows 0, rstep, 2 rstep, ...)
 template <int LEVEL>
-__device__ __forceinline__ void tvg_level(const float2* __restrict__ e, long long rows, int n, int col, bool colok,
-                                          unsigned* h, const unsigned* prefix) {
+__device__ __forceinline__ void tvg_level(const float2* __restrict__ e, long long rows, long long rstep, int n, int col,
+                                          bool colok, unsigned* h, const unsigned* prefix) {
     constexpr int NB = LEVEL == 1 ? 2048 : 1024, BSH = LEVEL == 1 ? 20 : (LEVEL == 2 ? 10 : 0);
     constexpr int PSH = LEVEL == 2 ? 20 : 10;
     const int c = threadIdx.x % TVG_COLS;
@@ -400,11 +402,11 @@ __device__ __forceinline__ void tvg_level(const float2* __restrict__ e, long lon
     for (; r + 7 * TVG_RPI < rows; r += 8 * TVG_RPI) {
         float2 v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = e[(r + u * TVG_RPI) * n + col];
+        for (int u = 0; u < 8; ++u) v[u] = e[(r + u * TVG_RPI) * rstep * n + col];
 #pragma unroll
         for (int u = 0; u < 8; ++u) add(tvg_bits(v[u]));
     }
-    for (; r < rows; r += TVG_RPI) add(tvg_bits(e[r * n + col]));
+    for (; r < rows; r += TVG_RPI) add(tvg_bits(e[r * rstep * n + col]));
 }
 
 // The bins of every (column, rank) holding the rank's residual: one warp per
@@ -449,39 +451,184 @@ __device__ __forceinline__ void tvg_pick(const unsigned* h, unsigned* prefix, un
     }
 }
 
-__global__ void __launch_bounds__(TVG_THREADS, 2) tvg_median_kernel(const float2* __restrict__ e, long long rows, int n,
-                                                                 double* __restrict__ med) {
+// Two order statistics (ranks r_lo <= r_hi) of every column of the strip, over
+// rows 0, rstep, 2 rstep, ... (rows of them).  Writes the midpoint of the
+// two (the median when the ranks are the middle ones) to med, or, with
+// bracket set, their bit patterns.  With flags set, a strip none of whose
+// columns is flagged returns at once.
+__global__ void __launch_bounds__(TVG_THREADS, 2) tvg_select_kernel(const float2* __restrict__ e, long long rows,
+                                                                   long long rstep, int n, unsigned r_lo,
+                                                                   unsigned r_hi, double* __restrict__ med,
+                                                                   uint2* __restrict__ bracket,
+                                                                   const int* __restrict__ flags) {
     extern __shared__ unsigned tvg_h[];                       // TVG_COLS x 2048 counters
     __shared__ unsigned prefix[2 * TVG_COLS], rank[2 * TVG_COLS];   // index 2 c + r
+    __shared__ int any;
+    if (flags) {
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        const int fc = blockIdx.x * TVG_COLS + (int)threadIdx.x;
+        if (threadIdx.x < TVG_COLS && fc < n && flags[fc]) any = 1;
+        __syncthreads();
+        if (!any) return;
+    }
     const int col = blockIdx.x * TVG_COLS + (int)(threadIdx.x % TVG_COLS);
     const bool colok = col < n;
     if (threadIdx.x < 2 * TVG_COLS) {
         prefix[threadIdx.x] = 0u;
-        rank[threadIdx.x] = (threadIdx.x & 1) ? (unsigned)(rows / 2) : (unsigned)((rows - 1) / 2);
+        rank[threadIdx.x] = (threadIdx.x & 1) ? r_hi : r_lo;
     }
     for (int t = threadIdx.x; t < TVG_COLS * 2048; t += TVG_THREADS) tvg_h[t] = 0u;
     __syncthreads();
-    tvg_level<1>(e, rows, n, col, colok, tvg_h, prefix);
+    tvg_level<1>(e, rows, rstep, n, col, colok, tvg_h, prefix);
     __syncthreads();
     tvg_pick<1>(tvg_h, prefix, rank);
     __syncthreads();
     for (int t = threadIdx.x; t < TVG_COLS * 2048; t += TVG_THREADS) tvg_h[t] = 0u;
     __syncthreads();
-    tvg_level<2>(e, rows, n, col, colok, tvg_h, prefix);
+    tvg_level<2>(e, rows, rstep, n, col, colok, tvg_h, prefix);
     __syncthreads();
     tvg_pick<2>(tvg_h, prefix, rank);
     __syncthreads();
     for (int t = threadIdx.x; t < TVG_COLS * 2048; t += TVG_THREADS) tvg_h[t] = 0u;
     __syncthreads();
-    tvg_level<3>(e, rows, n, col, colok, tvg_h, prefix);
+    tvg_level<3>(e, rows, rstep, n, col, colok, tvg_h, prefix);
     __syncthreads();
     tvg_pick<3>(tvg_h, prefix, rank);
     __syncthreads();
     if (threadIdx.x < TVG_COLS && blockIdx.x * TVG_COLS + (int)threadIdx.x < n) {
-        const int c = threadIdx.x;
-        const float lo = __uint_as_float(prefix[2 * c]), hi = __uint_as_float(prefix[2 * c + 1]);
-        med[blockIdx.x * TVG_COLS + c] = 0.5 * ((double)lo + (double)hi);
+        const int c = threadIdx.x, gc = blockIdx.x * TVG_COLS + c;
+        if (bracket) {
+            bracket[gc] = make_uint2(prefix[2 * c], prefix[2 * c + 1]);
+        } else {
+            const float lo = __uint_as_float(prefix[2 * c]), hi = __uint_as_float(prefix[2 * c + 1]);
+            med[gc] = 0.5 * ((double)lo + (double)hi);
+        }
     }
+}
+
+// Bracketed select (large row counts).  An exact select on every rstep-th row
+// gives each column a bracket [lo, hi] (bit patterns) that holds the column's
+// middle order statistics with overwhelming probability; one pass over all
+// rows counts the values below lo and collects those inside the bracket
+// (at most TVG_CAP a column); a block per column then selects both middle
+// ranks among the collected values.  A column whose bracket misses a middle
+// rank, or whose collection overflowed, is flagged and selected again by the
+// full three-level kernel, so the result is exact in every case.
+constexpr int TVG_CAP = 8192;
+constexpr long long TVG_BRACKET_MIN_ROWS = 16384;   // fewer rows: the three-level select directly
+constexpr long long TVG_SAMPLE = 2048;              // rows of the sample (about)
+
+__global__ void __launch_bounds__(TVG_THREADS) tvg_collect_kernel(const float2* __restrict__ e, long long rows, int n,
+                                                                  const uint2* __restrict__ bracket,
+                                                                  unsigned* __restrict__ cand,
+                                                                  unsigned* __restrict__ below,
+                                                                  unsigned* __restrict__ nin) {
+    __shared__ unsigned s_cnt[TVG_COLS], s_below[TVG_COLS];
+    const int c = threadIdx.x % TVG_COLS, col = blockIdx.x * TVG_COLS + c;
+    if (threadIdx.x < TVG_COLS) s_cnt[threadIdx.x] = s_below[threadIdx.x] = 0u;
+    __syncthreads();
+    if (col < n) {
+        const uint2 br = bracket[col];
+        unsigned* cc = cand + (size_t)col * TVG_CAP;
+        unsigned nb = 0u;
+        auto put = [&](unsigned bits) {
+            if (bits < br.x) {
+                ++nb;
+            } else if (bits <= br.y) {
+                const unsigned pos = atomicAdd(&s_cnt[c], 1u);
+                if (pos < (unsigned)TVG_CAP) cc[pos] = bits;
+            }
+        };
+        long long r = threadIdx.x / TVG_COLS;
+        for (; r + 7 * TVG_RPI < rows; r += 8 * TVG_RPI) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = e[(r + u * TVG_RPI) * n + col];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) put(tvg_bits(v[u]));
+        }
+        for (; r < rows; r += TVG_RPI) put(tvg_bits(e[r * n + col]));
+        atomicAdd(&s_below[c], nb);
+    }
+    __syncthreads();
+    if (threadIdx.x < TVG_COLS && blockIdx.x * TVG_COLS + (int)threadIdx.x < n) {
+        below[blockIdx.x * TVG_COLS + threadIdx.x] = s_below[threadIdx.x];
+        nin[blockIdx.x * TVG_COLS + threadIdx.x] = s_cnt[threadIdx.x];
+    }
+}
+
+// One column per block: checks the bracket and selects both middle ranks
+// among its collected values (three radix levels on the bit patterns, as
+// above), else flags the column.
+__global__ void __launch_bounds__(256) tvg_bracket_select_kernel(const unsigned* __restrict__ cand,
+                                                                 const unsigned* __restrict__ below,
+                                                                 const unsigned* __restrict__ nin, long long rows,
+                                                                 double* __restrict__ med, int* __restrict__ flags) {
+    __shared__ unsigned v[TVG_CAP];
+    __shared__ unsigned h[2048];     // level 0: one histogram of 2048 bins; levels 1, 2: one of 1024 per rank
+    __shared__ unsigned pre[2], rk[2];
+    const int col = blockIdx.x;
+    const unsigned nb = below[col], ni = nin[col];
+    const unsigned R0 = (unsigned)((rows - 1) / 2), R1 = (unsigned)(rows / 2);
+    const bool ok = ni <= (unsigned)TVG_CAP && nb <= R0 && R1 < nb + ni;
+    if (threadIdx.x == 0) flags[col] = ok ? 0 : 1;
+    if (!ok) return;
+    for (unsigned t = threadIdx.x; t < ni; t += blockDim.x) v[t] = cand[(size_t)col * TVG_CAP + t];
+    if (threadIdx.x < 2) {
+        pre[threadIdx.x] = 0u;
+        rk[threadIdx.x] = (threadIdx.x ? R1 : R0) - nb;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll 1
+    for (int L = 0; L < 3; ++L) {
+        const int NB = L == 0 ? 2048 : 1024, SH = L == 0 ? 20 : (L == 1 ? 10 : 0), PSH = L == 1 ? 20 : 10;
+        for (int t = threadIdx.x; t < 2048; t += blockDim.x) h[t] = 0u;
+        __syncthreads();
+        const unsigned p0 = pre[0] >> PSH, p1 = pre[1] >> PSH;
+        for (unsigned t = threadIdx.x; t < ni; t += blockDim.x) {
+            const unsigned b = v[t], k = (b >> SH) & (unsigned)(NB - 1);
+            if (L == 0 || (b >> PSH) == p0) atomicAdd(&h[k], 1u);
+            if (L > 0 && (b >> PSH) == p1) atomicAdd(&h[1024 + k], 1u);
+        }
+        __syncthreads();
+        // warp r picks the bin of rank r (level 0: one histogram for both)
+        if (wid < 2) {
+            const unsigned* hh = h + (L == 0 ? 0 : wid * 1024);
+            const int PER = NB / 32;
+            const unsigned want = rk[wid];
+            unsigned tot = 0u;
+            for (int k = 0; k < PER; ++k) tot += hh[lane * PER + k];
+            unsigned x = tot;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            unsigned bl = x - tot, bin = 0u, before = 0u;
+            const bool mine = want >= bl && want - bl < tot;
+            if (mine) {
+                for (int k = 0; k < PER; ++k) {
+                    const unsigned hk = hh[lane * PER + k];
+                    if (want - bl < hk) {
+                        bin = lane * PER + k;
+                        before = bl;
+                        break;
+                    }
+                    bl += hk;
+                }
+            }
+            const unsigned who = __ballot_sync(0xffffffffu, mine);
+            const int src = who ? __ffs(who) - 1 : 0;
+            bin = __shfl_sync(0xffffffffu, bin, src);
+            before = __shfl_sync(0xffffffffu, before, src);
+            if (lane == 0) {
+                rk[wid] = want - before;
+                pre[wid] |= bin << SH;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) med[col] = 0.5 * ((double)__uint_as_float(pre[0]) + (double)__uint_as_float(pre[1]));
 }
 
 // Every block forms the mean of the medians (the same sum in the same order:
@@ -871,12 +1018,43 @@ extern "C" int sas_tvg(const void* d_in, void* d_out, int64_t rows, int32_t n, d
         if (!med) med = own;
         if (!gain) gain = reinterpret_cast<float*>(own + n);
     }
-    cudaError_t e0 = cudaFuncSetAttribute(tvg_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TVG_SMEM);
+    cudaError_t e0 = cudaFuncSetAttribute(tvg_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TVG_SMEM);
     if (e0 != cudaSuccess) {
         if (own) cudaFreeAsync(own, st);
         return cuda_fail(e0, "tvg");
     }
-    tvg_median_kernel<<<(n + TVG_COLS - 1) / TVG_COLS, TVG_THREADS, TVG_SMEM, st>>>((const float2*)d_in, rows, n, med);
+    const unsigned strips = (unsigned)((n + TVG_COLS - 1) / TVG_COLS);
+    const float2* ein = (const float2*)d_in;
+    if (rows < TVG_BRACKET_MIN_ROWS) {
+        tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, rows, 1, n, (unsigned)((rows - 1) / 2),
+                                                                 (unsigned)(rows / 2), med, nullptr, nullptr);
+    } else {
+        // the sample: every rstep-th row (m of them), its ranks m/2 -+ about four standard deviations
+        const long long rstep = rows / TVG_SAMPLE, m = (rows + rstep - 1) / rstep;
+        const long long d = (long long)std::ceil(2.0 * std::sqrt((double)m)) + 1;
+        const unsigned k_lo = (unsigned)std::max(0LL, (m - 1) / 2 - d), k_hi = (unsigned)std::min(m - 1, m / 2 + d);
+        // scratch: brackets, candidates, counts, flags
+        const size_t o_c = (sizeof(uint2) * n + 255) / 256 * 256;
+        const size_t o_b = o_c + sizeof(unsigned) * (size_t)n * TVG_CAP;
+        const size_t o_n = o_b + sizeof(unsigned) * n, o_f = o_n + sizeof(unsigned) * n;
+        char* scr = nullptr;
+        cudaError_t ea = cudaMallocAsync((void**)&scr, o_f + sizeof(int) * n, st);
+        if (ea != cudaSuccess) {
+            if (own) cudaFreeAsync(own, st);
+            return cuda_fail(ea, "tvg scratch");
+        }
+        uint2* br = reinterpret_cast<uint2*>(scr);
+        unsigned* cand = reinterpret_cast<unsigned*>(scr + o_c);
+        unsigned* nb = reinterpret_cast<unsigned*>(scr + o_b);
+        unsigned* ni = reinterpret_cast<unsigned*>(scr + o_n);
+        int* fl = reinterpret_cast<int*>(scr + o_f);
+        tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, m, rstep, n, k_lo, k_hi, nullptr, br, nullptr);
+        tvg_collect_kernel<<<strips, TVG_THREADS, 0, st>>>(ein, rows, n, br, cand, nb, ni);
+        tvg_bracket_select_kernel<<<(unsigned)n, 256, 0, st>>>(cand, nb, ni, rows, med, fl);
+        tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, rows, 1, n, (unsigned)((rows - 1) / 2),
+                                                                 (unsigned)(rows / 2), med, nullptr, fl);
+        cudaFreeAsync(scr, st);
+    }
     tvg_gain_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(med, n, alpha, gain);
     const unsigned gx = (unsigned)((n + 255) / 256);
     const unsigned gy = (unsigned)std::max<long long>(1, std::min<long long>(rows, (16LL * sm_count() + gx - 1) / gx));

@@ -92,6 +92,32 @@ def test_whitening_output_not_16_byte_aligned():
     assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-5
 
 
+@pytest.mark.parametrize("rows,n", [(20000, 37), (65537, 24)])
+def test_tvg_bracketed_select_matches_oracle(rows, n):
+    """Row counts that take the bracketed select (a sample's bracket, one
+    collecting pass, a select among the collected values), with columns that
+    force the exact fallback: a constant column (every value inside the
+    bracket: the collection overflows), a column whose lower half is one value
+    (the bracket's lower end ties with half the column) and zeros; medians
+    exact, gains and output as for the direct select."""
+    rng = np.random.default_rng(rows + n)
+    env = np.exp(-np.linspace(0, 4, n))
+    e = ((rng.normal(size=(rows, n)) + 1j * rng.normal(size=(rows, n))) * env).astype(np.complex64)
+    e[:, 3] = 0.5 - 0.25j                                   # constant column
+    e[: rows // 2 + 1, 5] = 0.3                             # a tie across the lower half and the median
+    e[:7, 0] = 0.0
+    d_in = torch.from_numpy(e).cuda()
+    out = torch.empty_like(d_in)
+    gain = torch.empty(n, dtype=torch.float32, device="cuda")
+    med = torch.empty(n, dtype=torch.float64, device="cuda")
+    sas.sas_tvg(d_in, out, rows, n, 0.2, gain, med)
+    torch.cuda.synchronize()
+    ref, G, Pmed = cond.tvg(e, 0.2)
+    assert np.array_equal(med.cpu().numpy(), Pmed)            # exact selection
+    assert np.abs(gain.cpu().numpy() - np.sqrt(G)).max() <= 1e-6 * np.sqrt(G).max()
+    assert oracle.rel_l2(out.cpu().numpy(), ref) < 1e-6
+
+
 @pytest.mark.parametrize("rows,n,alpha", [(41, 300, 0.0), (64, 333, 0.25), (1, 40, 0.1), (2, 65, 0.0),
                                             (700, 50, 0.2), (300, 17, 0.0)])
 def test_tvg_matches_oracle(rows, n, alpha):
