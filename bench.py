@@ -363,18 +363,29 @@ def run_ours(args, rank, world, local_rank):
         fn(geoms[1].h, grid, interp, images[1], 0)          # first use of the second handle, untimed
         torch.cuda.synchronize()
         done = [None, None]                                 # event: last backprojection of handle b
-        t0 = time.perf_counter()
-        for k in range(args.e2e_steps):
+
+        def upload(k):
+            # handle k % 2: after its previous backprojection has read its echo
             b = k % 2
             if done[b] is not None:
                 s_copy.wait_event(done[b])
             sas.sas_echo_upload(geoms[b].h, h_echo, 0, store, stream=s_copy)
-            up = torch.cuda.Event()
-            up.record(s_copy)
+            ev = torch.cuda.Event()
+            ev.record(s_copy)
+            return ev
+
+        t0 = time.perf_counter()
+        up = upload(0)
+        for k in range(args.e2e_steps):
+            b = k % 2
             s_comp.wait_event(up)
             fn(geoms[b].h, grid, interp, images[b], 0, stream=s_comp)
             done[b] = torch.cuda.Event()
             done[b].record(s_comp)
+            # the next step's upload goes on the copy stream before this step's
+            # read-back (which waits for this backprojection)
+            if k + 1 < args.e2e_steps:
+                up = upload(k + 1)
             s_copy.wait_event(done[b])
             with torch.cuda.stream(s_copy):
                 h_imgs[b].copy_(images[b], non_blocking=True)
