@@ -81,6 +81,9 @@ def parse():
                     help="azimuth beam width [deg] (ray culling on); 0 = omnidirectional")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip the learned-interpolator / BF16 arm (2D straight-path workloads only)")
+    ap.add_argument("--grad", action="store_true",
+                    help="time the offset gradient (the autofocus VJP, tile recompute) for a seeded image "
+                         "gradient instead of the forward backprojection; no end-to-end or learned arm")
     ap.add_argument("--refraction", type=float, default=0.0, metavar="C_SEDIMENT",
                     help="seabed refraction: sediment sound speed [m/s] below the interface z = 0 (the "
                          "workloads' seafloor); 0 = straight paths")
@@ -235,7 +238,9 @@ def config_of(w, args):
     g = w.grid
     return {"workload": w.name, "pings": w.n_pings, "rx": w.n_rx, "samples": w.n_samples,
             "pixels": "%dx%dx%d" % (g.nx, g.ny, g.nz), "pixel_m": g.dx, "taps": 8,
-            "interp": "kaiser_sinc beta=%g (Farrow form, a cubic on each half sample)" % BETA, "echo": args.echo,
+            "interp": "kaiser_sinc beta=%g (Farrow form, a %s on each half sample)" % (
+                BETA, "quadratic" if args.echo != "c64" and not args.grad else "cubic"), "echo": args.echo,
+            **({"pass": "offset gradient (VJP) of a seeded image gradient"} if args.grad else {}),
             "updates_per_step": w.updates, "l2": l2_note(w, args), "parallelism": "replicas",
             "delay_model": ("receiver moving during reception" if args.motion else "stop-and-hop") +
                            (", seabed refraction (interface z = 0, c_sediment = %g m/s)" % args.refraction
@@ -283,6 +288,14 @@ def run_ours(args, rank, world, local_rank):
 
     def step():
         fn(geom.h, grid, interp, image, 0)
+
+    if args.grad:
+        gimg = torch.randn(image.shape, dtype=torch.complex64, device=dev,
+                           generator=torch.Generator(device=dev).manual_seed(99))
+        gbuf = torch.empty((w.n_pings, 3), dtype=torch.float64, device=dev)
+
+        def step():
+            sas.sas_backproject_adjoint(geom.h, grid, interp, gimg, None, gbuf)
 
     # the paper's timing protocol (Sec. III-C): the same job three times, the
     # third reported -- here the third of the warm-up runs, each timed alone
@@ -338,7 +351,7 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
             "traffic": (TRAFFIC_BYTES.get((w.name, args.echo))
                         if args.beam_deg <= 0 and not args.pings and not args.motion and args.refraction <= 0
-                        else None),
+                        and not args.grad else None),
             "peak_basis": "%d SMs x %.0f MHz x %.0f updates/clk/SM (FP32 128 lanes / 32 ops, SFU 16 lanes / 4 ops)"
                           % (props.multi_processor_count, sm_max, UPDATES_PER_CLK_PER_SM)}
     if clk.get("sm_mhz"):
@@ -353,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
     # after the backprojection that last read it.  The timed region starts
     # with every stream idle, so the first upload is not hidden.
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not args.grad:
         h_echo = torch.from_numpy(echo).pin_memory()
         geoms = [geom, make_geometry()]
         images = [image, torch.empty_like(image)]
@@ -404,7 +417,7 @@ def run_ours(args, rank, world, local_rank):
     # on the same workload, its speed against the FP32 Kaiser-sinc line above and
     # its error against the FP64 oracle's 32-tap interpolation on sampled pixels
     learned_line = None
-    if args.learned and not (args.beam_deg > 0 or args.motion or args.refraction > 0 or dim3):
+    if args.learned and not (args.beam_deg > 0 or args.motion or args.refraction > 0 or dim3 or args.grad):
         learned_line = learned_arm(args, w, nav, echo, geom, grid, image, stream, ms_per_step, rank == 0)
 
     cb = None
@@ -417,7 +430,7 @@ def run_ours(args, rank, world, local_rank):
                 "vs_baseline": None, "dtype": "f32" if args.echo == "c64" else "f32 (echo %s)" % args.echo,
                 "data": "synthetic (seeded band-limited Gaussian echo rows, stripmap nav with sway/heave/yaw)",
                 "config": config_of(w, args), "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
-                "clocks": clk, "gpu_launches": args.steps,
+                "clocks": clk, "gpu_launches": args.steps * (2 if args.grad else 1),
                 **({"cull": {"blocks_candidate": cand, "blocks_computed": computed, "blocks_beam_edge": edge,
                              "computed_fraction": computed / max(cand, 1.0),
                              "updates_computed": computed_updates, "updates_dense": w.updates}}

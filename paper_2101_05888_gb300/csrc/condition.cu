@@ -454,24 +454,13 @@ __device__ __forceinline__ void tvg_pick(const unsigned* h, unsigned* prefix, un
 // Two order statistics (ranks r_lo <= r_hi) of every column of the strip, over
 // rows 0, rstep, 2 rstep, ... (rows of them).  Writes the midpoint of the
 // two (the median when the ranks are the middle ones) to med, or, with
-// bracket set, their bit patterns.  With flags set, a strip none of whose
-// columns is flagged returns at once.
+// bracket set, their bit patterns.
 __global__ void __launch_bounds__(TVG_THREADS, 2) tvg_select_kernel(const float2* __restrict__ e, long long rows,
                                                                    long long rstep, int n, unsigned r_lo,
                                                                    unsigned r_hi, double* __restrict__ med,
-                                                                   uint2* __restrict__ bracket,
-                                                                   const int* __restrict__ flags) {
+                                                                   uint2* __restrict__ bracket) {
     extern __shared__ unsigned tvg_h[];                       // TVG_COLS x 2048 counters
     __shared__ unsigned prefix[2 * TVG_COLS], rank[2 * TVG_COLS];   // index 2 c + r
-    __shared__ int any;
-    if (flags) {
-        if (threadIdx.x == 0) any = 0;
-        __syncthreads();
-        const int fc = blockIdx.x * TVG_COLS + (int)threadIdx.x;
-        if (threadIdx.x < TVG_COLS && fc < n && flags[fc]) any = 1;
-        __syncthreads();
-        if (!any) return;
-    }
     const int col = blockIdx.x * TVG_COLS + (int)(threadIdx.x % TVG_COLS);
     const bool colok = col < n;
     if (threadIdx.x < 2 * TVG_COLS) {
@@ -513,8 +502,9 @@ __global__ void __launch_bounds__(TVG_THREADS, 2) tvg_select_kernel(const float2
 // rows counts the values below lo and collects those inside the bracket
 // (at most TVG_CAP a column); a block per column then selects both middle
 // ranks among the collected values.  A column whose bracket misses a middle
-// rank, or whose collection overflowed, is flagged and selected again by the
-// full three-level kernel, so the result is exact in every case.
+// rank, or whose collection overflowed, is flagged and selected again over
+// all its rows by a block of its own (the three radix levels), so the result
+// is exact in every case.
 constexpr int TVG_CAP = 8192;
 constexpr long long TVG_BRACKET_MIN_ROWS = 16384;   // fewer rows: the three-level select directly
 constexpr long long TVG_SAMPLE = 2048;              // rows of the sample (about)
@@ -558,6 +548,46 @@ __global__ void __launch_bounds__(TVG_THREADS) tvg_collect_kernel(const float2* 
     }
 }
 
+// One radix level's pick for a block selecting two ranks of one column: warp
+// r (r = 0, 1) finds the bin of h holding rank r's residual (level 0: one
+// histogram of NB bins for both; later levels: 1024 bins per rank at h + 1024 r),
+// appends it to pre[r] at bit SH and keeps the rank within the bin.
+__device__ void tvg_block_pick(const unsigned* h, int L, int NB, int SH, unsigned* pre, unsigned* rk) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid >= 2) return;
+    const unsigned* hh = h + (L == 0 ? 0 : wid * 1024);
+    const int PER = NB / 32;
+    const unsigned want = rk[wid];
+    unsigned tot = 0u;
+    for (int k = 0; k < PER; ++k) tot += hh[lane * PER + k];
+    unsigned x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    unsigned bl = x - tot, bin = 0u, before = 0u;
+    const bool mine = want >= bl && want - bl < tot;
+    if (mine) {
+        for (int k = 0; k < PER; ++k) {
+            const unsigned hk = hh[lane * PER + k];
+            if (want - bl < hk) {
+                bin = lane * PER + k;
+                before = bl;
+                break;
+            }
+            bl += hk;
+        }
+    }
+    const unsigned who = __ballot_sync(0xffffffffu, mine);
+    const int src = who ? __ffs(who) - 1 : 0;
+    bin = __shfl_sync(0xffffffffu, bin, src);
+    before = __shfl_sync(0xffffffffu, before, src);
+    if (lane == 0) {
+        rk[wid] = want - before;
+        pre[wid] |= bin << SH;
+    }
+}
+
 // One column per block: checks the bracket and selects both middle ranks
 // among its collected values (three radix levels on the bit patterns, as
 // above), else flags the column.
@@ -579,7 +609,6 @@ __global__ void __launch_bounds__(256) tvg_bracket_select_kernel(const unsigned*
         pre[threadIdx.x] = 0u;
         rk[threadIdx.x] = (threadIdx.x ? R1 : R0) - nb;
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll 1
     for (int L = 0; L < 3; ++L) {
         const int NB = L == 0 ? 2048 : 1024, SH = L == 0 ? 20 : (L == 1 ? 10 : 0), PSH = L == 1 ? 20 : 10;
@@ -592,40 +621,48 @@ __global__ void __launch_bounds__(256) tvg_bracket_select_kernel(const unsigned*
             if (L > 0 && (b >> PSH) == p1) atomicAdd(&h[1024 + k], 1u);
         }
         __syncthreads();
-        // warp r picks the bin of rank r (level 0: one histogram for both)
-        if (wid < 2) {
-            const unsigned* hh = h + (L == 0 ? 0 : wid * 1024);
-            const int PER = NB / 32;
-            const unsigned want = rk[wid];
-            unsigned tot = 0u;
-            for (int k = 0; k < PER; ++k) tot += hh[lane * PER + k];
-            unsigned x = tot;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            unsigned bl = x - tot, bin = 0u, before = 0u;
-            const bool mine = want >= bl && want - bl < tot;
-            if (mine) {
-                for (int k = 0; k < PER; ++k) {
-                    const unsigned hk = hh[lane * PER + k];
-                    if (want - bl < hk) {
-                        bin = lane * PER + k;
-                        before = bl;
-                        break;
-                    }
-                    bl += hk;
-                }
-            }
-            const unsigned who = __ballot_sync(0xffffffffu, mine);
-            const int src = who ? __ffs(who) - 1 : 0;
-            bin = __shfl_sync(0xffffffffu, bin, src);
-            before = __shfl_sync(0xffffffffu, before, src);
-            if (lane == 0) {
-                rk[wid] = want - before;
-                pre[wid] |= bin << SH;
-            }
+        tvg_block_pick(h, L, NB, SH, pre, rk);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) med[col] = 0.5 * ((double)__uint_as_float(pre[0]) + (double)__uint_as_float(pre[1]));
+}
+
+// The exact select of a flagged column over all its rows, one block per
+// column (columns not flagged return at once): the three radix levels, each
+// thread reading every 256th row, eight rows in flight.
+__global__ void __launch_bounds__(256) tvg_column_select_kernel(const float2* __restrict__ e, long long rows, int n,
+                                                                const int* __restrict__ flags,
+                                                                double* __restrict__ med) {
+    const int col = blockIdx.x;
+    if (!flags[col]) return;
+    __shared__ unsigned h[2048];
+    __shared__ unsigned pre[2], rk[2];
+    if (threadIdx.x < 2) {
+        pre[threadIdx.x] = 0u;
+        rk[threadIdx.x] = (unsigned)(threadIdx.x ? rows / 2 : (rows - 1) / 2);
+    }
+#pragma unroll 1
+    for (int L = 0; L < 3; ++L) {
+        const int NB = L == 0 ? 2048 : 1024, SH = L == 0 ? 20 : (L == 1 ? 10 : 0), PSH = L == 1 ? 20 : 10;
+        for (int t = threadIdx.x; t < 2048; t += blockDim.x) h[t] = 0u;
+        __syncthreads();
+        const unsigned p0 = pre[0] >> PSH, p1 = pre[1] >> PSH;
+        auto add = [&](unsigned b) {
+            const unsigned k = (b >> SH) & (unsigned)(NB - 1);
+            if (L == 0 || (b >> PSH) == p0) atomicAdd(&h[k], 1u);
+            if (L > 0 && (b >> PSH) == p1) atomicAdd(&h[1024 + k], 1u);
+        };
+        long long r = threadIdx.x;
+        for (; r + 7 * 256 < rows; r += 8 * 256) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = e[(r + u * 256) * n + col];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) add(tvg_bits(v[u]));
         }
+        for (; r < rows; r += 256) add(tvg_bits(e[r * n + col]));
+        __syncthreads();
+        tvg_block_pick(h, L, NB, SH, pre, rk);
         __syncthreads();
     }
     if (threadIdx.x == 0) med[col] = 0.5 * ((double)__uint_as_float(pre[0]) + (double)__uint_as_float(pre[1]));
@@ -1027,7 +1064,7 @@ extern "C" int sas_tvg(const void* d_in, void* d_out, int64_t rows, int32_t n, d
     const float2* ein = (const float2*)d_in;
     if (rows < TVG_BRACKET_MIN_ROWS) {
         tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, rows, 1, n, (unsigned)((rows - 1) / 2),
-                                                                 (unsigned)(rows / 2), med, nullptr, nullptr);
+                                                                 (unsigned)(rows / 2), med, nullptr);
     } else {
         // the sample: every rstep-th row (m of them), its ranks m/2 -+ about four standard deviations
         const long long rstep = rows / TVG_SAMPLE, m = (rows + rstep - 1) / rstep;
@@ -1048,11 +1085,10 @@ extern "C" int sas_tvg(const void* d_in, void* d_out, int64_t rows, int32_t n, d
         unsigned* nb = reinterpret_cast<unsigned*>(scr + o_b);
         unsigned* ni = reinterpret_cast<unsigned*>(scr + o_n);
         int* fl = reinterpret_cast<int*>(scr + o_f);
-        tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, m, rstep, n, k_lo, k_hi, nullptr, br, nullptr);
+        tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, m, rstep, n, k_lo, k_hi, nullptr, br);
         tvg_collect_kernel<<<strips, TVG_THREADS, 0, st>>>(ein, rows, n, br, cand, nb, ni);
         tvg_bracket_select_kernel<<<(unsigned)n, 256, 0, st>>>(cand, nb, ni, rows, med, fl);
-        tvg_select_kernel<<<strips, TVG_THREADS, TVG_SMEM, st>>>(ein, rows, 1, n, (unsigned)((rows - 1) / 2),
-                                                                 (unsigned)(rows / 2), med, nullptr, fl);
+        tvg_column_select_kernel<<<(unsigned)n, 256, 0, st>>>(ein, rows, n, fl, med);
         cudaFreeAsync(scr, st);
     }
     tvg_gain_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(med, n, alpha, gain);
