@@ -647,7 +647,7 @@ def run_dpc(args, rank, world, local_rank):
             "metric": "DPC time-delay estimation throughput (algorithmic bytes)", "value": world * gbs,
             "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (solve f64)",
-            "data": "synthetic (seeded band-limited echo rows; the delays are timed, not judged; the solve uses "
+            "data": "synthetic (seeded band-limited echo rows; the delays are timed, not scored; the solve uses "
                     "delays predicted from a sway/heave trajectory plus 50 ns noise)",
             "config": {"workload": w.name, "stage": "dpc", "pings": P, "rx": C, "shift": shift, "windows": K,
                        "window_samples": W, "max_lag": L, "measurements": M,

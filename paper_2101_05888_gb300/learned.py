@@ -10,7 +10,8 @@ windows produced by the library's own echo simulator (the targets are the
 residual of that interpolation over the prior's), then tabulated (prior +
 network) at table_n + 1 fractions and handed to the backprojection kernels
 through the interpolator table slot (SAS_INTERP_TABLE).  The plain
-Kaiser-sinc stays available as the fallback and as the judge of its error.
+Kaiser-sinc stays available as the fallback, and the 32-tap Kaiser-sinc is the
+reference its error is measured against.
 
 Learning the correction rather than the taps themselves keeps the network's
 outputs small, so the FP16 rounding of its weights and its fitting error cost
