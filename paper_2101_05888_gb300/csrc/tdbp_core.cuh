@@ -1210,9 +1210,13 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
     // path is D / (1 + eps), eps = u_R.v / c ~ 1e-3, taken as
     // D (1 - eps + eps^2) (neglected: eps^3 D ~ 1e-9 m and the curvature term
     // |v dtau|^2 / (2 |R|) ~ 2e-8 m).
-    auto pixels = [&](auto masked, const float4 q0, const float4 q1, const float* rot, uint32_t rmask_needed,
+    // DIRECT: the carrier phase goes to the SFU without a range reduction
+    // (p.phase_direct); a compile-time branch, so that the reduction's
+    // instructions are not issued predicated off on every pixel
+    auto pixels = [&](auto masked, auto direct, const float4 q0, const float4 q1, const float* rot, uint32_t rmask_needed,
                       const unsigned char* erow, const float4 q6, const float4 q7, const float4* hr, int rfl) {
         constexpr bool MASKED = decltype(masked)::value;
+        constexpr bool DIRECT = decltype(direct)::value;
         const float tRx = q0.x, tRy = q0.y, tRz = q0.z, nR2 = q0.w;
         const float nR = q1.x, ufc = q1.y, phr = q1.z;   // phr: reference carrier phase [rad]
         const float tRv = DIM3 ? tRz : tRy;
@@ -1291,7 +1295,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             // t = v + 1.5*2^23 (round to nearest), and g = v - that = frac(2u) - 1/2
             const float2 t = fadd2(v, magic2);
             const float2 g2 = fsub2(v, fsub2(t, magic2));
-            if (!p.phase_direct) x2 = reduce_phase2(x2);
+            if constexpr (!DIRECT) x2 = reduce_phase2(x2);
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
             const int s = 2 * k + j;
@@ -1480,11 +1484,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) tdbp_kernel(const __grid_constant
             const float4 q6 = MOTION ? hr[6] : make_float4(0.f, 0.f, 0.f, 0.f);
             const float4 q7 = (MOTION && BEAM) ? hr[7] : make_float4(0.f, 0.f, 0.f, 0.f);
             const unsigned char* erow = eb + j * ebuf_pair;
-            if (!BEAM || (flags & (FL_TX_FULL | FL_RX_FULL)) == (FL_TX_FULL | FL_RX_FULL))
-                pixels(std::integral_constant<bool, false>{}, q0, q1, rot, 0u, erow, q6, q7, hr, rfl);
-            else
-                pixels(std::integral_constant<bool, BEAM>{}, q0, q1, rot, (flags & FL_RX_FULL) ? 0u : 1u, erow, q6,
-                       q7, hr, rfl);
+            using F_ = std::integral_constant<bool, false>;
+            using T_ = std::integral_constant<bool, true>;
+            using B_ = std::integral_constant<bool, BEAM>;
+            if (!BEAM || (flags & (FL_TX_FULL | FL_RX_FULL)) == (FL_TX_FULL | FL_RX_FULL)) {
+                if (p.phase_direct)
+                    pixels(F_{}, T_{}, q0, q1, rot, 0u, erow, q6, q7, hr, rfl);
+                else
+                    pixels(F_{}, F_{}, q0, q1, rot, 0u, erow, q6, q7, hr, rfl);
+            } else {
+                const uint32_t rmn = (flags & FL_RX_FULL) ? 0u : 1u;
+                if (p.phase_direct)
+                    pixels(B_{}, T_{}, q0, q1, rot, rmn, erow, q6, q7, hr, rfl);
+                else
+                    pixels(B_{}, F_{}, q0, q1, rot, rmn, erow, q6, q7, hr, rfl);
+            }
         }
         warp_arrive(&eempty[b]);
         if (gflags & GD_STAGE_END) warp_arrive(&rempty[rs]);
