@@ -84,3 +84,15 @@ def test_conditioning_and_dpc_argument_errors_without_gpu(libsas):
     assert libsas.sas_dpc_footprints(None, fake, fake, fake, None) == sas.SAS_ERR_ARG
     pr = sas.sas_dpc_problem(P=1, C=8, shift=2, K=4, side=1, c=1500.0)                          # P < 2
     assert libsas.sas_dpc_solve(ctypes.byref(pr), fake, fake, 10, None, None, None) == sas.SAS_ERR_ARG
+
+
+def test_build_flags_and_interp_form_degree_without_gpu(libsas):
+    """The plain library reports no checked build (the checked one, built with
+    -DSAS_CHECKED, reports bit 0); the Farrow-form evaluation refuses a degree
+    other than the cubic (3) and the quadratic (2) before touching a device."""
+    expect = 1 if os.environ.get("SAS_CHECKED") == "1" else 0
+    assert libsas.sas_build_flags() == expect
+    it = sas.kaiser(4.0)
+    for degree in (0, 1, 4):
+        rc = libsas.sas_interp_eval_form(ctypes.byref(it), degree, None, 0, None, None, None)
+        assert rc == sas.SAS_ERR_ARG
